@@ -1,0 +1,248 @@
+"""Plain FP64 CPU oracle for ILU0-preconditioned BiCGStab on 3x3 BSR matrices.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the benchmark's CPU-baseline leg import this package; the GPU library and its
+Python binding never do, and this package imports nothing from them.
+
+The arithmetic lives in ``oracle.c`` (single-threaded C, ``-O2
+-ffp-contract=off``); this module only marshals numpy arrays through ctypes and
+assembles dense matrices for brute-force checks.
+
+Section references are to arXiv 2309.11488:
+  * SpMV                       -- Section 4.3
+  * ILU0 decomposition          -- Section 2.2, Algorithm 2 (block reading:
+                                   right product with the inverse pivot block)
+  * ILU0 application            -- Section 2.2, Algorithm 1, equations 3-4
+  * BiCGStab and stopping rule  -- Section 4.2 (method: van der Vorst 1992,
+                                   right preconditioning, x0 = 0)
+  * level scheduling / colouring-- Section 4.4
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library beside it (plain gcc)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        L.orc_inv3.argtypes = [_f64p, _f64p]
+        L.orc_spmv.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.orc_spmv.restype = None
+        L.orc_ilu0.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.orc_ilu0_f32.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f32p, _f32p]
+        L.orc_ilu_apply.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_ilu_apply.restype = None
+        L.orc_ilu_apply_f32.argtypes = [ctypes.c_int32, _i32p, _i32p, _f32p, _f32p, _f64p, _f64p]
+        L.orc_ilu_apply_f32.restype = None
+        L.orc_bicgstab.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f32p, _f32p,
+                                   _f64p, _f64p, ctypes.c_double, ctypes.c_int32, _i32p, _f64p, _f64p]
+        L.orc_dense_solve.argtypes = [ctypes.c_int32, _f64p, _f64p]
+        L.orc_levels.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        L.orc_levels.restype = ctypes.c_int32
+        L.orc_colours.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        L.orc_colours.restype = ctypes.c_int32
+        L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
+        L.orc_order_by_key.restype = None
+        L.orc_permute.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
+        L.orc_permute.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+
+def inv3(a):
+    a = _f64(a).reshape(9)
+    out = np.empty(9)
+    st = lib().orc_inv3(_p(a, _f64p), _p(out, _f64p))
+    return out.reshape(3, 3), st
+
+
+def spmv(nb, rowptr, colidx, vals, x):
+    rowptr, colidx, vals, x = _i32(rowptr), _i32(colidx), _f64(vals), _f64(x)
+    y = np.empty(3 * nb)
+    lib().orc_spmv(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p), _p(x, _f64p), _p(y, _f64p))
+    return y
+
+
+@dataclass
+class Factors:
+    lu: np.ndarray    # same pattern as A, (nnzb, 9)
+    dinv: np.ndarray  # (nb, 9)
+    status: int       # 0, or -(1+i) singular pivot at row i, -(1+nb+i) no diagonal in row i
+    f32: bool = False
+
+
+def ilu0(nb, rowptr, colidx, vals, f32=False) -> Factors:
+    rowptr, colidx, vals = _i32(rowptr), _i32(colidx), _f64(vals)
+    nnzb = int(rowptr[nb])
+    if f32:
+        lu = np.empty((nnzb, 9), dtype=np.float32)
+        dinv = np.empty((nb, 9), dtype=np.float32)
+        st = lib().orc_ilu0_f32(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+                                _p(lu, _f32p), _p(dinv, _f32p))
+    else:
+        lu = np.empty((nnzb, 9))
+        dinv = np.empty((nb, 9))
+        st = lib().orc_ilu0(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+                            _p(lu, _f64p), _p(dinv, _f64p))
+    return Factors(lu, dinv, int(st), f32)
+
+
+def ilu_apply(nb, rowptr, colidx, fac: Factors, r):
+    rowptr, colidx, r = _i32(rowptr), _i32(colidx), _f64(r)
+    z = np.empty(3 * nb)
+    if fac.f32:
+        lib().orc_ilu_apply_f32(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(fac.lu, _f32p),
+                                _p(fac.dinv, _f32p), _p(r, _f64p), _p(z, _f64p))
+    else:
+        lib().orc_ilu_apply(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(fac.lu, _f64p),
+                            _p(fac.dinv, _f64p), _p(r, _f64p), _p(z, _f64p))
+    return z
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    status: int      # 0 converged, 1 not converged, -5 breakdown, -6 non-finite rhs
+    iters: int
+    relres: float    # true ||b - A x|| / ||b||
+    res_hist: np.ndarray
+
+
+def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200) -> SolveResult:
+    rowptr, colidx, vals, b = _i32(rowptr), _i32(colidx), _f64(vals), _f64(b)
+    x = np.empty(3 * nb)
+    it = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1)
+    hist = np.full(2 * maxit + 1, np.nan)
+    lu64 = fac.lu if not fac.f32 else None
+    d64 = fac.dinv if not fac.f32 else None
+    lu32 = fac.lu if fac.f32 else None
+    d32 = fac.dinv if fac.f32 else None
+    st = lib().orc_bicgstab(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+                            _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
+                            _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
+                            _p(hist, _f64p))
+    return SolveResult(x, int(st), int(it[0]), float(rr[0]), hist)
+
+
+def dense_solve(a, b):
+    a = np.array(a, dtype=np.float64, order="C", copy=True)
+    b = np.array(b, dtype=np.float64, copy=True)
+    st = lib().orc_dense_solve(a.shape[0], _p(a, _f64p), _p(b, _f64p))
+    return b, st
+
+
+def levels(nb, rowptr, colidx):
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    lev = np.empty(nb, dtype=np.int32)
+    n = lib().orc_levels(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(lev, _i32p))
+    return lev, int(n)
+
+
+def colours(nb, rowptr, colidx):
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    col = np.empty(nb, dtype=np.int32)
+    n = lib().orc_colours(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(col, _i32p))
+    return col, int(n)
+
+
+def order_by_key(key, nkeys):
+    key = _i32(key)
+    perm = np.empty(key.shape[0], dtype=np.int32)
+    lib().orc_order_by_key(key.shape[0], _p(key, _i32p), nkeys, _p(perm, _i32p))
+    return perm
+
+
+def schedule_perm(nb, rowptr, colidx, schedule):
+    """perm[new] = old for 'natural', 'level' or 'colour' (Section 4.4);
+    returns (perm, number of sets)."""
+    if schedule == "natural":
+        return np.arange(nb, dtype=np.int32), 1
+    if schedule == "level":
+        key, n = levels(nb, rowptr, colidx)
+    elif schedule == "colour":
+        key, n = colours(nb, rowptr, colidx)
+    else:
+        raise ValueError(schedule)
+    return order_by_key(key, n), n
+
+
+def permute(nb, rowptr, colidx, vals, perm):
+    rowptr, colidx, vals, perm = _i32(rowptr), _i32(colidx), _f64(vals), _i32(perm)
+    nnzb = int(rowptr[nb])
+    prow = np.empty(nb + 1, dtype=np.int32)
+    pcol = np.empty(nnzb, dtype=np.int32)
+    pval = np.empty((nnzb, 9))
+    lib().orc_permute(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p), _p(perm, _i32p),
+                      _p(prow, _i32p), _p(pcol, _i32p), _p(pval, _f64p))
+    return prow, pcol, pval
+
+
+def to_dense(nb, rowptr, colidx, vals):
+    """Assemble the 3nb x 3nb dense matrix (brute-force checks only)."""
+    a = np.zeros((3 * nb, 3 * nb))
+    vals = np.asarray(vals).reshape(-1, 3, 3)
+    for i in range(nb):
+        for m in range(rowptr[i], rowptr[i + 1]):
+            j = colidx[m]
+            a[3 * i:3 * i + 3, 3 * j:3 * j + 3] = vals[m]
+    return a
+
+
+def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False):
+    """Same-ordering reference: ILU0 + BiCGStab on P A P^T with the oracle's
+    own schedule permutation; returns (x in natural order, SolveResult, perm, nsets)."""
+    perm, nsets = schedule_perm(nb, rowptr, colidx, schedule)
+    prow, pcol, pval = permute(nb, rowptr, colidx, vals, perm)
+    pb = np.asarray(b).reshape(nb, 3)[perm].ravel()
+    fac = ilu0(nb, prow, pcol, pval, f32=f32)
+    if fac.status != 0:
+        raise ArithmeticError(f"oracle ILU0 failed with status {fac.status}")
+    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit)
+    x = np.empty(3 * nb)
+    x.reshape(nb, 3)[perm] = res.x.reshape(nb, 3)
+    return x, res, perm, nsets

@@ -1,0 +1,568 @@
+/*
+ * Plain FP64 CPU oracle for ILU0-preconditioned BiCGStab on 3x3 block-CSR
+ * matrices.  TEST INFRASTRUCTURE ONLY: the GPU library never links, loads or
+ * calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do.
+ *
+ * Everything here is written for a reader checking it against the paper by
+ * eye: single-threaded loops, no blocking, no fusion, no reordering beyond what
+ * each definition states.  Compiled with -O2 -ffp-contract=off so that no
+ * multiply-add is fused.
+ *
+ * Storage convention (Section 4.1, "Figure: Memory layout of blocks in OPM",
+ * left panel): block-CSR with nb block rows, rowptr[nb+1], colidx[nnzb]
+ * sorted and unique inside every row, and each 3x3 block stored contiguously
+ * and row-major: entry (r, c) of block m is vals[9*m + 3*r + c].  Vectors are
+ * nb*3 doubles, the 3 unknowns of one cell contiguous (Section 4.1).
+ *
+ * Pins: every function below is checked by the CPU test suite against
+ * something other than itself (dense brute force, exact LU on no-fill
+ * patterns, the ILU0 defining identity, closed forms of grid schedules).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define BS 3
+#define BS2 9
+
+/* ------------------------------------------------------------------------ */
+/* small dense helpers on 3x3 row-major blocks                              */
+/* ------------------------------------------------------------------------ */
+
+/* c = a * b */
+static void blk_mul(const double *a, const double *b, double *c) {
+  for (int r = 0; r < BS; ++r)
+    for (int s = 0; s < BS; ++s) {
+      double acc = 0.0;
+      for (int t = 0; t < BS; ++t) acc += a[r * BS + t] * b[t * BS + s];
+      c[r * BS + s] = acc;
+    }
+}
+
+/* c -= a * b */
+static void blk_mul_sub(const double *a, const double *b, double *c) {
+  double p[BS2];
+  blk_mul(a, b, p);
+  for (int e = 0; e < BS2; ++e) c[e] -= p[e];
+}
+
+/* y += a * x (3-vector) */
+static void blk_matvec_add(const double *a, const double *x, double *y) {
+  for (int r = 0; r < BS; ++r) {
+    double acc = 0.0;
+    for (int c = 0; c < BS; ++c) acc += a[r * BS + c] * x[c];
+    y[r] += acc;
+  }
+}
+
+/*
+ * Inverse of a 3x3 block by Gauss-Jordan elimination with partial pivoting
+ * (textbook method; deliberately not the adjugate formula the GPU uses).
+ * Returns 0, or -1 when a pivot is exactly zero or the result is not finite.
+ */
+int orc_inv3(const double *a_in, double *ainv) {
+  double a[BS][2 * BS];
+  for (int r = 0; r < BS; ++r)
+    for (int c = 0; c < BS; ++c) {
+      a[r][c] = a_in[r * BS + c];
+      a[r][BS + c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int col = 0; col < BS; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < BS; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (a[piv][col] == 0.0) return -1;
+    if (piv != col)
+      for (int c = 0; c < 2 * BS; ++c) {
+        double t = a[col][c];
+        a[col][c] = a[piv][c];
+        a[piv][c] = t;
+      }
+    double d = a[col][col];
+    for (int c = 0; c < 2 * BS; ++c) a[col][c] /= d;
+    for (int r = 0; r < BS; ++r) {
+      if (r == col) continue;
+      double f = a[r][col];
+      if (f != 0.0)
+        for (int c = 0; c < 2 * BS; ++c) a[r][c] -= f * a[col][c];
+    }
+  }
+  for (int r = 0; r < BS; ++r)
+    for (int c = 0; c < BS; ++c) {
+      ainv[r * BS + c] = a[r][BS + c];
+      if (!isfinite(ainv[r * BS + c])) return -1;
+    }
+  return 0;
+}
+
+/* position of column j in row i, or -1 (linear scan: rows are short) */
+static int64_t find_block(const int32_t *rowptr, const int32_t *colidx, int32_t i, int32_t j) {
+  for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m)
+    if (colidx[m] == j) return m;
+  return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Blocked SpMV, y = A x (Section 4.3): y_i = sum over the blocks A_ij of    */
+/* row i, in colidx order, of the dense product A_ij x_j.                   */
+/* ------------------------------------------------------------------------ */
+void orc_spmv(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+              const double *x, double *y) {
+  for (int32_t i = 0; i < nb; ++i) {
+    double yi[BS] = {0.0, 0.0, 0.0};
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m)
+      blk_matvec_add(vals + BS2 * m, x + (int64_t)BS * colidx[m], yi);
+    for (int r = 0; r < BS; ++r) y[(int64_t)BS * i + r] = yi[r];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* ILU0 decomposition (Section 2.2, Algorithm 2), block version.            */
+/*                                                                          */
+/* Algorithm 2 eliminates pivot r = 0..nb-1 in turn: every row i > r that   */
+/* has a block (i, r) in the pattern S gets a_ir <- a_ir * inv(a_rr), and   */
+/* then a_ij <- a_ij - a_ir * a_rj for each j > r with (i,j) and (r,j) in S. */
+/* For blocks the multiplier is a right product with the inverse pivot      */
+/* block.  Here the same updates are applied row by row: for row i, its     */
+/* pivots k < i are taken in ascending order, which gives every entry the    */
+/* same updates in the same order as the pivot-by-pivot loop.               */
+/*                                                                          */
+/* Output: lu holds L (unit lower, strictly-lower blocks stored) and U      */
+/* (diagonal and strictly-upper blocks) in the pattern of A; dinv[9*i] is   */
+/* the inverse of U's diagonal block of row i.                              */
+/* Returns 0, or -(1 + i) when the pivot block of row i is singular, or     */
+/* -(1 + nb + i) when row i has no diagonal block.                          */
+/* ------------------------------------------------------------------------ */
+int orc_ilu0(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+             double *lu, double *dinv) {
+  memcpy(lu, vals, sizeof(double) * BS2 * (size_t)rowptr[nb]);
+  for (int32_t i = 0; i < nb; ++i) {
+    for (int64_t mk = rowptr[i]; mk < rowptr[i + 1]; ++mk) {
+      int32_t k = colidx[mk];
+      if (k >= i) break; /* colidx is sorted: the rest is diagonal / upper */
+      /* L_ik = A_ik * inv(U_kk) */
+      double lik[BS2];
+      blk_mul(lu + BS2 * mk, dinv + BS2 * (int64_t)k, lik);
+      memcpy(lu + BS2 * mk, lik, sizeof lik);
+      /* A_ij -= L_ik * U_kj for every j > k present in both row i and row k */
+      for (int64_t mj = mk + 1; mj < rowptr[i + 1]; ++mj) {
+        int32_t j = colidx[mj];
+        int64_t mkj = find_block(rowptr, colidx, k, j);
+        if (mkj >= 0) blk_mul_sub(lik, lu + BS2 * mkj, lu + BS2 * mj);
+      }
+    }
+    int64_t md = find_block(rowptr, colidx, i, i);
+    if (md < 0) return -(1 + nb + i);
+    if (orc_inv3(lu + BS2 * md, dinv + BS2 * (int64_t)i) != 0) return -(1 + i);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ILU0 application (Section 2.2, Algorithm 1, equations 3 and 4):          */
+/* solve L y = r by forward substitution with the unit lower factor, then   */
+/* U z = y by backward substitution.                                        */
+/*   forward:  y_i = r_i - sum_{j<i} L_ij y_j,             i ascending      */
+/*   backward: z_i = inv(U_ii) (y_i - sum_{j>i} U_ij z_j),  i descending     */
+/* ------------------------------------------------------------------------ */
+void orc_ilu_apply(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *lu,
+                   const double *dinv, const double *r, double *z) {
+  double *y = (double *)malloc(sizeof(double) * BS * (size_t)nb);
+  for (int32_t i = 0; i < nb; ++i) {
+    double acc[BS];
+    for (int c = 0; c < BS; ++c) acc[c] = r[(int64_t)BS * i + c];
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j >= i) break;
+      double t[BS] = {0.0, 0.0, 0.0};
+      blk_matvec_add(lu + BS2 * m, y + (int64_t)BS * j, t);
+      for (int c = 0; c < BS; ++c) acc[c] -= t[c];
+    }
+    for (int c = 0; c < BS; ++c) y[(int64_t)BS * i + c] = acc[c];
+  }
+  for (int32_t i = nb - 1; i >= 0; --i) {
+    double acc[BS];
+    for (int c = 0; c < BS; ++c) acc[c] = y[(int64_t)BS * i + c];
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j <= i) continue;
+      double t[BS] = {0.0, 0.0, 0.0};
+      blk_matvec_add(lu + BS2 * m, z + (int64_t)BS * j, t);
+      for (int c = 0; c < BS; ++c) acc[c] -= t[c];
+    }
+    double zi[BS] = {0.0, 0.0, 0.0};
+    blk_matvec_add(dinv + BS2 * (int64_t)i, acc, zi);
+    for (int c = 0; c < BS; ++c) z[(int64_t)BS * i + c] = zi[c];
+  }
+  free(y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Single-precision variant of the two functions above: the same steps in   */
+/* float arithmetic, on values rounded to float.  Used as the reference for  */
+/* the form that stores and runs the ILU0 factors in FP32.                   */
+/* ------------------------------------------------------------------------ */
+static int inv3_f(const float *a_in, float *ainv) {
+  double a[BS2], o[BS2];
+  for (int e = 0; e < BS2; ++e) a[e] = a_in[e];
+  if (orc_inv3(a, o) != 0) return -1;
+  for (int e = 0; e < BS2; ++e) ainv[e] = (float)o[e];
+  return 0;
+}
+
+static void blk_mul_f(const float *a, const float *b, float *c) {
+  for (int r = 0; r < BS; ++r)
+    for (int s = 0; s < BS; ++s) {
+      float acc = 0.0f;
+      for (int t = 0; t < BS; ++t) acc += a[r * BS + t] * b[t * BS + s];
+      c[r * BS + s] = acc;
+    }
+}
+
+int orc_ilu0_f32(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                 float *lu, float *dinv) {
+  size_t nnz = (size_t)rowptr[nb];
+  for (size_t e = 0; e < BS2 * nnz; ++e) lu[e] = (float)vals[e];
+  for (int32_t i = 0; i < nb; ++i) {
+    for (int64_t mk = rowptr[i]; mk < rowptr[i + 1]; ++mk) {
+      int32_t k = colidx[mk];
+      if (k >= i) break;
+      float lik[BS2];
+      blk_mul_f(lu + BS2 * mk, dinv + BS2 * (int64_t)k, lik);
+      memcpy(lu + BS2 * mk, lik, sizeof lik);
+      for (int64_t mj = mk + 1; mj < rowptr[i + 1]; ++mj) {
+        int64_t mkj = find_block(rowptr, colidx, k, colidx[mj]);
+        if (mkj >= 0) {
+          float p[BS2];
+          blk_mul_f(lik, lu + BS2 * mkj, p);
+          for (int e = 0; e < BS2; ++e) lu[BS2 * mj + e] -= p[e];
+        }
+      }
+    }
+    int64_t md = find_block(rowptr, colidx, i, i);
+    if (md < 0) return -(1 + nb + i);
+    if (inv3_f(lu + BS2 * md, dinv + BS2 * (int64_t)i) != 0) return -(1 + i);
+  }
+  return 0;
+}
+
+void orc_ilu_apply_f32(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const float *lu,
+                       const float *dinv, const double *r, double *z) {
+  float *y = (float *)malloc(sizeof(float) * BS * (size_t)nb);
+  float *zf = (float *)malloc(sizeof(float) * BS * (size_t)nb);
+  for (int32_t i = 0; i < nb; ++i) {
+    float acc[BS];
+    for (int c = 0; c < BS; ++c) acc[c] = (float)r[(int64_t)BS * i + c];
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j >= i) break;
+      for (int a = 0; a < BS; ++a) {
+        float t = 0.0f;
+        for (int c = 0; c < BS; ++c) t += lu[BS2 * m + a * BS + c] * y[(int64_t)BS * j + c];
+        acc[a] -= t;
+      }
+    }
+    for (int c = 0; c < BS; ++c) y[(int64_t)BS * i + c] = acc[c];
+  }
+  for (int32_t i = nb - 1; i >= 0; --i) {
+    float acc[BS];
+    for (int c = 0; c < BS; ++c) acc[c] = y[(int64_t)BS * i + c];
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j <= i) continue;
+      for (int a = 0; a < BS; ++a) {
+        float t = 0.0f;
+        for (int c = 0; c < BS; ++c) t += lu[BS2 * m + a * BS + c] * zf[(int64_t)BS * j + c];
+        acc[a] -= t;
+      }
+    }
+    for (int a = 0; a < BS; ++a) {
+      float t = 0.0f;
+      for (int c = 0; c < BS; ++c) t += dinv[BS2 * (int64_t)i + a * BS + c] * acc[c];
+      zf[(int64_t)BS * i + a] = t;
+    }
+  }
+  for (size_t e = 0; e < BS * (size_t)nb; ++e) z[e] = zf[e];
+  free(y);
+  free(zf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* BiCGStab (van der Vorst, SIAM J. Sci. Stat. Comput. 13(2), 1992), right  */
+/* preconditioned by the ILU0 factors, x0 = 0, shadow residual r^ = r0.     */
+/* Stopping rule (Section 4.2): relative reduction of the residual 2-norm   */
+/* by rtol, at most maxit iterations; it is tested after each half step.    */
+/* The preconditioner is either the FP64 factors (lu, dinv) or, when lu32   */
+/* is not NULL, the FP32 ones (lu32, dinv32).                               */
+/*                                                                          */
+/* Returns 0 converged, 1 not converged after maxit, -5 breakdown           */
+/* (rho, (r^,v), (t,t) or omega exactly zero), -6 non-finite rhs.           */
+/* *iters = iterations begun (a half-step exit counts as its iteration);    */
+/* *relres = true ||b - A x|| / ||b|| after the solve; res_hist (optional,  */
+/* length 2*maxit+1) receives ||r0||, then ||s|| and ||r|| of each step.     */
+/* ------------------------------------------------------------------------ */
+static double dot(size_t n, const double *a, const double *b) {
+  double s = 0.0;
+  for (size_t e = 0; e < n; ++e) s += a[e] * b[e];
+  return s;
+}
+
+int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                 const double *lu, const double *dinv, const float *lu32, const float *dinv32,
+                 const double *b, double *x, double rtol, int32_t maxit, int32_t *iters,
+                 double *relres, double *res_hist) {
+  size_t n = (size_t)BS * nb;
+  double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double));
+  double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
+  double *ph = calloc(n, sizeof(double)), *s = calloc(n, sizeof(double));
+  double *sh = calloc(n, sizeof(double)), *t = calloc(n, sizeof(double));
+  int status = 1;
+  *iters = 0;
+  for (size_t e = 0; e < n; ++e) {
+    x[e] = 0.0;
+    r[e] = b[e];
+    rh[e] = b[e];
+  }
+  double n0 = sqrt(dot(n, r, r));
+  if (res_hist) res_hist[0] = n0;
+  if (!isfinite(n0)) {
+    status = -6;
+    goto done;
+  }
+  if (n0 == 0.0) {
+    status = 0;
+    goto done;
+  }
+  double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  double tol = rtol * n0;
+  for (int32_t k = 1; k <= maxit; ++k) {
+    *iters = k;
+    double rho = dot(n, rh, r);
+    if (rho == 0.0) {
+      status = -5;
+      break;
+    }
+    double beta = (rho / rho_prev) * (alpha / omega);
+    for (size_t e = 0; e < n; ++e) p[e] = r[e] + beta * (p[e] - omega * v[e]);
+    if (lu32) orc_ilu_apply_f32(nb, rowptr, colidx, lu32, dinv32, p, ph);
+    else orc_ilu_apply(nb, rowptr, colidx, lu, dinv, p, ph);
+    orc_spmv(nb, rowptr, colidx, vals, ph, v);
+    double rhv = dot(n, rh, v);
+    if (rhv == 0.0) {
+      status = -5;
+      break;
+    }
+    alpha = rho / rhv;
+    for (size_t e = 0; e < n; ++e) s[e] = r[e] - alpha * v[e];
+    double ns = sqrt(dot(n, s, s));
+    if (res_hist) res_hist[2 * k - 1] = ns;
+    if (ns <= tol) { /* half-step exit */
+      for (size_t e = 0; e < n; ++e) x[e] += alpha * ph[e];
+      status = 0;
+      break;
+    }
+    if (lu32) orc_ilu_apply_f32(nb, rowptr, colidx, lu32, dinv32, s, sh);
+    else orc_ilu_apply(nb, rowptr, colidx, lu, dinv, s, sh);
+    orc_spmv(nb, rowptr, colidx, vals, sh, t);
+    double tt = dot(n, t, t);
+    if (tt == 0.0) {
+      status = -5;
+      break;
+    }
+    omega = dot(n, t, s) / tt;
+    if (omega == 0.0) {
+      status = -5;
+      break;
+    }
+    for (size_t e = 0; e < n; ++e) {
+      x[e] += alpha * ph[e] + omega * sh[e];
+      r[e] = s[e] - omega * t[e];
+    }
+    rho_prev = rho;
+    double nr = sqrt(dot(n, r, r));
+    if (res_hist) res_hist[2 * k] = nr;
+    if (nr <= tol) {
+      status = 0;
+      break;
+    }
+  }
+done:
+  if (status == -6) {
+    *relres = NAN;
+  } else if (n0 == 0.0) {
+    *relres = 0.0;
+  } else {
+    orc_spmv(nb, rowptr, colidx, vals, x, t);
+    double nres = 0.0;
+    for (size_t e = 0; e < n; ++e) nres += (b[e] - t[e]) * (b[e] - t[e]);
+    *relres = sqrt(nres) / n0;
+  }
+  free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense Gaussian elimination with partial pivoting, A x = b in place      */
+/* (brute-force reference for tiny systems).  a is n x n row-major.         */
+/* Returns 0 or -1 when singular.                                           */
+/* ------------------------------------------------------------------------ */
+int orc_dense_solve(int32_t n, double *a, double *b) {
+  for (int32_t col = 0; col < n; ++col) {
+    int32_t piv = col;
+    for (int32_t r = col + 1; r < n; ++r)
+      if (fabs(a[(size_t)r * n + col]) > fabs(a[(size_t)piv * n + col])) piv = r;
+    if (a[(size_t)piv * n + col] == 0.0) return -1;
+    if (piv != col) {
+      for (int32_t c = 0; c < n; ++c) {
+        double t = a[(size_t)col * n + c];
+        a[(size_t)col * n + c] = a[(size_t)piv * n + c];
+        a[(size_t)piv * n + c] = t;
+      }
+      double t = b[col];
+      b[col] = b[piv];
+      b[piv] = t;
+    }
+    for (int32_t r = col + 1; r < n; ++r) {
+      double f = a[(size_t)r * n + col] / a[(size_t)col * n + col];
+      if (f == 0.0) continue;
+      for (int32_t c = col; c < n; ++c) a[(size_t)r * n + c] -= f * a[(size_t)col * n + c];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int32_t r = n - 1; r >= 0; --r) {
+    double acc = b[r];
+    for (int32_t c = r + 1; c < n; ++c) acc -= a[(size_t)r * n + c] * b[c];
+    b[r] = acc / a[(size_t)r * n + r];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parallel schedules (Section 4.4).  Both work on the symmetrised pattern  */
+/* (an edge i-j whenever block (i,j) or (j,i) is present).                  */
+/*                                                                          */
+/* Level scheduling: level(i) = 0 if i has no neighbour j < i, else         */
+/* 1 + max level(j) over its neighbours j < i.  Rows of one level have no   */
+/* edge between them, every edge joins rows of different levels, and        */
+/* ordering rows by level keeps every edge's direction, so the ILU0 of the  */
+/* level-ordered matrix is the natural-order ILU0 relabelled.               */
+/*                                                                          */
+/* Graph colouring: greedy first fit in natural row order, each row taking  */
+/* the smallest colour not used by a neighbour coloured before it.          */
+/*                                                                          */
+/* Both return the number of sets; key[i] is the set of row i.  The        */
+/* adjacency is built here from the pattern (CSR of the symmetrised graph). */
+/* ------------------------------------------------------------------------ */
+static void sym_graph(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int64_t **gptr,
+                      int32_t **gadj) {
+  int64_t *deg = calloc((size_t)nb + 1, sizeof(int64_t));
+  for (int32_t i = 0; i < nb; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j == i) continue;
+      deg[i]++;
+      deg[j]++;
+    }
+  int64_t *ptr = calloc((size_t)nb + 1, sizeof(int64_t));
+  for (int32_t i = 0; i < nb; ++i) ptr[i + 1] = ptr[i] + deg[i];
+  int32_t *adj = malloc(sizeof(int32_t) * (size_t)(ptr[nb] ? ptr[nb] : 1));
+  int64_t *fill = calloc((size_t)nb, sizeof(int64_t));
+  for (int32_t i = 0; i < nb; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j == i) continue;
+      adj[ptr[i] + fill[i]++] = j;
+      adj[ptr[j] + fill[j]++] = i;
+    }
+  free(deg);
+  free(fill);
+  *gptr = ptr;
+  *gadj = adj;
+}
+
+int32_t orc_levels(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *level) {
+  int64_t *gptr;
+  int32_t *gadj;
+  sym_graph(nb, rowptr, colidx, &gptr, &gadj);
+  int32_t nlev = 0;
+  for (int32_t i = 0; i < nb; ++i) {
+    int32_t l = 0;
+    for (int64_t m = gptr[i]; m < gptr[i + 1]; ++m) {
+      int32_t j = gadj[m];
+      if (j < i && level[j] + 1 > l) l = level[j] + 1;
+    }
+    level[i] = l;
+    if (l + 1 > nlev) nlev = l + 1;
+  }
+  free(gptr);
+  free(gadj);
+  return nlev;
+}
+
+int32_t orc_colours(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *colour) {
+  int64_t *gptr;
+  int32_t *gadj;
+  sym_graph(nb, rowptr, colidx, &gptr, &gadj);
+  int32_t ncol = 0;
+  for (int32_t i = 0; i < nb; ++i) colour[i] = -1;
+  for (int32_t i = 0; i < nb; ++i) {
+    int32_t c = 0;
+    for (;;) { /* smallest colour unused by an already coloured neighbour */
+      int used = 0;
+      for (int64_t m = gptr[i]; m < gptr[i + 1]; ++m)
+        if (colour[gadj[m]] == c) {
+          used = 1;
+          break;
+        }
+      if (!used) break;
+      ++c;
+    }
+    colour[i] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  free(gptr);
+  free(gadj);
+  return ncol;
+}
+
+/* perm[new] = old: rows ordered by key, natural order inside each key */
+void orc_order_by_key(int32_t nb, const int32_t *key, int32_t nkeys, int32_t *perm) {
+  int32_t pos = 0;
+  for (int32_t k = 0; k < nkeys; ++k)
+    for (int32_t i = 0; i < nb; ++i)
+      if (key[i] == k) perm[pos++] = i;
+}
+
+/*
+ * P A P^T for perm[new] = old: new row i' is old row perm[i'], its columns
+ * renumbered by the inverse permutation and sorted.  Output arrays are
+ * sized like the input (prowptr nb+1, pcolidx nnzb, pvals 9*nnzb).
+ */
+void orc_permute(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                 const int32_t *perm, int32_t *prowptr, int32_t *pcolidx, double *pvals) {
+  int32_t *iperm = malloc(sizeof(int32_t) * (size_t)nb);
+  for (int32_t i = 0; i < nb; ++i) iperm[perm[i]] = i;
+  prowptr[0] = 0;
+  for (int32_t ni = 0; ni < nb; ++ni) {
+    int32_t oi = perm[ni];
+    int64_t len = rowptr[oi + 1] - rowptr[oi];
+    int64_t base = prowptr[ni];
+    prowptr[ni + 1] = (int32_t)(base + len);
+    /* insertion sort of the renumbered columns, carrying the blocks along */
+    for (int64_t q = 0; q < len; ++q) {
+      int64_t m = rowptr[oi] + q;
+      int32_t nc = iperm[colidx[m]];
+      int64_t at = base + q;
+      while (at > base && pcolidx[at - 1] > nc) {
+        pcolidx[at] = pcolidx[at - 1];
+        memcpy(pvals + BS2 * at, pvals + BS2 * (at - 1), sizeof(double) * BS2);
+        --at;
+      }
+      pcolidx[at] = nc;
+      memcpy(pvals + BS2 * at, vals + BS2 * m, sizeof(double) * BS2);
+    }
+  }
+  free(iperm);
+}

@@ -1,0 +1,407 @@
+"""Pins of the FP64 CPU oracle to facts outside itself (CPU only).
+
+Each test checks the oracle against mathematics or the paper, never against a
+retyping of its own formula: dense brute force, exact LU on no-fill patterns,
+the ILU0 defining identity (LU)_ij = A_ij on the pattern, closed forms of the
+block Thomas recurrence and of grid schedules, and the generator's sizes
+printed in the paper's benchmark table.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_11488_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_facts():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_facts.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+def dense_factors(sysm, fac):
+    """Dense unit-lower L and upper U from the oracle's packed factors."""
+    nb = sysm.nb
+    L = np.eye(3 * nb)
+    U = np.zeros((3 * nb, 3 * nb))
+    lu = fac.lu.reshape(-1, 3, 3).astype(np.float64)
+    for i in range(nb):
+        for m in range(sysm.rowptr[i], sysm.rowptr[i + 1]):
+            j = sysm.colidx[m]
+            if j < i:
+                L[3 * i:3 * i + 3, 3 * j:3 * j + 3] = lu[m]
+            else:
+                U[3 * i:3 * i + 3, 3 * j:3 * j + 3] = lu[m]
+    return L, U
+
+
+def rhs(s):
+    return O.spmv(s.nb, s.rowptr, s.colidx, s.vals, s.x_true)
+
+
+# ---------------------------------------------------------------- blocks
+
+def test_inv3_matches_numpy():
+    key = synth.stream_key(7, 1)
+    a = synth.uniform(key, np.arange(9 * 50, dtype=np.uint64), -1, 1).reshape(50, 3, 3)
+    a += 3 * np.eye(3)
+    for m in range(50):
+        inv, st = O.inv3(a[m])
+        assert st == 0
+        np.testing.assert_allclose(inv, np.linalg.inv(a[m]), rtol=1e-13, atol=1e-14)
+
+
+def test_inv3_needs_pivoting_and_flags_singular():
+    a = np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 2.0]])  # zero leading entry
+    inv, st = O.inv3(a)
+    assert st == 0
+    np.testing.assert_allclose(inv @ a, np.eye(3), atol=1e-15)
+    _, st = O.inv3(np.array([[1.0, 2, 3], [2, 4, 6], [0, 0, 1]]))
+    assert st == -1
+
+
+# ---------------------------------------------------------------- SpMV
+
+@pytest.mark.parametrize("maker", [synth.config1, lambda: synth.random_pattern_system(40, 3, 11),
+                                   lambda: synth.tree_system(30, 5)])
+def test_spmv_brute_force(maker):
+    s = maker()
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    y = O.spmv(s.nb, s.rowptr, s.colidx, s.vals, s.x_true)
+    np.testing.assert_allclose(y, A @ s.x_true, rtol=1e-13, atol=1e-13)
+
+
+def test_spmv_block_is_row_major():
+    # one block row, one block: y = B x with B[r][c] = vals[3r + c]
+    vals = np.arange(1.0, 10.0).reshape(1, 9)
+    y = O.spmv(1, np.array([0, 1]), np.array([0]), vals, np.array([1.0, 0.0, 0.0]))
+    np.testing.assert_array_equal(y, [1.0, 4.0, 7.0])  # first column of row-major [[1,2,3],[4,5,6],[7,8,9]]
+
+
+# ---------------------------------------------------------------- ILU0
+
+def test_block_thomas_closed_form():
+    rows = []
+    with open(os.path.join(GOLDEN, "block_thomas.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    nb = len(rows)
+    rowptr = [0]
+    colidx, vals = [], []
+    for i in range(nb):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < nb:
+                colidx.append(j)
+                vals.append((2.0 if i == j else -1.0) * np.eye(3).ravel())
+        rowptr.append(len(colidx))
+    rowptr, colidx, vals = np.array(rowptr), np.array(colidx), np.array(vals)
+    fac = O.ilu0(nb, rowptr, colidx, vals)
+    assert fac.status == 0
+    for k, (_, d, l) in enumerate(rows):
+        d = float(Fraction(d))
+        np.testing.assert_allclose(fac.dinv[k].reshape(3, 3), np.eye(3) / d, rtol=1e-15)
+        md = rowptr[k] + (1 if k > 0 else 0)
+        np.testing.assert_allclose(fac.lu[md].reshape(3, 3), d * np.eye(3), rtol=1e-15)
+        if l != "none":
+            ml = rowptr[k + 1]  # block (k+1, k) is first in row k+1
+            np.testing.assert_allclose(fac.lu[ml].reshape(3, 3), float(Fraction(l)) * np.eye(3),
+                                       rtol=1e-15)
+
+
+@pytest.mark.parametrize("nb", [1, 2, 5])
+def test_ilu0_dense_pattern_is_exact_lu(nb):
+    s = synth.random_pattern_system(nb, 0, seed=100 + nb, dense=True)
+    assert s.nnzb == nb * nb
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    assert fac.status == 0
+    L, U = dense_factors(s, fac)
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    np.testing.assert_allclose(L @ U, A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    # dinv is the inverse of U's diagonal blocks
+    for i in range(nb):
+        np.testing.assert_allclose(fac.dinv[i].reshape(3, 3) @ U[3 * i:3 * i + 3, 3 * i:3 * i + 3],
+                                   np.eye(3), atol=1e-12)
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.chain_system(40), lambda: synth.tree_system(60, 3),
+                                   lambda: synth.block_diagonal_system(25, 4)])
+def test_no_fill_patterns_exact_and_one_iteration(maker):
+    s = maker()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    assert fac.status == 0
+    L, U = dense_factors(s, fac)
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    np.testing.assert_allclose(L @ U, A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    b = rhs(s)
+    z = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, b)
+    xd, st = O.dense_solve(A, b)
+    assert st == 0
+    np.testing.assert_allclose(z, xd, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(xd, s.x_true, rtol=1e-10, atol=1e-11)
+    res = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-10, maxit=50)
+    assert res.status == 0 and res.iters == 1
+    assert res.relres < 1e-13
+    np.testing.assert_allclose(res.x, s.x_true, rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("maker", [synth.config1, lambda: synth.random_pattern_system(60, 4, 21, dense=False)])
+def test_ilu0_defining_identity_on_pattern(maker):
+    s = maker()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    assert fac.status == 0
+    L, U = dense_factors(s, fac)
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    LU = L @ U
+    scale = np.abs(A).max()
+    mask = np.zeros((s.nb, s.nb), dtype=bool)
+    for i in range(s.nb):
+        mask[i, s.colidx[s.rowptr[i]:s.rowptr[i + 1]]] = True
+    big = np.kron(mask, np.ones((3, 3), dtype=bool))
+    err_on = np.abs(LU - A)[big].max() / scale
+    assert err_on < 1e-13
+    # and it is an *incomplete* factorisation: fill outside the pattern is dropped
+    assert np.abs(LU - A)[~big].max() / scale > 1e-6
+
+
+def test_ilu_apply_solves_lu_system():
+    s = synth.config1()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    L, U = dense_factors(s, fac)
+    r = synth.uniform(synth.stream_key(3, 3), np.arange(3 * s.nb, dtype=np.uint64), -1, 1)
+    z = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, r)
+    assert np.linalg.norm(L @ (U @ z) - r) / np.linalg.norm(r) < 1e-13
+
+
+def test_ilu0_flags_singular_pivot_row():
+    s = synth.block_diagonal_system(4, 9)
+    vals = s.vals.copy()
+    vals[2] = np.array([1.0, 2, 3, 2, 4, 6, 0, 0, 1])  # rank-2 diagonal block at row 2
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, vals)
+    assert fac.status == -(1 + 2)
+
+
+def test_ilu0_f32_close_to_f64():
+    s = synth.config1()
+    f64 = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    f32 = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, f32=True)
+    assert f32.status == 0 and f32.lu.dtype == np.float32
+    rel = np.abs(f32.lu - f64.lu).max() / np.abs(f64.lu).max()
+    assert 0 < rel < 1e-5
+
+
+# ---------------------------------------------------------------- BiCGStab
+
+def test_bicgstab_converges_to_x_true_at_tight_tolerance():
+    s = synth.config1()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    res = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-12, maxit=200)
+    assert res.status == 0
+    assert res.relres <= 1e-12 * (1 + 1e-6) * 10  # true residual near the recurrence bound
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    kappa = np.linalg.cond(A)
+    err = np.linalg.norm(res.x - s.x_true) / np.linalg.norm(s.x_true)
+    assert err <= kappa * 1e-11
+
+
+@pytest.mark.parametrize("rtol", [1e-2, 1e-4, 1e-8])
+def test_bicgstab_stopping_rule(rtol):
+    s = synth.config1()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    res = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=rtol, maxit=200)
+    assert res.status == 0
+    h = res.res_hist / res.res_hist[0]
+    k = res.iters
+    last = h[2 * k - 1] if np.isnan(h[2 * k]) else h[2 * k]
+    assert last <= rtol
+    # no earlier half or full step met the rule
+    assert np.all(h[1:2 * k - 1][~np.isnan(h[1:2 * k - 1])] > rtol)
+    assert res.relres <= rtol * (1 + 1e-6)
+
+
+def test_bicgstab_scaling_and_zero_rhs():
+    s = synth.config1()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    r1 = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-6)
+    r2 = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, 4.0 * b, rtol=1e-6)
+    assert r1.iters == r2.iters
+    np.testing.assert_allclose(r2.x, 4.0 * r1.x, rtol=1e-12, atol=1e-14)
+    r0 = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, np.zeros_like(b))
+    assert r0.status == 0 and r0.iters == 0 and r0.relres == 0.0
+    assert np.all(r0.x == 0.0)
+
+
+def test_bicgstab_maxit_and_nonfinite():
+    s = synth.config1()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    r = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-14, maxit=1)
+    assert r.status == 1 and r.iters == 1
+    b2 = b.copy()
+    b2[5] = np.nan
+    r = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b2)
+    assert r.status == -6
+
+
+def test_bicgstab_matches_dense_solution_on_config2_subset():
+    s = synth.random_pattern_system(80, 3, 77)
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    res = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-13, maxit=200)
+    xd, _ = O.dense_solve(O.to_dense(s.nb, s.rowptr, s.colidx, s.vals), b)
+    np.testing.assert_allclose(res.x, xd, rtol=1e-9, atol=1e-10)
+
+
+def test_f32_preconditioner_reaches_the_same_residual():
+    s = synth.config1()
+    b = rhs(s)
+    f32 = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, f32=True)
+    f64 = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    r32 = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, f32, b, rtol=1e-10)
+    r64 = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, f64, b, rtol=1e-10)
+    assert r32.status == 0 and r32.relres <= 1e-10 * (1 + 1e-6)
+    np.testing.assert_allclose(r32.x, r64.x, rtol=1e-8, atol=1e-9)
+
+
+# ---------------------------------------------------------------- schedules
+
+def grid_pattern(nx, ny, nz):
+    s = synth.grid_system(nx, ny, nz, np.zeros((nz, ny, nx)))
+    return s
+
+
+def test_levels_closed_form_on_full_grid():
+    nx, ny, nz = 6, 5, 4
+    s = grid_pattern(nx, ny, nz)
+    lev, n = O.levels(s.nb, s.rowptr, s.colidx)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    np.testing.assert_array_equal(lev, (i + j + k).ravel())
+    assert n == nx + ny + nz - 2
+
+
+def test_colours_closed_form_on_full_grid():
+    nx, ny, nz = 7, 4, 3
+    s = grid_pattern(nx, ny, nz)
+    col, n = O.colours(s.nb, s.rowptr, s.colidx)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    np.testing.assert_array_equal(col, ((i + j + k) % 2).ravel())
+    assert n == 2
+
+
+def _edges(s):
+    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
+    off = rows != s.colidx
+    return rows[off], s.colidx[off]
+
+
+@pytest.mark.parametrize("maker", [synth.config2, lambda: synth.random_pattern_system(300, 3, 5)])
+def test_schedule_sets_are_independent_and_minimal(maker):
+    s = maker()
+    a, b = _edges(s)
+    lev, nl = O.levels(s.nb, s.rowptr, s.colidx)
+    col, nc = O.colours(s.nb, s.rowptr, s.colidx)
+    assert np.all(lev[a] != lev[b]) and np.all(col[a] != col[b])
+    # brute-force definitions on the symmetrised graph
+    nbrs = [set() for _ in range(s.nb)]
+    for x, y in zip(a.tolist(), b.tolist()):
+        nbrs[x].add(y)
+        nbrs[y].add(x)
+    for i in range(s.nb):
+        earlier = [j for j in nbrs[i] if j < i]
+        assert lev[i] == (1 + max(lev[j] for j in earlier) if earlier else 0)
+        used = {int(col[j]) for j in earlier}
+        c = 0
+        while c in used:
+            c += 1
+        assert col[i] == c
+    assert nl == lev.max() + 1 and nc == col.max() + 1
+
+
+def test_order_by_key_is_stable_and_complete():
+    key = np.array([2, 0, 1, 0, 2, 1, 0])
+    perm = O.order_by_key(key, 3)
+    np.testing.assert_array_equal(perm, [1, 3, 6, 2, 5, 0, 4])
+
+
+def test_level_order_gives_the_natural_factors():
+    s = synth.config2()
+    nat = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, "level")
+    prow, pcol, pval = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    lev = O.ilu0(s.nb, prow, pcol, pval)
+    assert nat.status == 0 and lev.status == 0
+    # block (i', j') of the permuted factors is block (perm[i'], perm[j']) of the natural ones
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(s.nb)
+    for ip in range(0, s.nb, 97):
+        i = perm[ip]
+        for m in range(prow[ip], prow[ip + 1]):
+            j = perm[pcol[m]]
+            mn = s.rowptr[i] + np.searchsorted(s.colidx[s.rowptr[i]:s.rowptr[i + 1]], j)
+            np.testing.assert_allclose(lev.lu[m], nat.lu[mn], rtol=1e-12,
+                                       atol=1e-13 * np.abs(nat.lu[mn]).max())
+    np.testing.assert_allclose(lev.dinv, nat.dinv[perm], rtol=1e-12, atol=1e-14)
+
+
+def test_colour_order_changes_the_preconditioner_but_still_solves():
+    s = synth.config2()
+    b = rhs(s)
+    x_nat, r_nat, _, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-6, 200, "natural")
+    x_gc, r_gc, perm, nc = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-6, 200, "colour")
+    assert r_nat.status == 0 and r_gc.status == 0
+    assert r_gc.relres <= 1e-6 * (1 + 1e-6) and r_nat.relres <= 1e-6 * (1 + 1e-6)
+    assert nc >= 2
+    # the paper reports more iterations for colouring than for level scheduling
+    facts = paper_facts()
+    assert facts["gc_linear_iterations"] > facts["ls_linear_iterations"]
+    assert r_gc.iters >= r_nat.iters
+
+
+def test_permute_round_trip():
+    s = synth.random_pattern_system(50, 3, 8)
+    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, "colour")
+    prow, pcol, pval = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    PA = O.to_dense(s.nb, prow, pcol, pval)
+    P = np.kron(np.eye(s.nb)[perm], np.eye(3))
+    np.testing.assert_array_equal(PA, P @ A @ P.T)
+    assert all(np.all(np.diff(pcol[prow[i]:prow[i + 1]]) > 0) for i in range(s.nb))
+
+
+# ---------------------------------------------------------------- generator
+
+def test_generator_matches_paper_sizes_and_is_deterministic():
+    facts = paper_facts()
+    s2 = synth.config2()
+    assert s2.nb == int(facts["norne_active_cells"])
+    s1a, s1b = synth.config1(), synth.config1()
+    assert s1a.nb == 500 and s1a.nnzb == 3100
+    np.testing.assert_array_equal(s1a.vals, s1b.vals)
+    np.testing.assert_array_equal(s1a.x_true, s1b.x_true)
+    assert np.all(np.diff(s1a.rowptr) >= 1)
+
+
+def test_generator_rows_are_diagonally_dominant_up_to_noise():
+    s = synth.config1()
+    v = s.vals.reshape(-1, 3, 3)
+    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
+    diag = rows == s.colidx
+    off_sum = np.zeros((s.nb, 3))
+    for r in range(3):
+        off_sum[:, r] = np.bincount(rows[~diag], weights=np.abs(v[~diag, r, :]).sum(axis=1), minlength=s.nb)
+    d = v[diag]
+    for r in range(3):
+        assert np.all(d[:, r, r] >= off_sum[:, r] + 0.1 - 0.05)
