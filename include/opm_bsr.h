@@ -1,0 +1,200 @@
+/*
+ * opm_bsr.h -- C ABI of a GB300 (sm_103a) solver for 3x3 block-sparse
+ * (BSR) black-oil Jacobians: ILU0-preconditioned BiCGStab.
+ *
+ * The problem statement follows arXiv 2309.11488 ("An Evaluation and
+ * Comparison of GPU Hardware and Solver Libraries for Accelerating the OPM
+ * Flow Reservoir Simulator"):
+ *   - matrix format: block-CSR with 3x3 blocks stored contiguously and
+ *     row-major inside each block (Section 4.1 and the figure "Memory layout
+ *     of blocks in OPM", left panel; Section 4.3 on row-major Dune blocks);
+ *   - preconditioner: ILU0 without fill (Section 2.2, Algorithms 1 and 2);
+ *   - parallel schedule: level scheduling or graph colouring of the rows,
+ *     with the matrix reordered once (Section 4.4);
+ *   - solver: BiCGStab built from SpMV, axpy, dot and norm (Section 4.2),
+ *     stopping at a relative residual reduction rtol or after maxit
+ *     iterations, Dune's defaults being 1e-2 and 200 (Section 4.2);
+ *   - a solver failure is reported rather than handled (the paper falls back
+ *     to the CPU solver, Section 4.10; this library returns a status).
+ *
+ * Conventions for every entry point:
+ *   - nb = number of block rows (cells); vectors hold 3*nb doubles, the 3
+ *     unknowns of a cell contiguous, in the caller's (natural) row order.
+ *   - rowptr[nb+1] is 0-based and non-decreasing, colidx[nnzb] (nnzb =
+ *     rowptr[nb]) is strictly increasing inside every row, and every row holds
+ *     its diagonal block.  vals[9*nnzb] stores block m's entry (r, c) at
+ *     vals[9*m + 3*r + c].
+ *   - A pointer argument may be host memory or device memory of the current
+ *     device; the library tells them apart with cudaPointerGetAttributes.
+ *     It never keeps a caller pointer past the return of the call.
+ *   - Work is issued on the stream given in opm_options (NULL = the legacy
+ *     default stream) and every call has completed when it returns.
+ *   - No call traps, aborts or exits.  Device-side failures (a singular
+ *     pivot, a bounded wait that expired) are written to a status word in
+ *     device memory and returned as a negative opm_status.
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     distinct host threads.
+ */
+#ifndef OPM_BSR_H
+#define OPM_BSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct opm_solver *opm_handle; /* opaque, owned by the library */
+
+typedef enum {
+  OPM_OK = 0,
+  OPM_NOT_CONVERGED = 1,   /* maxit reached; x holds the last iterate          */
+  OPM_ERR_ARG = -1,        /* bad argument (NULL handle, nb < 0, bad option)   */
+  OPM_ERR_PATTERN = -2,    /* rowptr not monotone, colidx unsorted, duplicate
+                              or out of range                                  */
+  OPM_ERR_NO_DIAG = -3,    /* a row has no diagonal block                      */
+  OPM_ERR_ZERO_PIVOT = -4, /* singular 3x3 pivot in ILU0; opm_last_error_row  */
+  OPM_ERR_BREAKDOWN = -5,  /* BiCGStab breakdown: rho, (r^,v), (t,t) or omega
+                              exactly zero                                     */
+  OPM_ERR_NONFINITE = -6,  /* non-finite right-hand side                       */
+  OPM_ERR_OOM = -7,        /* device allocation failed                         */
+  OPM_ERR_TIMEOUT = -8,    /* a bounded device-side wait expired               */
+  OPM_ERR_CUDA = -9        /* a CUDA runtime call failed                       */
+} opm_status;
+
+/* Row order used for the parallel schedule (Section 4.4). */
+enum {
+  OPM_SCHED_AUTO = 0,    /* the library picks (currently: colouring)          */
+  OPM_SCHED_NATURAL = 1, /* caller's order; sequential dependency chains      */
+  OPM_SCHED_LEVEL = 2,   /* level scheduling: same factors as natural order   */
+  OPM_SCHED_COLOUR = 3   /* greedy graph colouring: a different ILU0          */
+};
+
+/* Storage precision of the ILU0 factors.  The Krylov recurrences, dots,
+ * norms, the SpMV with A and the final true residual are FP64 in both. */
+enum {
+  OPM_PREC_FP64 = 0,        /* factors and triangular solves in FP64          */
+  OPM_PREC_FP32_FACTORS = 1 /* factors stored and triangular solves run in
+                               FP32 with FP32 accumulation                    */
+};
+
+typedef struct opm_options {
+  int32_t schedule;      /* OPM_SCHED_*                                       */
+  int32_t precision;     /* OPM_PREC_*                                        */
+  void *stream;          /* cudaStream_t to issue work on; NULL = default     */
+  int32_t chunk;         /* BiCGStab iterations per graph launch between two
+                            reads of the device status word; 0 = default (8)  */
+  int32_t spin_limit_us; /* bound of every device-side wait in microseconds;
+                            0 = default (2,000,000)                           */
+  int32_t debug_skip_item; /* test hook, -1 = off: the sweep item with this
+                            index is never signalled, so waits on it expire
+                            after spin_limit_us (OPM_ERR_TIMEOUT)            */
+  int32_t reserved[7];
+} opm_options;
+
+/* Fill *opt with the defaults (AUTO schedule, FP64, default stream). */
+void opm_options_default(opm_options *opt);
+
+/*
+ * Symbolic analysis and first factorisation.  Validates the pattern
+ * (Section 4.1: the bridge flattens the BCRS pattern; the diagonal check of
+ * the paper's per-solve table moves here), computes the level or colour
+ * schedule and the row permutation (Section 4.4), builds the library's
+ * permuted device copy of the matrix and factorises it (Algorithm 2).
+ *   nb >= 0; rowptr, colidx, vals as above (host or device); opt may be NULL.
+ *   On success *out receives a new handle.  On OPM_ERR_ZERO_PIVOT *out still
+ *   receives the handle (its factors invalid) so that opm_last_error_row can
+ *   be read and opm_ilu0_factor retried with other values; the caller
+ *   destroys it.  On any other failure *out = NULL and, for pattern errors,
+ *   opm_last_error_row(NULL) returns the offending row for this host thread.
+ * Returns OPM_OK, OPM_ERR_ARG, OPM_ERR_PATTERN, OPM_ERR_NO_DIAG,
+ * OPM_ERR_ZERO_PIVOT, OPM_ERR_OOM, OPM_ERR_TIMEOUT or OPM_ERR_CUDA.
+ */
+opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
+                          const double *vals, const opm_options *opt, opm_handle *out);
+
+/*
+ * ILU0 refactorisation in place (Algorithm 2) with the analysis kept
+ * (Section 4.4: the pattern, hence the schedule, does not change during a
+ * simulation).  vals (host or device, 9*nnzb doubles, the caller's block
+ * order) replaces the matrix values; vals = NULL refactors the values the
+ * handle already holds.  The SpMV in later solves uses the new values.
+ * Returns OPM_OK, OPM_ERR_ARG, OPM_ERR_ZERO_PIVOT (row in
+ * opm_last_error_row, caller's numbering), OPM_ERR_TIMEOUT or OPM_ERR_CUDA.
+ */
+opm_status opm_ilu0_factor(opm_handle h, const double *vals);
+
+/*
+ * Solve A x = b by BiCGStab right-preconditioned with the current ILU0
+ * factors (Section 4.2), x0 = 0, shadow residual r^ = b.  Stops when
+ * ||r_k||_2 <= rtol * ||b||_2, tested after each half step, or after maxit
+ * iterations.  b, x: 3*nb doubles, host or device, caller's order; x is
+ * output only.  *iters (may be NULL) = iterations begun, a half-step exit
+ * counting as its iteration; *relres (may be NULL) = true
+ * ||b - A x||_2 / ||b||_2 computed in FP64 after the solve.  b = 0 gives
+ * x = 0, iters = 0, relres = 0 and OPM_OK.
+ * Returns OPM_OK, OPM_NOT_CONVERGED (x = last iterate), OPM_ERR_BREAKDOWN,
+ * OPM_ERR_NONFINITE, OPM_ERR_TIMEOUT, OPM_ERR_ARG or OPM_ERR_CUDA; on a
+ * negative status x is zero-filled.
+ */
+opm_status opm_bicgstab_solve(opm_handle h, const double *b, double *x, double rtol,
+                              int32_t maxit, int32_t *iters, double *relres);
+
+/* y = A x with the handle's current values (Section 4.3); x, y host or
+ * device, 3*nb doubles, caller's order. */
+opm_status opm_spmv(opm_handle h, const double *x, double *y);
+
+/* z = U^-1 L^-1 r with the current factors (Algorithm 1, equations 3-4);
+ * r, z host or device, 3*nb doubles, caller's order. */
+opm_status opm_ilu_apply(opm_handle h, const double *r, double *z);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void opm_destroy(opm_handle h);
+
+/* Static text of a status code. */
+const char *opm_status_str(opm_status s);
+
+/* Row (caller's numbering) of the handle's last OPM_ERR_ZERO_PIVOT, or -1;
+ * with h = NULL, the row of this thread's last failed opm_bsr_create
+ * (OPM_ERR_PATTERN or OPM_ERR_NO_DIAG), or -1. */
+int32_t opm_last_error_row(opm_handle h);
+
+typedef struct opm_info {
+  int32_t nb;
+  int32_t schedule;    /* schedule in use (never OPM_SCHED_AUTO)            */
+  int32_t precision;
+  int32_t nsets;       /* number of levels or colours (1 for natural)       */
+  int64_t nnzb;
+  int64_t nnzb_lower;  /* strictly lower blocks of the permuted matrix      */
+  int64_t nnzb_upper;
+  int64_t device_bytes; /* device memory held by the handle                 */
+} opm_info;
+
+opm_status opm_get_info(opm_handle h, opm_info *info);
+
+/* perm[new] = old row (host array of nb int32): the schedule's order. */
+opm_status opm_get_permutation(opm_handle h, int32_t *perm);
+
+/*
+ * Copy the current factors out in the permuted matrix's CSR order: lu (host,
+ * 9*nnzb doubles) holds L's strictly-lower blocks (unit diagonal implied) and
+ * U's strictly-upper blocks in the pattern of P A P^T with columns
+ * ascending; the diagonal-block positions of lu receive inv(U_ii), which the
+ * library stores instead of U_ii.  dinv (host, 9*nb doubles, schedule order)
+ * also receives inv(U_ii).  FP32 factors are widened exactly.  Either pointer
+ * may be NULL.
+ */
+opm_status opm_get_factors(opm_handle h, double *lu, double *dinv);
+
+/* Cumulative device time, in milliseconds, of the last solve's phases
+ * measured with CUDA events (0 when not measured). */
+typedef struct opm_timing {
+  float setup_ms, iterate_ms, finish_ms, factor_ms;
+} opm_timing;
+opm_status opm_get_timing(opm_handle h, opm_timing *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPM_BSR_H */

@@ -1,0 +1,85 @@
+// Internal declarations of the GB300 BSR ILU0-BiCGStab library.
+//
+// Device data layout ("warp-sliced" block storage, used for A, L and U):
+//   Rows are in the schedule's order and grouped in slices of 32 consecutive
+//   rows, one slice per warp, one row per lane.  The blocks of a slice occupy
+//   the same block range as in CSR (rowptr[32s] .. rowptr[32s+32]) but are
+//   reordered "k-major": slab k holds the k-th block of every row of the slice
+//   that has more than k blocks, in lane order.  Inside slab k the 9 entries
+//   are stored entry-planar: entry e of the block of rank q is value
+//   9*base_k + e*cnt_k + q, where base_k is the slab's first block and cnt_k
+//   its number of blocks.  A warp walking slab k therefore reads every entry
+//   with one coalesced load, and the storage has no padding.  A lane finds
+//   cnt_k = popc(ballot(len > k)) and q = popc(ballot & lanemask_lt) itself,
+//   so only the CSR row pointer is needed to walk a row.
+//
+//   A "slot" packs the location of one block: (entry-0 value index << 6) |
+//   stride, with stride = cnt_k <= 32; entry e lives at off + e*stride.
+//
+//   The inverted diagonal blocks of U (Dinv) are stored per slice as 9 planes
+//   of 32 values: row i's entry e is value 288*(i/32) + 32*e + i%32.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/opm_bsr.h"
+
+namespace opm {
+
+constexpr int kWarp = 32;
+constexpr int kTileRows = 256;  // rows per CTA of the static-tiled kernels
+constexpr int kSliceVals = 288;  // 32 rows x 9 entries per Dinv slice
+constexpr int32_t kRunning = 0x7fffffff;
+
+inline int64_t slot_pack(int64_t off, int stride) { return (off << 6) | (int64_t)stride; }
+
+// Result of the host symbolic analysis of one pattern (Section 4.4).
+struct Analysis {
+  int32_t n = 0;
+  int64_t nnzb = 0, nnz_l = 0, nnz_u = 0;
+  int32_t schedule = 0, nsets = 0;
+  std::vector<int32_t> perm, iperm;           // perm[new] = old
+  std::vector<int32_t> a_rowptr, l_rowptr, u_rowptr;
+  std::vector<int32_t> a_col, l_col, u_col;   // warp-sliced order
+  std::vector<int32_t> a_src;                 // per A block (sliced order): caller's block index
+  std::vector<int64_t> a_dst;                 // per A block (sliced order): slot in the factor values
+  std::vector<int64_t> a_csr_slot;            // per A block in permuted CSR order: slot in the factor values
+  std::vector<int32_t> upd_ptr;               // per L block (CSR order of L) into the update lists
+  std::vector<int64_t> upd_dst, upd_src;      // slots: A_ij -= L_ik * U_kj
+  // sweep dependencies: per slice, the distinct other slices its rows read
+  // (forward: L's columns, backward: U's), and per row the lanes of its own
+  // slice it reads
+  std::vector<int32_t> fdep_ptr, fdep, bdep_ptr, bdep;
+  std::vector<uint32_t> fmask, bmask;
+  int64_t d_off = 0;                          // first value of Dinv inside the factor values
+  int64_t lu_vals = 0;                        // total factor values
+  int32_t max_row_len = 0;
+};
+
+// Validates and analyses the pattern; returns OPM_OK or a pattern error with
+// *err_row set to the offending row (caller's numbering).
+opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
+                   Analysis &an, int32_t *err_row);
+
+// Krylov scalars and control words, one per system, in device memory.
+struct DevState {
+  double rho, rho_prev, alpha, omega, beta;
+  double n0, tol;
+  double rhv, ss, ts, tt, rr, rhr;
+  double relres;
+  int32_t status;  // kRunning or an opm_status
+  int32_t k;       // current iteration, 1-based
+  int32_t iters;
+  int32_t maxit;
+  int32_t half;    // the last half step met the stopping rule
+  int32_t error;   // device-detected error (opm_status) or 0
+  int32_t err_row; // smallest permuted row with a singular pivot
+  uint32_t done, epoch;          // sweep kernels: CTAs finished, launch epoch
+  uint32_t red_count;            // last-CTA reduction counter
+  int32_t pad[3];
+};
+
+}  // namespace opm

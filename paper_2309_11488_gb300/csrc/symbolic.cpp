@@ -1,0 +1,299 @@
+// Host symbolic analysis: pattern validation, level or colour schedule, the
+// row permutation, the warp-sliced layouts of A, L and U and the ILU0 update
+// lists.  Runs once per sparsity pattern; the paper reuses its analysis for
+// the whole simulation because the pattern never changes (Section 4.4).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <utility>
+
+#include "opm_internal.h"
+
+namespace opm {
+namespace {
+
+// Edge list of the symmetrised pattern (i-j whenever block (i,j) or (j,i)
+// exists, i != j), as CSR.
+void symmetrise(int32_t n, const int32_t *rowptr, const int32_t *colidx, std::vector<int64_t> &gp,
+                std::vector<int32_t> &ga) {
+  gp.assign((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j != i) {
+        gp[i + 1]++;
+        gp[j + 1]++;
+      }
+    }
+  for (int32_t i = 0; i < n; ++i) gp[i + 1] += gp[i];
+  ga.resize((size_t)gp[n]);
+  std::vector<int64_t> fill(gp.begin(), gp.end() - 1);
+  for (int32_t i = 0; i < n; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j != i) {
+        ga[fill[i]++] = j;
+        ga[fill[j]++] = i;
+      }
+    }
+}
+
+// Level of a row: 0 without an earlier neighbour, else one more than the
+// deepest earlier neighbour.  Rows of equal level share no edge.
+int32_t level_sets(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                   std::vector<int32_t> &key) {
+  key.assign(n, 0);
+  int32_t nsets = n > 0 ? 1 : 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int64_t m = gp[i]; m < gp[i + 1]; ++m) {
+      int32_t j = ga[m];
+      if (j < i) l = std::max(l, key[j] + 1);
+    }
+    key[i] = l;
+    nsets = std::max(nsets, l + 1);
+  }
+  return nsets;
+}
+
+// Greedy first-fit colouring in natural order: each row takes the smallest
+// colour that no earlier neighbour holds.
+int32_t colour_sets(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                    std::vector<int32_t> &key) {
+  key.assign(n, -1);
+  std::vector<int32_t> stamp;
+  int32_t nsets = n > 0 ? 1 : 0;
+  for (int32_t i = 0; i < n; ++i) {
+    for (int64_t m = gp[i]; m < gp[i + 1]; ++m) {
+      int32_t c = key[ga[m]];
+      if (c >= 0) {
+        if ((size_t)c >= stamp.size()) stamp.resize((size_t)c + 1, -1);
+        stamp[c] = i;
+      }
+    }
+    int32_t c = 0;
+    while ((size_t)c < stamp.size() && stamp[c] == i) ++c;
+    key[i] = c;
+    nsets = std::max(nsets, c + 1);
+  }
+  return nsets;
+}
+
+// Warp-sliced order of a CSR part: fills pos[csr block] = sliced block index
+// and slot[csr block] = packed value location.
+void slice_layout(int32_t n, const std::vector<int32_t> &rp, std::vector<int64_t> &pos,
+                  std::vector<int64_t> &slot, int64_t val_base) {
+  int64_t nnz = rp[n];
+  pos.assign((size_t)nnz, 0);
+  slot.assign((size_t)nnz, 0);
+  for (int32_t r0 = 0; r0 < n; r0 += kWarp) {
+    int32_t r1 = std::min(n, r0 + kWarp);
+    int32_t maxlen = 0;
+    for (int32_t i = r0; i < r1; ++i) maxlen = std::max(maxlen, rp[i + 1] - rp[i]);
+    int64_t base = rp[r0];
+    for (int32_t k = 0; k < maxlen; ++k) {
+      int32_t cnt = 0;
+      for (int32_t i = r0; i < r1; ++i)
+        if (rp[i + 1] - rp[i] > k) ++cnt;
+      int32_t q = 0;
+      for (int32_t i = r0; i < r1; ++i)
+        if (rp[i + 1] - rp[i] > k) {
+          int64_t c = rp[i] + k;
+          pos[c] = base + q;
+          slot[c] = slot_pack(val_base + 9 * base + q, cnt);
+          ++q;
+        }
+      base += cnt;
+    }
+  }
+}
+
+}  // namespace
+
+opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
+                   Analysis &an, int32_t *err_row) {
+  *err_row = -1;
+  if (n < 0) return OPM_ERR_ARG;
+  if (rowptr[0] != 0) {
+    *err_row = 0;
+    return OPM_ERR_PATTERN;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) {
+      *err_row = i;
+      return OPM_ERR_PATTERN;
+    }
+  }
+  const int64_t nnzb = rowptr[n];
+  if (9 * (nnzb + (int64_t)n + kWarp) >= ((int64_t)1 << 31)) return OPM_ERR_ARG;  // int32 value offsets
+  for (int32_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (j < 0 || j >= n || (m > rowptr[i] && colidx[m - 1] >= j)) {
+        *err_row = i;
+        return OPM_ERR_PATTERN;
+      }
+      diag |= (j == i);
+    }
+    if (!diag) {
+      *err_row = i;
+      return OPM_ERR_NO_DIAG;
+    }
+  }
+
+  an = Analysis();
+  an.n = n;
+  an.nnzb = nnzb;
+  if (schedule == OPM_SCHED_AUTO) schedule = OPM_SCHED_COLOUR;
+  an.schedule = schedule;
+
+  // ---- schedule and permutation (perm[new] = old, stable inside a set)
+  std::vector<int32_t> key;
+  if (schedule == OPM_SCHED_NATURAL) {
+    key.assign(n, 0);
+    an.nsets = n > 0 ? 1 : 0;
+  } else {
+    std::vector<int64_t> gp;
+    std::vector<int32_t> ga;
+    symmetrise(n, rowptr, colidx, gp, ga);
+    an.nsets = schedule == OPM_SCHED_LEVEL ? level_sets(n, gp, ga, key) : colour_sets(n, gp, ga, key);
+  }
+  std::vector<int64_t> count((size_t)an.nsets + 1, 0);
+  for (int32_t i = 0; i < n; ++i) count[key[i] + 1]++;
+  for (int32_t s = 0; s < an.nsets; ++s) count[s + 1] += count[s];
+  an.perm.resize(n);
+  an.iperm.resize(n);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t ni = (int32_t)count[key[i]]++;
+    an.perm[ni] = i;
+    an.iperm[i] = ni;
+  }
+
+  // ---- permuted CSR with sorted columns and the caller's block index
+  std::vector<int32_t> &arp = an.a_rowptr;
+  arp.assign((size_t)n + 1, 0);
+  for (int32_t ni = 0; ni < n; ++ni) arp[ni + 1] = arp[ni] + (rowptr[an.perm[ni] + 1] - rowptr[an.perm[ni]]);
+  std::vector<int32_t> pcol((size_t)nnzb), psrc((size_t)nnzb);
+  std::vector<std::pair<int32_t, int32_t>> tmp;
+  an.l_rowptr.assign((size_t)n + 1, 0);
+  an.u_rowptr.assign((size_t)n + 1, 0);
+  for (int32_t ni = 0; ni < n; ++ni) {
+    int32_t oi = an.perm[ni];
+    tmp.clear();
+    for (int64_t m = rowptr[oi]; m < rowptr[oi + 1]; ++m) tmp.emplace_back(an.iperm[colidx[m]], (int32_t)m);
+    std::sort(tmp.begin(), tmp.end());
+    int32_t nl = 0, nu = 0;
+    for (size_t q = 0; q < tmp.size(); ++q) {
+      pcol[arp[ni] + q] = tmp[q].first;
+      psrc[arp[ni] + q] = tmp[q].second;
+      nl += tmp[q].first < ni;
+      nu += tmp[q].first > ni;
+    }
+    an.l_rowptr[ni + 1] = an.l_rowptr[ni] + nl;
+    an.u_rowptr[ni + 1] = an.u_rowptr[ni] + nu;
+    an.max_row_len = std::max<int32_t>(an.max_row_len, (int32_t)tmp.size());
+  }
+  an.nnz_l = an.l_rowptr[n];
+  an.nnz_u = an.u_rowptr[n];
+
+  // ---- warp-sliced layouts.  Factor values: [L | U | Dinv slices].
+  std::vector<int64_t> a_pos, a_slot, l_pos, l_slot, u_pos, u_slot;
+  slice_layout(n, arp, a_pos, a_slot, 0);
+  slice_layout(n, an.l_rowptr, l_pos, l_slot, 0);
+  slice_layout(n, an.u_rowptr, u_pos, u_slot, 9 * an.nnz_l);
+  an.d_off = 9 * (an.nnz_l + an.nnz_u);
+  const int64_t nslices = ((int64_t)n + kWarp - 1) / kWarp;
+  an.lu_vals = an.d_off + kSliceVals * nslices;
+  auto d_slot = [&](int32_t i) { return slot_pack(an.d_off + kSliceVals * (i / kWarp) + (i % kWarp), kWarp); };
+
+  an.a_col.assign((size_t)nnzb, 0);
+  an.a_src.assign((size_t)nnzb, 0);
+  an.a_dst.assign((size_t)nnzb, 0);
+  an.a_csr_slot.assign((size_t)nnzb, 0);
+  an.l_col.assign((size_t)an.nnz_l, 0);
+  an.u_col.assign((size_t)an.nnz_u, 0);
+  for (int32_t ni = 0; ni < n; ++ni) {
+    int64_t lc = an.l_rowptr[ni], uc = an.u_rowptr[ni];
+    for (int64_t c = arp[ni]; c < arp[ni + 1]; ++c) {
+      int32_t j = pcol[c];
+      int64_t dst;
+      if (j < ni) {
+        an.l_col[l_pos[lc]] = j;
+        dst = l_slot[lc++];
+      } else if (j > ni) {
+        an.u_col[u_pos[uc]] = j;
+        dst = u_slot[uc++];
+      } else {
+        dst = d_slot(ni);
+      }
+      an.a_col[a_pos[c]] = j;
+      an.a_src[a_pos[c]] = psrc[c];
+      an.a_dst[a_pos[c]] = dst;
+      an.a_csr_slot[c] = dst;
+    }
+  }
+
+  // ---- sweep dependencies per slice and per row
+  auto sweep_deps = [&](bool lower, std::vector<int32_t> &ptr,
+                        std::vector<int32_t> &dep, std::vector<uint32_t> &mask) {
+    const int32_t ns = (n + kWarp - 1) / kWarp;
+    ptr.assign((size_t)ns + 1, 0);
+    dep.clear();
+    mask.assign((size_t)n, 0u);
+    std::vector<int32_t> tmpd;
+    for (int32_t sl = 0; sl < ns; ++sl) {
+      const int32_t r0 = sl * kWarp, r1 = std::min(n, r0 + kWarp);
+      tmpd.clear();
+      for (int32_t i = r0; i < r1; ++i)
+        for (int64_t c = arp[i]; c < arp[i + 1]; ++c) {
+          const int32_t j = pcol[c];
+          if (lower ? !(j < i) : !(j > i)) continue;
+          if (j >= r0 && j < r1) mask[i] |= 1u << (j - r0);
+          else tmpd.push_back(j / kWarp);
+        }
+      std::sort(tmpd.begin(), tmpd.end());
+      tmpd.erase(std::unique(tmpd.begin(), tmpd.end()), tmpd.end());
+      dep.insert(dep.end(), tmpd.begin(), tmpd.end());
+      ptr[sl + 1] = (int32_t)dep.size();
+    }
+  };
+  sweep_deps(true, an.fdep_ptr, an.fdep, an.fmask);
+  sweep_deps(false, an.bdep_ptr, an.bdep, an.bmask);
+
+  // ---- ILU0 update lists: for L block (i,k), every j > k present in row i
+  // and in row k gives A_ij -= L_ik * U_kj (Algorithm 2's inner loop).
+  an.upd_ptr.assign((size_t)an.nnz_l + 1, 0);
+  an.upd_dst.clear();
+  an.upd_src.clear();
+  for (int32_t ni = 0; ni < n; ++ni) {
+    int64_t lc = an.l_rowptr[ni];
+    for (int64_t c = arp[ni]; c < arp[ni + 1] && pcol[c] < ni; ++c, ++lc) {
+      int32_t k = pcol[c];
+      // row k's upper blocks, permuted CSR positions
+      int64_t ku = an.u_rowptr[k];
+      int64_t kc = arp[k];
+      while (kc < arp[k + 1] && pcol[kc] <= k) ++kc;  // first upper block of row k
+      int64_t ic = c + 1;
+      while (ic < arp[ni + 1] && kc < arp[k + 1]) {
+        if (pcol[ic] < pcol[kc]) {
+          ++ic;
+        } else if (pcol[ic] > pcol[kc]) {
+          ++kc;
+          ++ku;
+        } else {
+          an.upd_dst.push_back(an.a_csr_slot[ic]);
+          an.upd_src.push_back(u_slot[ku]);
+          ++ic;
+          ++kc;
+          ++ku;
+        }
+      }
+      an.upd_ptr[lc + 1] = (int32_t)an.upd_dst.size();
+    }
+  }
+  if (an.upd_dst.size() >= ((size_t)1 << 31)) return OPM_ERR_ARG;
+  return OPM_OK;
+}
+
+}  // namespace opm

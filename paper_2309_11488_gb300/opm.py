@@ -1,0 +1,287 @@
+"""Thin Python binding of ``libopm_bsr.so`` (C ABI in ``include/opm_bsr.h``).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Functions keep the C names (``opm_bsr_create``,
+``opm_ilu0_factor``, ``opm_bicgstab_solve`` ...).  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); PyTorch supplies device memory
+and streams only.  If the compiled library is missing, loading raises
+``ImportError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libopm_bsr.so")
+
+OPM_OK = 0
+OPM_NOT_CONVERGED = 1
+OPM_ERR_ARG = -1
+OPM_ERR_PATTERN = -2
+OPM_ERR_NO_DIAG = -3
+OPM_ERR_ZERO_PIVOT = -4
+OPM_ERR_BREAKDOWN = -5
+OPM_ERR_NONFINITE = -6
+OPM_ERR_OOM = -7
+OPM_ERR_TIMEOUT = -8
+OPM_ERR_CUDA = -9
+
+SCHEDULES = {"auto": 0, "natural": 1, "level": 2, "colour": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+# every symbol include/opm_bsr.h declares
+EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicgstab_solve",
+           "opm_spmv", "opm_ilu_apply", "opm_destroy", "opm_status_str", "opm_last_error_row",
+           "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing"]
+
+
+class opm_options(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("precision", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("chunk", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
+                ("debug_skip_item", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class opm_info(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int32), ("schedule", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nsets", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
+                ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class opm_timing(ctypes.Structure):
+    _fields_ = [("setup_ms", ctypes.c_float), ("iterate_ms", ctypes.c_float),
+                ("finish_ms", ctypes.c_float), ("factor_ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the compiled library; raise ImportError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2309_11488_gb300/build.py (no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.opm_options_default.argtypes = [ctypes.POINTER(opm_options)]
+        L.opm_options_default.restype = None
+        L.opm_bsr_create.argtypes = [i32, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
+        L.opm_bsr_create.restype = i32
+        L.opm_ilu0_factor.argtypes = [vp, vp]
+        L.opm_ilu0_factor.restype = i32
+        L.opm_bicgstab_solve.argtypes = [vp, vp, vp, f64, i32, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+        L.opm_bicgstab_solve.restype = i32
+        L.opm_spmv.argtypes = [vp, vp, vp]
+        L.opm_spmv.restype = i32
+        L.opm_ilu_apply.argtypes = [vp, vp, vp]
+        L.opm_ilu_apply.restype = i32
+        L.opm_destroy.argtypes = [vp]
+        L.opm_destroy.restype = None
+        L.opm_status_str.argtypes = [i32]
+        L.opm_status_str.restype = ctypes.c_char_p
+        L.opm_last_error_row.argtypes = [vp]
+        L.opm_last_error_row.restype = i32
+        L.opm_get_info.argtypes = [vp, ctypes.POINTER(opm_info)]
+        L.opm_get_info.restype = i32
+        L.opm_get_permutation.argtypes = [vp, vp]
+        L.opm_get_permutation.restype = i32
+        L.opm_get_factors.argtypes = [vp, vp, vp]
+        L.opm_get_factors.restype = i32
+        L.opm_get_timing.argtypes = [vp, ctypes.POINTER(opm_timing)]
+        L.opm_get_timing.restype = i32
+        _lib = L
+    return _lib
+
+
+class OpmError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {opm_status_str(status)} ({status})")
+
+
+def opm_status_str(status: int) -> str:
+    return lib().opm_status_str(status).decode()
+
+
+def _ptr(a, dtype):
+    """Address of a contiguous numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    # torch tensor
+    import torch
+    want = {np.float64: torch.float64, np.int32: torch.int32}[np.dtype(dtype).type]
+    if a.dtype != want or not a.is_contiguous():
+        raise TypeError(f"expected a contiguous {want} tensor")
+    return a.data_ptr()
+
+
+@dataclass
+class Handle:
+    ptr: int
+    nb: int
+    nnzb: int
+
+    def __bool__(self):
+        return bool(self.ptr)
+
+
+def opm_options_default(**kw) -> opm_options:
+    o = opm_options()
+    lib().opm_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "schedule" and isinstance(v, str):
+            v = SCHEDULES[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def opm_bsr_create(nb, rowptr, colidx, vals, options: opm_options | None = None, check=True):
+    """Returns (status, Handle or None)."""
+    out = ctypes.c_void_p()
+    st = lib().opm_bsr_create(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32), _ptr(vals, np.float64),
+                              ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    nnzb = int(rowptr[-1]) if nb >= 0 and len(rowptr) else 0
+    h = Handle(out.value or 0, int(nb), nnzb) if out.value else None
+    if check and st != OPM_OK:
+        if h:
+            opm_destroy(h)
+        raise OpmError(st, "opm_bsr_create")
+    return st, h
+
+
+def opm_ilu0_factor(h: Handle, vals=None) -> int:
+    return lib().opm_ilu0_factor(h.ptr, _ptr(vals, np.float64))
+
+
+def opm_bicgstab_solve(h: Handle, b, x, rtol=1e-2, maxit=200):
+    """Returns (status, iters, relres); x is filled in place."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().opm_bicgstab_solve(h.ptr, _ptr(b, np.float64), _ptr(x, np.float64), float(rtol), int(maxit),
+                                  ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def opm_spmv(h: Handle, x, y) -> int:
+    return lib().opm_spmv(h.ptr, _ptr(x, np.float64), _ptr(y, np.float64))
+
+
+def opm_ilu_apply(h: Handle, r, z) -> int:
+    return lib().opm_ilu_apply(h.ptr, _ptr(r, np.float64), _ptr(z, np.float64))
+
+
+def opm_destroy(h: Handle | None) -> None:
+    if h and h.ptr:
+        lib().opm_destroy(h.ptr)
+        h.ptr = 0
+
+
+def opm_last_error_row(h: Handle | None) -> int:
+    return lib().opm_last_error_row(h.ptr if h else None)
+
+
+def opm_get_info(h: Handle) -> opm_info:
+    info = opm_info()
+    st = lib().opm_get_info(h.ptr, ctypes.byref(info))
+    if st != OPM_OK:
+        raise OpmError(st, "opm_get_info")
+    return info
+
+
+def opm_get_permutation(h: Handle) -> np.ndarray:
+    perm = np.empty(h.nb, dtype=np.int32)
+    st = lib().opm_get_permutation(h.ptr, perm.ctypes.data if h.nb else None)
+    if st != OPM_OK:
+        raise OpmError(st, "opm_get_permutation")
+    return perm
+
+
+def opm_get_factors(h: Handle):
+    """(lu (nnzb, 9), dinv (nb, 9)) in the schedule's CSR order."""
+    lu = np.empty((h.nnzb, 9))
+    dinv = np.empty((h.nb, 9))
+    st = lib().opm_get_factors(h.ptr, lu.ctypes.data, dinv.ctypes.data)
+    if st != OPM_OK:
+        raise OpmError(st, "opm_get_factors")
+    return lu, dinv
+
+
+def opm_get_timing(h: Handle) -> opm_timing:
+    t = opm_timing()
+    lib().opm_get_timing(h.ptr, ctypes.byref(t))
+    return t
+
+
+class Solver:
+    """Convenience owner of one handle (context manager)."""
+
+    def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
+                 spin_limit_us=0, debug_skip_item=-1):
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
+                                           spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item)
+        self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options)
+        self.nb = nb
+
+    def factor(self, vals=None) -> int:
+        return opm_ilu0_factor(self.h, vals)
+
+    def solve(self, b, x=None, rtol=1e-2, maxit=200):
+        if x is None:
+            x = np.empty(3 * self.nb) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+        st, it, rr = opm_bicgstab_solve(self.h, b, x, rtol, maxit)
+        return x, st, it, rr
+
+    def spmv(self, x, y=None):
+        if y is None:
+            y = np.empty(3 * self.nb) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        st = opm_spmv(self.h, x, y)
+        if st != OPM_OK:
+            raise OpmError(st, "opm_spmv")
+        return y
+
+    def ilu_apply(self, r, z=None):
+        if z is None:
+            z = np.empty(3 * self.nb) if isinstance(r, np.ndarray) else r.new_empty(r.shape)
+        st = opm_ilu_apply(self.h, r, z)
+        if st != OPM_OK:
+            raise OpmError(st, "opm_ilu_apply")
+        return z
+
+    def info(self):
+        return opm_get_info(self.h)
+
+    def permutation(self):
+        return opm_get_permutation(self.h)
+
+    def factors(self):
+        return opm_get_factors(self.h)
+
+    def timing(self):
+        return opm_get_timing(self.h)
+
+    def close(self):
+        opm_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

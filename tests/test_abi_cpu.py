@@ -1,0 +1,94 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects bad patterns on the host before touching CUDA."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2309_11488_gb300 import opm, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "opm_bsr.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(opm_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2309_11488_gb300 import build
+    build.build()
+
+
+def test_every_declared_symbol_is_exported():
+    syms = header_symbols()
+    assert "opm_bsr_create" in syms and "opm_bicgstab_solve" in syms and "opm_ilu0_factor" in syms
+    L = opm.lib()
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(opm.EXPORTS) == sorted(syms)
+
+
+def test_status_strings():
+    assert opm.opm_status_str(0) == "ok"
+    assert "singular" in opm.opm_status_str(opm.OPM_ERR_ZERO_PIVOT)
+    assert opm.opm_status_str(42) == "unknown status"
+
+
+def test_options_default():
+    o = opm.opm_options_default()
+    assert o.schedule == 0 and o.precision == 0 and o.debug_skip_item == -1 and o.chunk == 0
+
+
+def _create(nb, rp, ci, vals, **kw):
+    return opm.opm_bsr_create(nb, np.asarray(rp, np.int32), np.asarray(ci, np.int32),
+                              np.asarray(vals, np.float64), opm.opm_options_default(**kw), check=False)
+
+
+def test_pattern_errors_are_found_on_the_host():
+    s = synth.config1()
+    # unsorted columns in row 3
+    ci = s.colidx.copy()
+    a = s.rowptr[3]
+    ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    st, h = _create(s.nb, s.rowptr, ci, s.vals)
+    assert st == opm.OPM_ERR_PATTERN and h is None and opm.opm_last_error_row(None) == 3
+    # column out of range in row 10
+    ci = s.colidx.copy()
+    ci[s.rowptr[11] - 1] = s.nb
+    st, h = _create(s.nb, s.rowptr, ci, s.vals)
+    assert st == opm.OPM_ERR_PATTERN and opm.opm_last_error_row(None) == 10
+    # decreasing rowptr
+    rp = s.rowptr.copy()
+    rp[5] = rp[6] + 1
+    st, h = _create(s.nb, rp, s.colidx, s.vals)
+    assert st == opm.OPM_ERR_PATTERN
+    # a row without its diagonal: row 0 of a 2-row system holds only column 1
+    st, h = _create(2, [0, 1, 3], [1, 0, 1], np.ones(27))
+    assert st == opm.OPM_ERR_NO_DIAG and opm.opm_last_error_row(None) == 0
+    # duplicate column
+    st, h = _create(2, [0, 2, 3], [0, 0, 1], np.ones(27))
+    assert st == opm.OPM_ERR_PATTERN
+
+
+def test_bad_arguments():
+    s = synth.config1()
+    st, h = _create(-1, [0], [], [])
+    assert st == opm.OPM_ERR_ARG
+    st, h = _create(s.nb, s.rowptr, s.colidx, s.vals, schedule=9)
+    assert st == opm.OPM_ERR_ARG
+    st, h = _create(s.nb, s.rowptr, s.colidx, s.vals, precision=5)
+    assert st == opm.OPM_ERR_ARG
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2309_11488_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "oracle.c" not in txt and "liboracle" not in txt, f
