@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""ILU0-BiCGStab solves/s on the 1M-cell synthetic black-oil Jacobian (GB300).
+
+One step = one Newton-step linear solve as the paper's OPM Flow integration
+performs it: the new matrix values are permuted into the schedule order and
+factorised (ILU0), then BiCGStab runs to a relative residual reduction of
+1e-3 (the workload's rtol) and the true residual is computed.  The matrix is
+the seeded 100^3 grid with a 5% inactive mask and 1% fault connections
+(949,871 cells, 6.33M 3x3 blocks), b = A x_true formed on the GPU with the
+library's own SpMV.  Inputs (456 MB of values) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own replica (the single-system
+path does not shard); value = solves of all ranks / the slowest rank's time.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on the same system: the paper publishes no runnable code.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ILU0-BiCGStab solves/s & HBM roofline frac; FP32-ILU vs FP64; p50/p99 latency"
+UNIT = "solves/s"
+RTOL = 1e-3
+WORKLOAD = ("C3: 100^3 grid, 5% inactive cells, 1% fault connections, lognormal perm sigma=2; "
+            "949,871 cells, 6,328,435 3x3 blocks; per step: value permutation + ILU0 factorisation + "
+            "BiCGStab to rtol 1e-3 + true residual")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--schedule", default="auto")
+    p.add_argument("--grid", type=int, default=100, help="grid edge (100 = the 1M-cell workload)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # first sample before timing starts
+                time.sleep(0.02)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_apply_bytes(info, fp32: bool) -> int:
+    """Bytes one preconditioner application must move at least: every factor
+    block once (L, U and the inverted diagonal, 9 values each), L's and U's
+    column indices and row pointers, and the vectors: r, p, v read, p and z
+    written, the intermediate y written and read back."""
+    n, nnzb = info.nb, info.nnzb
+    val = 4 if fp32 else 8
+    factors = 9 * val * nnzb + 4 * (nnzb - n) + 2 * 4 * (n + 1)
+    vectors = 5 * 24 * n + 2 * 3 * val * n
+    return factors + vectors
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "solver.cu"):
+        with open(os.path.join(ROOT, "paper_2309_11488_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, precision: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{kernel}_{precision}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def make_system(grid):
+    from paper_2309_11488_gb300 import synth
+    return synth.config3(grid)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2309_11488_gb300 import opm
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s = make_system(args.grid)
+    rp, ci, vals = dev(s.rowptr), dev(s.colidx), dev(s.vals)
+    xt = dev(s.x_true)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def measure(precision):
+        sv = opm.Solver(s.nb, rp, ci, vals, schedule=args.schedule, precision=precision, profile_kernels=True)
+        b = sv.spmv(xt)  # b = A x_true on the GPU
+        x = torch.empty_like(b)
+        info = sv.info()
+        stat = {}
+
+        def step():
+            st = sv.factor(vals)
+            _, st2, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+            stat.update(st=st, st2=st2, iters=it, relres=rr)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        sv.reset_timing()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record()
+            for _ in range(args.steps):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        t = sv.timing()
+        err = float(np.linalg.norm(x.cpu().numpy() - s.x_true) / np.linalg.norm(s.x_true))
+        return sv, dict(ms=ms, timing=t, info=info, clocks=clk.summary(), err=err, **stat)
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        tt = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    sv64, r64 = measure("fp64")
+    sv32, r32 = measure("fp32")
+    ms64 = max_over_ranks(r64["ms"])
+    ms32 = max_over_ranks(r32["ms"])
+
+    # end to end through the C ABI from pinned host buffers: per step the
+    # values and b go host -> device and x comes back
+    vals_h = torch.from_numpy(np.ascontiguousarray(s.vals)).pin_memory()
+    b_h = sv64.spmv(xt).cpu().pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+
+    def e2e_step():
+        sv64.factor(vals_h)
+        sv64.solve(b_h, x_h, rtol=RTOL, maxit=200)
+
+    for _ in range(2):
+        e2e_step()
+    n_e2e = max(3, args.steps // 3)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+
+    def roofline(r, precision):
+        t = r["timing"]
+        ms, cnt = t.kernel_ms[1], t.kernel_count[1]
+        avg = ms / max(cnt, 1)
+        nbytes = algorithmic_apply_bytes(r["info"], precision == "fp32")
+        peak, src = peaks()
+        ach = nbytes / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        return {"kernel": f"k_apply<{'float' if precision == 'fp32' else 'double'}> (ILU0 forward+backward)",
+                "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": f"{src} (MEMORY copy, MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_launch": int(nbytes), "avg_launch_us": round(avg * 1e3, 2), "launches": int(cnt),
+                "traffic": measured_traffic("apply", precision)}
+
+    def kernels(r):
+        t = r["timing"]
+        return {k: {"ms_total": round(t.kernel_ms[q], 3), "launches": int(t.kernel_count[q]),
+                    "avg_us": round(1e3 * t.kernel_ms[q] / max(t.kernel_count[q], 1), 2)}
+                for q, k in enumerate(opm.KERNELS)}
+
+    out = {
+        "metric": METRIC,
+        "value": round(world * args.steps / (ms64 * 1e-3), 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": round(ms64 / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded generator shaped like the paper's 1M-cell model)",
+        "config": {"workload": WORKLOAD, "schedule": args.schedule, "nsets": r64["info"].nsets,
+                   "precision": "fp64 factors and Krylov", "rtol": RTOL, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (A values 456 MB, factors 456 MB)"},
+        "iters": r64["iters"], "relres": r64["relres"], "status": [r64["st"], r64["st2"]],
+        "x_err_vs_x_true": r64["err"],
+        "roofline": roofline(r64, "fp64"),
+        "e2e": {"value": round(world * n_e2e / e2e_s, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(s.vals.nbytes + 24 * s.nb), "d2h_bytes_per_step": int(24 * s.nb)},
+        "gpu_launches": int(r64["timing"].launches),
+        "clocks": r64["clocks"],
+        "kernels": kernels(r64),
+        "fp32_factors": {"value": round(world * args.steps / (ms32 * 1e-3), 3), "unit": UNIT,
+                         "ms_per_step": round(ms32 / args.steps, 4), "iters": r32["iters"],
+                         "relres": r32["relres"], "x_err_vs_x_true": r32["err"], "dtype": "f64 Krylov + f32 factors",
+                         "roofline": roofline(r32, "fp32"), "kernels": kernels(r32),
+                         "gpu_launches": int(r32["timing"].launches), "clocks": r32["clocks"]},
+    }
+    sv64.close()
+    sv32.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(s, n_solves=2)
+    return out
+
+
+def cpu_oracle_setup(s):
+    import oracle as O
+    b = O.spmv(s.nb, s.rowptr, s.colidx, s.vals, s.x_true)
+    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, "colour")
+    prow, pcol, pval = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    pb = b.reshape(-1, 3)[perm].ravel()
+    return O, prow, pcol, pval, pb
+
+
+def oracle_solve(O, s, prow, pcol, pval, pb):
+    fac = O.ilu0(s.nb, prow, pcol, pval)
+    return O.bicgstab(s.nb, prow, pcol, pval, fac, pb, RTOL, 200)
+
+
+def cpu_baseline(s, n_solves=2):
+    O, prow, pcol, pval, pb = cpu_oracle_setup(s)
+    t0 = time.perf_counter()
+    for _ in range(n_solves):
+        res = oracle_solve(O, s, prow, pcol, pval, pb)
+    dt = time.perf_counter() - t0
+    return {"value": round(n_solves / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_solves} full solves (ILU0 + BiCGStab to rtol 1e-3, {res.iters} iterations) of the same "
+                      f"system in colour order, single-threaded C, {os.cpu_count()} host cores present"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    s = make_system(args.grid)
+    O, prow, pcol, pval, pb = cpu_oracle_setup(s)
+    for _ in range(args.warmup):
+        oracle_solve(O, s, prow, pcol, pval, pb)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = oracle_solve(O, s, prow, pcol, pval, pb)
+    dt = time.perf_counter() - t0
+    v = round(args.steps / dt, 4)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "schedule": "colour", "rtol": RTOL},
+            "iters": res.iters, "relres": res.relres,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step one full solve of the workload (single-threaded C oracle)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_2309_11488_gb300 import build
+    build.build()
+    out = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -79,6 +79,15 @@ enum {
                                FP32 with FP32 accumulation                    */
 };
 
+/* Launch structure of the sweeps over the schedule's phases (runs of
+ * mutually independent rows: the levels or colours). */
+enum {
+  OPM_SWEEP_AUTO = 0,        /* per-phase launches up to 1024 phases        */
+  OPM_SWEEP_PER_PHASE = 1,   /* one kernel launch per phase                 */
+  OPM_SWEEP_COOPERATIVE = 2  /* one cooperative launch walking all phases,
+                                with a bounded grid barrier between them    */
+};
+
 typedef struct opm_options {
   int32_t schedule;      /* OPM_SCHED_*                                       */
   int32_t precision;     /* OPM_PREC_*                                        */
@@ -87,10 +96,18 @@ typedef struct opm_options {
                             reads of the device status word; 0 = default (8)  */
   int32_t spin_limit_us; /* bound of every device-side wait in microseconds;
                             0 = default (2,000,000)                           */
-  int32_t debug_skip_item; /* test hook, -1 = off: the sweep item with this
-                            index is never signalled, so waits on it expire
-                            after spin_limit_us (OPM_ERR_TIMEOUT)            */
-  int32_t reserved[7];
+  int32_t debug_skip_item; /* test hook, -1 = off: the CTA with this index
+                            never arrives at the grid barriers of the
+                            cooperative sweep kernels, so the other CTAs'
+                            waits expire after spin_limit_us
+                            (OPM_ERR_TIMEOUT)                                */
+  int32_t profile_kernels; /* nonzero: record CUDA events around every kernel
+                            (also inside the iteration graph) and accumulate
+                            per-kernel device time in opm_timing             */
+  int32_t sweep_launch;  /* how the factorisation and the triangular sweeps
+                            walk the phases: OPM_SWEEP_AUTO, _PER_PHASE or
+                            _COOPERATIVE                                     */
+  int32_t reserved[5];
 } opm_options;
 
 /* Fill *opt with the defaults (AUTO schedule, FP64, default stream). */
@@ -169,6 +186,10 @@ typedef struct opm_info {
   int64_t nnzb_lower;  /* strictly lower blocks of the permuted matrix      */
   int64_t nnzb_upper;
   int64_t device_bytes; /* device memory held by the handle                 */
+  int32_t nphases;     /* runs of mutually independent rows the sweeps walk
+                          (the levels or colours; for natural order, runs of
+                          consecutive independent rows)                      */
+  int32_t reserved;
 } opm_info;
 
 opm_status opm_get_info(opm_handle h, opm_info *info);
@@ -187,12 +208,32 @@ opm_status opm_get_permutation(opm_handle h, int32_t *perm);
  */
 opm_status opm_get_factors(opm_handle h, double *lu, double *dinv);
 
-/* Cumulative device time, in milliseconds, of the last solve's phases
- * measured with CUDA events (0 when not measured). */
+/* Kernels of the path, for opm_timing's per-kernel counters. */
+enum {
+  OPM_KERNEL_FACTOR = 0, /* value permutation + ILU0 decomposition          */
+  OPM_KERNEL_APPLY = 1,  /* forward + backward substitution (2 per iteration) */
+  OPM_KERNEL_SPMV = 2,   /* SpMV with fused dot products (2 per iteration)  */
+  OPM_KERNEL_UPDATE = 3, /* x, r update and stopping rule                   */
+  OPM_KERNEL_SETUP = 4,  /* b permutation and ||b||                         */
+  OPM_KERNEL_FINISH = 5, /* true residual and x permutation                 */
+  OPM_KERNEL_COUNT = 6
+};
+
+/* Device time, in milliseconds, of the last solve's phases and of the last
+ * factorisation, measured with CUDA events on the handle's stream; the
+ * number of kernels the handle has launched (graph nodes included); and,
+ * with opm_options.profile_kernels, per-kernel device time and launch counts
+ * accumulated over the iterations that did work since the last
+ * opm_reset_timing. */
 typedef struct opm_timing {
   float setup_ms, iterate_ms, finish_ms, factor_ms;
+  int64_t launches;
+  double kernel_ms[OPM_KERNEL_COUNT];
+  int64_t kernel_count[OPM_KERNEL_COUNT];
 } opm_timing;
 opm_status opm_get_timing(opm_handle h, opm_timing *t);
+/* Zero the launch counter and the per-kernel accumulators. */
+opm_status opm_reset_timing(opm_handle h);
 
 #ifdef __cplusplus
 }

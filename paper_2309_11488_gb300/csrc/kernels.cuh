@@ -11,10 +11,9 @@
 //  * k_update      x and r updates of BiCGStab plus the next reductions.
 //
 // The triangular kernels replace the paper's one launch per colour or level
-// (Section 4.4) by one cooperative launch per preconditioner application:
-// resident warps walk slices of 32 rows in schedule order, wait (bounded) on
-// the ready flags of the other slices a slice reads, and publish their own.
-// Dependencies inside one slice are resolved in rounds within the warp.
+// (Section 4.4) by one cooperative launch per preconditioner application (or
+// factorisation) that walks the colours or levels with a bounded grid
+// barrier between them.
 //
 // Reductions are deterministic: every static-tiled kernel reduces its 256
 // rows in a fixed butterfly, writes one partial per tile, and the last CTA to
@@ -43,13 +42,12 @@ struct Sys {
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
   void *y;   // forward intermediate (factor precision)
-  uint32_t *fflag, *bflag;
-  const int32_t *fdep_ptr, *fdep, *bdep_ptr, *bdep;
-  const uint32_t *fmask, *bmask;
+  const int32_t *phase_ptr;
+  int32_t nphases;
   double *partials;
   DevState *st;
   uint64_t spin_limit_ns;
-  int32_t skip_item;
+  int32_t skip_cta;  // test hook: this CTA never arrives at grid barriers (-1: off)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -80,27 +78,6 @@ __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Bounded wait until *flag == epoch.  Gives up (false) when another warp has
-// reported an error, or sets OPM_ERR_TIMEOUT once limit_ns has passed.
-__device__ __noinline__ bool wait_flag(const uint32_t *flag, uint32_t epoch, DevState *st,
-                                       uint64_t limit_ns) {
-  if (ld_acquire(flag) == epoch) return true;
-  const uint64_t t0 = gtimer();
-  unsigned nap = 32;
-  for (uint32_t it = 1;; ++it) {
-    __nanosleep(nap);  // back off so that waiting warps do not flood L2 with polls
-    if (nap < 256) nap <<= 1;
-    if (ld_acquire(flag) == epoch) return true;
-    if ((it & 15u) == 0) {
-      if (ld_relaxed_i32(&st->error) != 0) return false;
-      if (gtimer() - t0 > limit_ns) {
-        atomicCAS(&st->error, 0, (int32_t)OPM_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
 }
 
 template <typename T>
@@ -165,7 +142,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
 template <int NV>
 __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], double *partials, uint32_t *counter,
                                                 double (&tot)[NV]) {
-  __shared__ double sm[8 * NV];
+  __shared__ double sm[32 * NV];
   __shared__ int amlast;
   block_reduce<NV>(v, sm);
   if (threadIdx.x == 0) {
@@ -225,25 +202,38 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
 }
 
 // ------------------------------------------------------------ static kernels
+//
+// Each CTA covers one tile of kTileRows = 1024 rows, so that a reduction
+// costs one partial and one arrival per 1024 rows: streaming kernels use 256
+// threads in 4 passes (thread t handles rows tile + t, + 256, + 512, + 768).
+
+#define OPM_TILE_ROWS(i)                                                    \
+  for (int pass_ = 0, i = blockIdx.x * kTileRows + threadIdx.x; pass_ < 4; \
+       ++pass_, i += 256)
+
+// SpMV-type kernels instead use 1024 threads per CTA, one row each (FP64 FMA
+// throughput wants every warp slot; 4 rows per thread costs registers).
+#define OPM_TILE_ROW1(i) for (int pass_ = 0, i = blockIdx.x * kTileRows + threadIdx.x; pass_ < 1; ++pass_)
 
 // r = P b, r^ = r, x = p = v = 0, ||b||^2; the last CTA starts the solve.
-__global__ void __launch_bounds__(256) k_setup(Sys S, const double *__restrict__ b_nat, double rtol,
+__global__ void __launch_bounds__(256, 6) k_setup(Sys S, const double *__restrict__ b_nat, double rtol,
                                                int32_t maxit) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
   double acc[1] = {0.0};
-  if (i < S.n) {
-    const int o = S.perm[i];
-    const double b0 = b_nat[3ll * o], b1 = b_nat[3ll * o + 1], b2 = b_nat[3ll * o + 2];
-    double *r = S.r + 3ll * i, *rh = S.rh + 3ll * i;
-    r[0] = b0; r[1] = b1; r[2] = b2;
-    rh[0] = b0; rh[1] = b1; rh[2] = b2;
+  OPM_TILE_ROWS(i) {
+    if (i < S.n) {
+      const int o = S.perm[i];
+      const double b0 = b_nat[3ll * o], b1 = b_nat[3ll * o + 1], b2 = b_nat[3ll * o + 2];
+      double *r = S.r + 3ll * i, *rh = S.rh + 3ll * i;
+      r[0] = b0; r[1] = b1; r[2] = b2;
+      rh[0] = b0; rh[1] = b1; rh[2] = b2;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S.x[3ll * i + c] = 0.0;
-      S.p[3ll * i + c] = 0.0;
-      S.v[3ll * i + c] = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        S.x[3ll * i + c] = 0.0;
+        S.p[3ll * i + c] = 0.0;
+        S.v[3ll * i + c] = 0.0;
+      }
+      acc[0] = fma(b0, b0, fma(b1, b1, fma(b2, b2, acc[0])));
     }
-    acc[0] = b0 * b0 + b1 * b1 + b2 * b2;
   }
   double tot[1];
   if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
@@ -256,6 +246,7 @@ __global__ void __launch_bounds__(256) k_setup(Sys S, const double *__restrict__
     st->iters = 0;
     st->half = 0;
     st->error = 0;
+    st->bar_count = 0;
     st->relres = 0.0;
     st->rho = tot[0];
     st->rho_prev = 1.0;
@@ -270,17 +261,18 @@ __global__ void __launch_bounds__(256) k_setup(Sys S, const double *__restrict__
 }
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).
-__global__ void __launch_bounds__(256) k_spmv_v(Sys S) {
+__global__ void __launch_bounds__(1024, 2) k_spmv_v(Sys S) {
   if (!running(S.st)) return;
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_spmv(S.a_rp, S.a_col, S.a_val, S.ph, i, S.n, y0, y1, y2);
   double acc[1] = {0.0};
-  if (i < S.n) {
-    double *v = S.v + 3ll * i;
-    v[0] = y0; v[1] = y1; v[2] = y2;
-    const double *rh = S.rh + 3ll * i;
-    acc[0] = rh[0] * y0 + rh[1] * y1 + rh[2] * y2;
+  OPM_TILE_ROW1(i) {
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    row_spmv(S.a_rp, S.a_col, S.a_val, S.ph, i, S.n, y0, y1, y2);
+    if (i < S.n) {
+      double *v = S.v + 3ll * i;
+      v[0] = y0; v[1] = y1; v[2] = y2;
+      const double *rh = S.rh + 3ll * i;
+      acc[0] = fma(rh[0], y0, fma(rh[1], y1, fma(rh[2], y2, acc[0])));
+    }
   }
   double tot[1];
   if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
@@ -296,19 +288,21 @@ __global__ void __launch_bounds__(256) k_spmv_v(Sys S) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(256) k_spmv_t(Sys S) {
+__global__ void __launch_bounds__(1024, 2) k_spmv_t(Sys S) {
   if (!running(S.st)) return;
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_spmv(S.a_rp, S.a_col, S.a_val, S.sh, i, S.n, y0, y1, y2);
   double acc[3] = {0.0, 0.0, 0.0};
-  if (i < S.n) {
-    double *t = S.t + 3ll * i;
-    t[0] = y0; t[1] = y1; t[2] = y2;
-    const double *s = S.s + 3ll * i;
-    acc[0] = y0 * s[0] + y1 * s[1] + y2 * s[2];
-    acc[1] = y0 * y0 + y1 * y1 + y2 * y2;
-    acc[2] = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+  OPM_TILE_ROW1(i) {
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    row_spmv(S.a_rp, S.a_col, S.a_val, S.sh, i, S.n, y0, y1, y2);
+    if (i < S.n) {
+      double *t = S.t + 3ll * i;
+      t[0] = y0; t[1] = y1; t[2] = y2;
+      const double *s = S.s + 3ll * i;
+      const double s0 = s[0], s1 = s[1], s2 = s[2];
+      acc[0] = fma(y0, s0, fma(y1, s1, fma(y2, s2, acc[0])));
+      acc[1] = fma(y0, y0, fma(y1, y1, fma(y2, y2, acc[1])));
+      acc[2] = fma(s0, s0, fma(s1, s1, fma(s2, s2, acc[2])));
+    }
   }
   double tot[3];
   if (last_cta_reduce<3>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
@@ -334,25 +328,26 @@ __global__ void __launch_bounds__(256) k_spmv_t(Sys S) {
 
 // x += alpha p^ + omega s^, r = s - omega t, ||r||^2, (r^, r); stopping rule,
 // then beta for the next iteration.
-__global__ void __launch_bounds__(256) k_update(Sys S) {
+__global__ void __launch_bounds__(256, 6) k_update(Sys S) {
   if (!running(S.st)) return;
-  const int i = blockIdx.x * 256 + threadIdx.x;
   const DevState *cst = S.st;
   const double alpha = cst->alpha, omega = cst->omega;
   const int half = cst->half;
   double acc[2] = {0.0, 0.0};
-  if (i < S.n) {
+  OPM_TILE_ROWS(i) {
+    if (i < S.n) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const size_t e = 3ll * i + c;
-      if (half) {
-        S.x[e] = fma(alpha, S.ph[e], S.x[e]);
-      } else {
-        S.x[e] = S.x[e] + fma(alpha, S.ph[e], omega * S.sh[e]);
-        const double rr = fma(-omega, S.t[e], S.s[e]);
-        S.r[e] = rr;
-        acc[0] = fma(rr, rr, acc[0]);
-        acc[1] = fma(S.rh[e], rr, acc[1]);
+      for (int c = 0; c < 3; ++c) {
+        const size_t e = 3ll * i + c;
+        if (half) {
+          S.x[e] = fma(alpha, S.ph[e], S.x[e]);
+        } else {
+          S.x[e] = fma(alpha, S.ph[e], fma(omega, S.sh[e], S.x[e]));
+          const double rr = fma(-omega, S.t[e], S.s[e]);
+          S.r[e] = rr;
+          acc[0] = fma(rr, rr, acc[0]);
+          acc[1] = fma(S.rh[e], rr, acc[1]);
+        }
       }
     }
   }
@@ -388,18 +383,19 @@ __global__ void __launch_bounds__(256) k_update(Sys S) {
 
 // Final true residual ||b - A x|| / ||b|| in FP64 and x back to the caller's
 // order.
-__global__ void __launch_bounds__(256) k_finish(Sys S, const double *__restrict__ b_nat,
+__global__ void __launch_bounds__(1024, 2) k_finish(Sys S, const double *__restrict__ b_nat,
                                                 double *__restrict__ x_nat) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
   double acc[1] = {0.0};
-  if (i < S.n) {
-    const int o = S.perm[i];
-    const double d0 = b_nat[3ll * o] - y0, d1 = b_nat[3ll * o + 1] - y1, d2 = b_nat[3ll * o + 2] - y2;
-    acc[0] = d0 * d0 + d1 * d1 + d2 * d2;
+  OPM_TILE_ROW1(i) {
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
+    if (i < S.n) {
+      const int o = S.perm[i];
+      const double d0 = b_nat[3ll * o] - y0, d1 = b_nat[3ll * o + 1] - y1, d2 = b_nat[3ll * o + 2] - y2;
+      acc[0] = fma(d0, d0, fma(d1, d1, fma(d2, d2, acc[0])));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x_nat[3ll * o + c] = S.x[3ll * i + c];
+      for (int c = 0; c < 3; ++c) x_nat[3ll * o + c] = S.x[3ll * i + c];
+    }
   }
   double tot[1];
   if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
@@ -408,81 +404,81 @@ __global__ void __launch_bounds__(256) k_finish(Sys S, const double *__restrict_
   }
 }
 
-// y = A x in the caller's order (x already permuted into S.w).
-__global__ void __launch_bounds__(256) k_spmv_plain(Sys S, const double *__restrict__ xp,
+// y = A x in the caller's order (x already permuted).
+__global__ void __launch_bounds__(1024, 2) k_spmv_plain(Sys S, const double *__restrict__ xp,
                                                     double *__restrict__ y_nat) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_spmv(S.a_rp, S.a_col, S.a_val, xp, i, S.n, y0, y1, y2);
-  if (i < S.n) {
-    const int o = S.perm[i];
-    y_nat[3ll * o] = y0;
-    y_nat[3ll * o + 1] = y1;
-    y_nat[3ll * o + 2] = y2;
-  }
-}
-
-// out[i] = in[perm[i]] (caller's order -> schedule order).
-__global__ void __launch_bounds__(256) k_gather(Sys S, const double *__restrict__ in, double *__restrict__ out) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  if (i < S.n) {
-    const int o = S.perm[i];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[3ll * i + c] = in[3ll * o + c];
-  }
-}
-
-// out[perm[i]] = in[i] (schedule order -> caller's order).
-__global__ void __launch_bounds__(256) k_scatter(Sys S, const double *__restrict__ in, double *__restrict__ out) {
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  if (i < S.n) {
-    const int o = S.perm[i];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[3ll * o + c] = in[3ll * i + c];
-  }
-}
-
-// ----------------------------------------------------- sync-free sweeps
-//
-// Sweep kernels are launched cooperatively with at most one wave of CTAs, so
-// all their warps are resident at once.  Warp g of W handles slices g, g+W,
-// g+2W, ... in increasing order (the backward sweep in decreasing order).  A
-// slice only waits for slices that precede it in its sweep; those belong to
-// resident warps that reach them without waiting on anything later, so every
-// wait ends (and is bounded in time anyway).
-
-struct Sweep {
-  uint32_t epoch;
-  uint64_t limit;
-};
-
-// Last CTA out advances the epoch for the next sweep launch.
-__device__ __forceinline__ void sweep_exit(DevState *st, uint32_t epoch) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&st->done, 1u) == gridDim.x - 1) {
-      st->done = 0;
-      st->epoch = epoch + 1;
-      __threadfence();
+  OPM_TILE_ROW1(i) {
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+    row_spmv(S.a_rp, S.a_col, S.a_val, xp, i, S.n, y0, y1, y2);
+    if (i < S.n) {
+      const int o = S.perm[i];
+      y_nat[3ll * o] = y0;
+      y_nat[3ll * o + 1] = y1;
+      y_nat[3ll * o + 2] = y2;
     }
   }
 }
 
-__device__ __forceinline__ void signal(const Sys &S, uint32_t *flags, int s, int item, uint32_t epoch) {
-  __threadfence();
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0 && item != S.skip_item) st_release(flags + s, epoch);
+// out[i] = in[perm[i]] (caller's order -> schedule order).
+__global__ void __launch_bounds__(256, 6) k_gather(Sys S, const double *__restrict__ in, double *__restrict__ out) {
+  OPM_TILE_ROWS(i) {
+    if (i < S.n) {
+      const int o = S.perm[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[3ll * i + c] = in[3ll * o + c];
+    }
+  }
 }
 
-// Lanes poll the distinct slices listed for this slice, up to 32 at a time.
-__device__ __forceinline__ void wait_slices(const Sys &S, const int32_t *__restrict__ ptr,
-                                            const int32_t *__restrict__ list, const uint32_t *flags, int sl,
-                                            const Sweep &sw) {
-  const int lane = threadIdx.x & 31;
-  const int d1 = ptr[sl + 1];
-  for (int d = ptr[sl] + lane; d < d1; d += 32) wait_flag(flags + list[d], sw.epoch, S.st, sw.limit);
-  __syncwarp();
+// out[perm[i]] = in[i] (schedule order -> caller's order).
+__global__ void __launch_bounds__(256, 6) k_scatter(Sys S, const double *__restrict__ in, double *__restrict__ out) {
+  OPM_TILE_ROWS(i) {
+    if (i < S.n) {
+      const int o = S.perm[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[3ll * o + c] = in[3ll * i + c];
+    }
+  }
+}
+
+// ----------------------------------------------------------- phase sweeps
+//
+// The schedule's row order is cut into phases: maximal runs of rows none of
+// which reads another row of its run (the levels or the colours).  A sweep
+// kernel is one cooperative launch (all CTAs resident) that walks the phases
+// in order, every warp taking 32-row slices of the current phase grid-strided,
+// with a grid barrier between phases.  Values produced in earlier phases by
+// other SMs are read through L2 (ld.global.cg), never from L1.
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  On timeout
+// it records OPM_ERR_TIMEOUT and lets the CTA continue; once an error is
+// recorded, later barriers do not wait.  The CTA numbered skip_cta (a test
+// hook, normally -1) never arrives, so the others' waits run out.
+__device__ __forceinline__ void grid_sync(DevState *st, uint64_t limit_ns, int skip_cta) {
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x != skip_cta) {
+    const uint32_t gen = ld_acquire(&st->bar_gen);
+    __threadfence();
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      st->bar_count = 0;
+      __threadfence();
+      st_release(&st->bar_gen, gen + 1);
+    } else if (ld_relaxed_i32(&st->error) == 0) {
+      const uint64_t t0 = gtimer();
+      for (uint32_t it = 0;; ++it) {
+        if (ld_acquire(&st->bar_gen) != gen) break;
+        __nanosleep(32);
+        if ((it & 63u) == 63u) {
+          if (ld_relaxed_i32(&st->error) != 0) break;
+          if (gtimer() - t0 > limit_ns) {
+            atomicCAS(&st->error, 0, (int32_t)OPM_ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
 }
 
 template <typename TF>
@@ -491,13 +487,23 @@ struct Vec3 {
 };
 
 template <typename TF>
-__device__ __forceinline__ Vec3<TF> load3(const TF *p) {
-  return {ldcg(p), ldcg(p + 1), ldcg(p + 2)};
+__device__ __forceinline__ Vec3<TF> load3cg(const TF *p) {
+  return {__ldcg(p), __ldcg(p + 1), __ldcg(p + 2)};
 }
 
-// acc -= sum over the lane's row of a sliced part of B_ij v_j, v read from
-// other warps' output (L2), two slabs per step for memory-level parallelism.
-// Lanes with !act skip their loads; all lanes must call.
+// a -= B v for one 3x3 block (entry-planar with stride c) in FMA form.
+template <typename TF>
+__device__ __forceinline__ void blk_sub(const TF *__restrict__ B, int c, TF v0, TF v1, TF v2, TF &a0, TF &a1,
+                                        TF &a2) {
+  a0 = fma(-__ldg(B), v0, fma(-__ldg(B + c), v1, fma(-__ldg(B + 2 * c), v2, a0)));
+  a1 = fma(-__ldg(B + 3 * c), v0, fma(-__ldg(B + 4 * c), v1, fma(-__ldg(B + 5 * c), v2, a1)));
+  a2 = fma(-__ldg(B + 6 * c), v0, fma(-__ldg(B + 7 * c), v1, fma(-__ldg(B + 8 * c), v2, a2)));
+}
+
+// a -= sum over the lane's row of a sliced part of B_ij v_j, v read through
+// L2; two slabs per step for memory-level parallelism.  All lanes call with
+// len = their row's block count (0 past n), which defines the slab layout of
+// the slice; lanes with !act issue no loads.
 template <typename TF, typename TV>
 __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const TF *__restrict__ vals,
                                         const TV *vec, int len, int base0, int maxlen, bool act, TF &a0,
@@ -511,43 +517,36 @@ __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const T
     base = b1 + __popc(m1);
     const bool u0 = act && len > k, u1 = act && len > k + 1;
     const int q0 = __popc(m0 & lt), q1 = __popc(m1 & lt);
-    const int c0 = __popc(m0), c1 = __popc(m1);
     int j0 = 0, j1 = 0;
-    if (u0) j0 = col[b0 + q0];
-    if (u1) j1 = col[b1 + q1];
+    if (u0) j0 = __ldg(col + b0 + q0);
+    if (u1) j1 = __ldg(col + b1 + q1);
     if (u0) {
-      const TF *B = vals + 9ll * b0 + q0;
-      const TF v0 = (TF)ldcg(vec + 3ll * j0), v1 = (TF)ldcg(vec + 3ll * j0 + 1), v2 = (TF)ldcg(vec + 3ll * j0 + 2);
-      a0 -= B[0] * v0 + B[c0] * v1 + B[2 * c0] * v2;
-      a1 -= B[3 * c0] * v0 + B[4 * c0] * v1 + B[5 * c0] * v2;
-      a2 -= B[6 * c0] * v0 + B[7 * c0] * v1 + B[8 * c0] * v2;
+      const Vec3<TV> v = load3cg(vec + 3ll * j0);
+      blk_sub<TF>(vals + 9ll * b0 + q0, __popc(m0), (TF)v.c0, (TF)v.c1, (TF)v.c2, a0, a1, a2);
     }
     if (u1) {
-      const TF *B = vals + 9ll * b1 + q1;
-      const TF v0 = (TF)ldcg(vec + 3ll * j1), v1 = (TF)ldcg(vec + 3ll * j1 + 1), v2 = (TF)ldcg(vec + 3ll * j1 + 2);
-      a0 -= B[0] * v0 + B[c1] * v1 + B[2 * c1] * v2;
-      a1 -= B[3 * c1] * v0 + B[4 * c1] * v1 + B[5 * c1] * v2;
-      a2 -= B[6 * c1] * v0 + B[7 * c1] * v1 + B[8 * c1] * v2;
+      const Vec3<TV> v = load3cg(vec + 3ll * j1);
+      blk_sub<TF>(vals + 9ll * b1 + q1, __popc(m1), (TF)v.c0, (TF)v.c1, (TF)v.c2, a0, a1, a2);
     }
   }
 }
 
-// One slice of the forward substitution y_i = rhs_i - sum_{j<i} L_ij y_j,
-// with the right-hand side formed on the fly (Algorithm 1, equation 3).
+// Forward substitution for the rows of slice sl inside [r0, r1):
+// y_i = rhs_i - sum_{j<i} L_ij y_j (Algorithm 1, equation 3), the right-hand
+// side formed on the fly.  With also_back (last phase: no U columns past the
+// phase), the backward step z_i = inv(U_ii) y_i follows at once.
 template <typename TF, int MODE>
-__device__ __forceinline__ void fwd_slice(const Sys &S, int sl, const Sweep &sw, double alpha, double beta,
-                                          double omega, const double *in) {
+__device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, double alpha, double beta,
+                                         double omega, const double *in, double *z, bool also_back) {
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
-  const int n = S.n;
-  const bool valid = i < n;
+  const bool act = i >= r0 && i < r1;
   TF *y = static_cast<TF *>(S.y);
   const TF *lu = static_cast<const TF *>(S.lu);
   double h0 = 0.0, h1 = 0.0, h2 = 0.0;
-  unsigned dep = 0;
-  int len = 0;
-  if (valid) {
+  const int len = (i < S.n) ? __ldg(S.l_rp + i + 1) - __ldg(S.l_rp + i) : 0;
+  if (act) {
     const size_t e = 3ll * i;
     if (MODE == kModeP) {
       h0 = fma(beta, fma(-omega, S.v[e], S.p[e]), S.r[e]);
@@ -562,221 +561,231 @@ __device__ __forceinline__ void fwd_slice(const Sys &S, int sl, const Sweep &sw,
     } else {
       h0 = in[e]; h1 = in[e + 1]; h2 = in[e + 2];
     }
-    dep = S.fmask[i];
-    len = S.l_rp[i + 1] - S.l_rp[i];
   }
-  wait_slices(S, S.fdep_ptr, S.fdep, S.fflag, sl, sw);
-  const int base0 = (s0 < n) ? S.l_rp[s0] : 0;
+  const int base0 = (s0 < S.n) ? __ldg(S.l_rp + s0) : 0;
   const int maxlen = __reduce_max_sync(0xffffffffu, len);
-  unsigned done = __ballot_sync(0xffffffffu, !valid);
-  bool mine = !valid;
-  while (done != 0xffffffffu) {
-    const bool ready = !mine && ((dep & ~done) == 0);
-    TF a0 = (TF)h0, a1 = (TF)h1, a2 = (TF)h2;
-    row_sub<TF, TF>(S.l_col, lu, y, len, base0, maxlen, ready, a0, a1, a2);
-    if (ready) {
+  TF a0 = (TF)h0, a1 = (TF)h1, a2 = (TF)h2;
+  row_sub<TF, TF>(S.l_col, lu, y, len, base0, maxlen, act, a0, a1, a2);
+  if (act) {
+    if (also_back) {
+      const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
+      double *zi = z + 3ll * i;
+      zi[0] = (double)fma(__ldg(D), a0, fma(__ldg(D + 32), a1, __ldg(D + 64) * a2));
+      zi[1] = (double)fma(__ldg(D + 96), a0, fma(__ldg(D + 128), a1, __ldg(D + 160) * a2));
+      zi[2] = (double)fma(__ldg(D + 192), a0, fma(__ldg(D + 224), a1, __ldg(D + 256) * a2));
+    } else {
       TF *yi = y + 3ll * i;
       yi[0] = a0; yi[1] = a1; yi[2] = a2;
-      mine = true;
     }
-    done |= __ballot_sync(0xffffffffu, ready);
-    __syncwarp();
   }
-  signal(S, S.fflag, sl, sl, sw.epoch);
 }
 
-// One slice of the backward substitution z_i = inv(U_ii)(y_i - sum_{j>i}
-// U_ij z_j) (Algorithm 1, equation 4); z is written in FP64.
+// Backward substitution for the rows of slice sl inside [r0, r1):
+// z_i = inv(U_ii)(y_i - sum_{j>i} U_ij z_j) (Algorithm 1, equation 4).
 template <typename TF>
-__device__ __forceinline__ void bwd_slice(const Sys &S, int sl, const Sweep &sw, double *z) {
+__device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1, double *z) {
+  const int lane = threadIdx.x & 31;
+  const int s0 = sl * 32;
+  const int i = s0 + lane;
+  const bool act = i >= r0 && i < r1;
+  const TF *y = static_cast<const TF *>(S.y);
+  const TF *lu = static_cast<const TF *>(S.lu);
+  const int len = (i < S.n) ? __ldg(S.u_rp + i + 1) - __ldg(S.u_rp + i) : 0;
+  TF a0 = TF(0), a1 = TF(0), a2 = TF(0);
+  if (act) {
+    const Vec3<TF> yi = load3cg(y + 3ll * i);
+    a0 = yi.c0; a1 = yi.c1; a2 = yi.c2;
+  }
+  const int base0 = (s0 < S.n) ? __ldg(S.u_rp + s0) : 0;
+  const int maxlen = __reduce_max_sync(0xffffffffu, len);
+  row_sub<TF, double>(S.u_col, lu + S.u_off, z, len, base0, maxlen, act, a0, a1, a2);
+  if (act) {
+    const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
+    double *zi = z + 3ll * i;
+    zi[0] = (double)fma(__ldg(D), a0, fma(__ldg(D + 32), a1, __ldg(D + 64) * a2));
+    zi[1] = (double)fma(__ldg(D + 96), a0, fma(__ldg(D + 128), a1, __ldg(D + 160) * a2));
+    zi[2] = (double)fma(__ldg(D + 192), a0, fma(__ldg(D + 224), a1, __ldg(D + 256) * a2));
+  }
+}
+
+// ILU0 application z = U^-1 L^-1 rhs (Algorithm 1) in one cooperative
+// launch: forward phases in order, then backward phases in reverse order;
+// the last phase does both sweeps at once.
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(1024) k_apply(Sys S, const double *in, double *out) {
+  DevState *st = S.st;
+  if (MODE != kModePlain && !running(st)) return;
+  const double alpha = st->alpha, beta = st->beta, omega = st->omega;
+  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int np = S.nphases;
+  for (int ph = 0; ph < np; ++ph) {
+    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
+    const bool last = ph == np - 1;
+    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W)
+      fwd_rows<TF, MODE>(S, sl, r0, r1, alpha, beta, omega, in, z, last);
+    if (!last) grid_sync(st, S.spin_limit_ns, S.skip_cta);
+  }
+  for (int ph = np - 2; ph >= 0; --ph) {
+    grid_sync(st, S.spin_limit_ns, S.skip_cta);
+    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
+    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W) bwd_rows<TF>(S, sl, r0, r1, z);
+  }
+}
+
+// The same sweeps with one launch per phase (kernel boundaries as the
+// barrier), for schedules with few phases: plain grids of 256-thread CTAs,
+// one 32-row slice per warp, at full occupancy.
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(256) k_fwd_phase(Sys S, int r0, int r1, int last, const double *in,
+                                                    double *out) {
+  DevState *st = S.st;
+  if (MODE != kModePlain && !running(st)) return;
+  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (sl > ((r1 - 1) >> 5)) return;
+  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
+  fwd_rows<TF, MODE>(S, sl, r0, r1, st->alpha, st->beta, st->omega, in, z, last != 0);
+}
+
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(256) k_bwd_phase(Sys S, int r0, int r1, double *out) {
+  DevState *st = S.st;
+  if (MODE != kModePlain && !running(st)) return;
+  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (sl > ((r1 - 1) >> 5)) return;
+  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
+  bwd_rows<TF>(S, sl, r0, r1, z);
+}
+
+// ILU0 decomposition (Algorithm 2) of the permuted matrix, phase by phase,
+// fused with the value permutation: with vals_user, block w of the permuted
+// matrix is copied from the caller's block a_src[w] (Algorithm 3's index
+// copy) into both A and the factors.  Row i of phase p reads only rows of
+// earlier phases (its pivots k < i) and updates only its own blocks.
+template <typename TF>
+__device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1,
+                                            const double *__restrict__ vals_user) {
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
   const int n = S.n;
-  const bool valid = i < n;
-  const TF *y = static_cast<const TF *>(S.y);
-  const TF *lu = static_cast<const TF *>(S.lu);
-  unsigned dep = 0;
-  int len = 0;
-  if (valid) {
-    dep = S.bmask[i];
-    len = S.u_rp[i + 1] - S.u_rp[i];
-  }
-  if (lane == 0) wait_flag(S.fflag + sl, sw.epoch, S.st, sw.limit);
-  wait_slices(S, S.bdep_ptr, S.bdep, S.bflag, sl, sw);
-  Vec3<TF> yi = {TF(0), TF(0), TF(0)};
-  if (valid) yi = load3(y + 3ll * i);
-  const int base0 = (s0 < n) ? S.u_rp[s0] : 0;
-  const int maxlen = __reduce_max_sync(0xffffffffu, len);
-  const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
-  TF d[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) d[c] = valid ? D[32 * c] : TF(0);
-  unsigned done = __ballot_sync(0xffffffffu, !valid);
-  bool mine = !valid;
-  while (done != 0xffffffffu) {
-    const bool ready = !mine && ((dep & ~done) == 0);
-    TF a0 = yi.c0, a1 = yi.c1, a2 = yi.c2;
-    row_sub<TF, double>(S.u_col, lu + S.u_off, z, len, base0, maxlen, ready, a0, a1, a2);
-    if (ready) {
-      double *zi = z + 3ll * i;
-      zi[0] = (double)(d[0] * a0 + d[1] * a1 + d[2] * a2);
-      zi[1] = (double)(d[3] * a0 + d[4] * a1 + d[5] * a2);
-      zi[2] = (double)(d[6] * a0 + d[7] * a1 + d[8] * a2);
-      mine = true;
-    }
-    done |= __ballot_sync(0xffffffffu, ready);
-    __syncwarp();
-  }
-  signal(S, S.bflag, sl, S.nslices + (S.nslices - 1 - sl), sw.epoch);
-}
-
-// ILU0 application z = U^-1 L^-1 rhs in one cooperative launch: every warp
-// runs its forward slices, then its backward slices.
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_apply(Sys S, const double *in, double *out) {
-  DevState *st = S.st;
-  const uint32_t epoch = st->epoch;
-  const bool run = (MODE == kModePlain) || running(st);
-  if (run) {
-    const Sweep sw{epoch, S.spin_limit_ns};
-    const double alpha = st->alpha, beta = st->beta, omega = st->omega;
-    double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
-    const int ns = S.nslices;
-    const int W = gridDim.x * (blockDim.x >> 5);
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (int sl = g; sl < ns; sl += W) fwd_slice<TF, MODE>(S, sl, sw, alpha, beta, omega, in);
-    for (int q = g; q < ns; q += W) bwd_slice<TF>(S, ns - 1 - q, sw, z);
-  }
-  sweep_exit(st, epoch);
-}
-
-// ILU0 decomposition (Algorithm 2) of the permuted matrix, one slice per
-// warp step in schedule order, fused with the value permutation: with
-// vals_user, block w of the permuted matrix is copied from the caller's
-// block a_src[w] (Algorithm 3's index copy) into both A and the factors.
-template <typename TF>
-__global__ void __launch_bounds__(256) k_factor(Sys S, const double *__restrict__ vals_user) {
-  DevState *st = S.st;
-  const uint32_t epoch = st->epoch;
-  const Sweep sw{epoch, S.spin_limit_ns};
-  const int n = S.n;
+  const bool act = i >= r0 && i < r1;
   TF *lu = static_cast<TF *>(S.lu);
   const unsigned lt = lanemask_lt();
-  const int lane = threadIdx.x & 31;
-  const int W = gridDim.x * (blockDim.x >> 5);
-  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (int sl = g; sl < S.nslices; sl += W) {
-    const int s0 = sl * 32;
-    const int i = s0 + lane;
-    const bool valid = i < n;
-    // ---- copy phase: A's row into A (sliced) and into L / D / U slots
-    {
-      const int len = valid ? S.a_rp[i + 1] - S.a_rp[i] : 0;
-      int base = (s0 < n) ? S.a_rp[s0] : 0;
-      const int maxlen = __reduce_max_sync(0xffffffffu, len);
-      for (int k = 0; k < maxlen; ++k) {
-        const unsigned m = __ballot_sync(0xffffffffu, len > k);
-        if (len > k) {
-          const int cnt = __popc(m);
-          const int q = __popc(m & lt);
-          const int w = base + q;
-          const int64_t dst = S.a_dst[w];
-          const int64_t doff = dst >> 6;
-          const int dstr = (int)(dst & 63);
-          double *av = S.a_val + 9ll * base + q;
-          double e[9];
-          if (vals_user) {
-            const double *src = vals_user + 9ll * S.a_src[w];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) {
-              e[c] = __ldg(src + c);
-              av[c * cnt] = e[c];
-            }
-          } else {
-#pragma unroll
-            for (int c = 0; c < 9; ++c) e[c] = av[c * cnt];
-          }
-#pragma unroll
-          for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
-        }
-        base += __popc(m);
-      }
-    }
-    // ---- dependencies on earlier rows (the pivots k < i of row i)
-    const unsigned dep = valid ? S.fmask[i] : 0u;
-    wait_slices(S, S.fdep_ptr, S.fdep, S.fflag, sl, sw);
-    const int len = valid ? S.l_rp[i + 1] - S.l_rp[i] : 0;
-    const int lrow = valid ? S.l_rp[i] : 0;
-    const int base0 = (s0 < n) ? S.l_rp[s0] : 0;
-    const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    unsigned done = __ballot_sync(0xffffffffu, !valid);
-    bool mine = !valid;
-    while (done != 0xffffffffu) {
-      const bool ready = !mine && ((dep & ~done) == 0);
-      int base = base0;
-      for (int k = 0; k < maxlen; ++k) {
-        const unsigned m = __ballot_sync(0xffffffffu, len > k);
-        if (ready && len > k) {
-          const int cnt = __popc(m);
-          const int q = __popc(m & lt);
-          const int kc = S.l_col[base + q];
-          TF *Lp = lu + 9ll * base + q;
-          const TF *Dk = lu + S.d_off + (int64_t)kSliceVals * (kc >> 5) + (kc & 31);
-          TF a[9], d[9], l[9];
+  DevState *st = S.st;
+  // ---- copy A's row into A (sliced) and into its L / D / U slots
+  {
+    const int len = (i < n) ? __ldg(S.a_rp + i + 1) - __ldg(S.a_rp + i) : 0;
+    int base = (s0 < n) ? __ldg(S.a_rp + s0) : 0;
+    const int maxlen = __reduce_max_sync(0xffffffffu, act ? len : 0);
+    for (int k = 0; k < maxlen; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, len > k);
+      if (act && len > k) {
+        const int cnt = __popc(m);
+        const int q = __popc(m & lt);
+        const int w = base + q;
+        const int64_t dst = __ldg(S.a_dst + w);
+        const int64_t doff = dst >> 6;
+        const int dstr = (int)(dst & 63);
+        double *av = S.a_val + 9ll * base + q;
+        double e[9];
+        if (vals_user) {
+          const double *src = vals_user + 9ll * __ldg(S.a_src + w);
 #pragma unroll
           for (int c = 0; c < 9; ++c) {
-            a[c] = Lp[c * cnt];
-            d[c] = ldcg(Dk + 32 * c);
+            e[c] = __ldg(src + c);
+            av[c * cnt] = e[c];
           }
-          // L_ik = A_ik * inv(U_kk)
+        } else {
 #pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              l[3 * r + c] = a[3 * r] * d[c] + a[3 * r + 1] * d[3 + c] + a[3 * r + 2] * d[6 + c];
-#pragma unroll
-          for (int c = 0; c < 9; ++c) Lp[c * cnt] = l[c];
-          // A_ij -= L_ik * U_kj for the listed j
-          const int u1 = S.upd_ptr[lrow + k + 1];
-          for (int u = S.upd_ptr[lrow + k]; u < u1; ++u) {
-            const int64_t ds = S.upd_dst[u], ss = S.upd_src[u];
-            TF *Ap = lu + (ds >> 6);
-            const int dstr = (int)(ds & 63);
-            const TF *Up = lu + (ss >> 6);
-            const int sstr = (int)(ss & 63);
-            TF uu[9];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) uu[c] = ldcg(Up + c * sstr);
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-              for (int c = 0; c < 3; ++c)
-                Ap[(3 * r + c) * dstr] -=
-                    l[3 * r] * uu[c] + l[3 * r + 1] * uu[3 + c] + l[3 * r + 2] * uu[6 + c];
-          }
-        }
-        base += __popc(m);
-      }
-      if (ready) {
-        TF *Dp = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
-        TF a[9], o[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) a[c] = Dp[32 * c];
-        if (!inv3<TF>(a, o)) {
-          atomicCAS(&st->error, 0, (int32_t)OPM_ERR_ZERO_PIVOT);
-          atomicMin(&st->err_row, i);
+          for (int c = 0; c < 9; ++c) e[c] = av[c * cnt];
         }
 #pragma unroll
-        for (int c = 0; c < 9; ++c) Dp[32 * c] = o[c];
-        mine = true;
+        for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
       }
-      done |= __ballot_sync(0xffffffffu, ready);
-      __syncwarp();
+      base += __popc(m);
     }
-    signal(S, S.fflag, sl, sl, epoch);
   }
-  sweep_exit(st, epoch);
+  // ---- eliminate with the pivots k < i (Algorithm 2's updates of row i)
+  const int lrow = (i < n) ? __ldg(S.l_rp + i) : 0;
+  const int len = (i < n) ? __ldg(S.l_rp + i + 1) - lrow : 0;
+  int base = (s0 < n) ? __ldg(S.l_rp + s0) : 0;
+  const int maxlen = __reduce_max_sync(0xffffffffu, act ? len : 0);
+  for (int k = 0; k < maxlen; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, len > k);
+    if (act && len > k) {
+      const int cnt = __popc(m);
+      const int q = __popc(m & lt);
+      const int kc = __ldg(S.l_col + base + q);
+      TF *Lp = lu + 9ll * base + q;
+      const TF *Dk = lu + S.d_off + (int64_t)kSliceVals * (kc >> 5) + (kc & 31);
+      TF a[9], d[9], l[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        a[c] = Lp[c * cnt];
+        d[c] = __ldcg(Dk + 32 * c);
+      }
+      // L_ik = A_ik * inv(U_kk)
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          l[3 * r + c] = fma(a[3 * r], d[c], fma(a[3 * r + 1], d[3 + c], a[3 * r + 2] * d[6 + c]));
+#pragma unroll
+      for (int c = 0; c < 9; ++c) Lp[c * cnt] = l[c];
+      // A_ij -= L_ik * U_kj for the listed j
+      const int u1 = __ldg(S.upd_ptr + lrow + k + 1);
+      for (int u = __ldg(S.upd_ptr + lrow + k); u < u1; ++u) {
+        const int64_t ds = __ldg(S.upd_dst + u), ss = __ldg(S.upd_src + u);
+        TF *Ap = lu + (ds >> 6);
+        const int dstr = (int)(ds & 63);
+        const TF *Up = lu + (ss >> 6);
+        const int sstr = (int)(ss & 63);
+        TF uu[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) uu[c] = __ldcg(Up + c * sstr);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            TF *ap = Ap + (3 * r + c) * dstr;
+            *ap = fma(-l[3 * r], uu[c], fma(-l[3 * r + 1], uu[3 + c], fma(-l[3 * r + 2], uu[6 + c], *ap)));
+          }
+      }
+    }
+    base += __popc(m);
+  }
+  if (act) {
+    TF *Dp = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
+    TF a[9], o[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a[c] = Dp[32 * c];
+    if (!inv3<TF>(a, o)) {
+      atomicCAS(&st->error, 0, (int32_t)OPM_ERR_ZERO_PIVOT);
+      atomicMin(&st->err_row, i);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Dp[32 * c] = o[c];
+  }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(256) k_factor_phase(Sys S, int r0, int r1, const double *__restrict__ vals_user) {
+  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (sl > ((r1 - 1) >> 5)) return;
+  factor_rows<TF>(S, sl, r0, r1, vals_user);
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(1024) k_factor(Sys S, const double *__restrict__ vals_user) {
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int ph = 0; ph < S.nphases; ++ph) {
+    if (ph > 0) grid_sync(S.st, S.spin_limit_ns, S.skip_cta);
+    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
+    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W) factor_rows<TF>(S, sl, r0, r1, vals_user);
+  }
 }
 
 }  // namespace opm

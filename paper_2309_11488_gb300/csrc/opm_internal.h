@@ -30,7 +30,8 @@
 namespace opm {
 
 constexpr int kWarp = 32;
-constexpr int kTileRows = 256;  // rows per CTA of the static-tiled kernels
+constexpr int kTileRows = 1024;    // rows per CTA of the static-tiled kernels (256 threads x 4)
+constexpr int kSweepThreads = 1024;  // threads per CTA of the cooperative sweep kernels
 constexpr int kSliceVals = 288;  // 32 rows x 9 entries per Dinv slice
 constexpr int32_t kRunning = 0x7fffffff;
 
@@ -49,11 +50,11 @@ struct Analysis {
   std::vector<int64_t> a_csr_slot;            // per A block in permuted CSR order: slot in the factor values
   std::vector<int32_t> upd_ptr;               // per L block (CSR order of L) into the update lists
   std::vector<int64_t> upd_dst, upd_src;      // slots: A_ij -= L_ik * U_kj
-  // sweep dependencies: per slice, the distinct other slices its rows read
-  // (forward: L's columns, backward: U's), and per row the lanes of its own
-  // slice it reads
-  std::vector<int32_t> fdep_ptr, fdep, bdep_ptr, bdep;
-  std::vector<uint32_t> fmask, bmask;
+  // phases: maximal runs of consecutive (schedule-order) rows none of which
+  // reads another row of its run in either sweep; rows [phase_ptr[p],
+  // phase_ptr[p+1]) form phase p.  For level and colour orders the phases are
+  // exactly the levels and colours.
+  std::vector<int32_t> phase_ptr;
   int64_t d_off = 0;                          // first value of Dinv inside the factor values
   int64_t lu_vals = 0;                        // total factor values
   int32_t max_row_len = 0;
@@ -64,8 +65,9 @@ struct Analysis {
 opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
                    Analysis &an, int32_t *err_row);
 
-// Krylov scalars and control words, one per system, in device memory.
-struct DevState {
+// Krylov scalars and control words, one per system, in device memory.  The
+// grid-barrier counter and generation sit on cache lines of their own.
+struct alignas(128) DevState {
   double rho, rho_prev, alpha, omega, beta;
   double n0, tol;
   double rhv, ss, ts, tt, rr, rhr;
@@ -77,9 +79,10 @@ struct DevState {
   int32_t half;    // the last half step met the stopping rule
   int32_t error;   // device-detected error (opm_status) or 0
   int32_t err_row; // smallest permuted row with a singular pivot
-  uint32_t done, epoch;          // sweep kernels: CTAs finished, launch epoch
   uint32_t red_count;            // last-CTA reduction counter
-  int32_t pad[3];
+  alignas(128) uint32_t bar_count;  // grid barrier of the cooperative sweep kernels: arrivals
+  alignas(128) uint32_t bar_gen;    // and generation
+  int32_t pad[31];
 };
 
 }  // namespace opm

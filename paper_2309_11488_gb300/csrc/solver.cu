@@ -29,6 +29,8 @@ struct opm_solver {
   int grid_apply = 1, grid_factor = 1;
   int chunk = 8;
   cudaGraphExec_t chunk_exec = nullptr;
+  int chunk_launches = 0;  // kernel nodes in the chunk graph
+  bool cooperative = false;  // sweeps as one cooperative launch
   DevState *h_state = nullptr;  // pinned
   std::vector<void *> allocs;
   double *vals_stage = nullptr;   // caller's values when given from host
@@ -38,6 +40,7 @@ struct opm_solver {
   bool factors_ok = false;
   opm_timing timing{};
   cudaEvent_t ev[6] = {};
+  std::vector<cudaEvent_t> kev;  // per-kernel events inside the graph (profiling)
 };
 
 namespace {
@@ -105,7 +108,7 @@ template <typename... P, typename... A>
 cudaError_t launch_coop(void (*kern)(P...), int grid, cudaStream_t st, A... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kSweepThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -116,55 +119,124 @@ cudaError_t launch_coop(void (*kern)(P...), int grid, cudaStream_t st, A... args
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// CTAs of 8 warps covering the slices of rows [r0, r1)
+int phase_blocks(int r0, int r1) { return (((r1 - 1) >> 5) - (r0 >> 5) + 1 + 7) / 8; }
+
+// Schedules with at most this many phases run one launch per phase; more
+// phases run as one cooperative launch with grid barriers.
+constexpr int kMaxPhaseLaunches = 1024;
+
 template <typename TF>
-void launch_factor(opm_solver *h, const double *vals_user, cudaStream_t st) {
-  launch_coop(k_factor<TF>, h->grid_factor, st, h->sys, vals_user);
+int launch_factor(opm_solver *h, const double *vals_user, cudaStream_t st) {
+  const Sys &S = h->sys;
+  if (h->cooperative) {
+    launch_coop(k_factor<TF>, h->grid_factor, st, S, vals_user);
+    return 1;
+  }
+  const std::vector<int32_t> &pp = h->an.phase_ptr;
+  for (int p = 0; p < S.nphases; ++p)
+    k_factor_phase<TF><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], vals_user);
+  return S.nphases;
 }
 
 template <typename TF, int MODE>
-void launch_apply(opm_solver *h, const double *in, double *out, cudaStream_t st) {
-  launch_coop(k_apply<TF, MODE>, h->grid_apply, st, h->sys, in, out);
+int launch_apply(opm_solver *h, const double *in, double *out, cudaStream_t st) {
+  const Sys &S = h->sys;
+  if (h->cooperative) {
+    launch_coop(k_apply<TF, MODE>, h->grid_apply, st, S, in, out);
+    return 1;
+  }
+  const std::vector<int32_t> &pp = h->an.phase_ptr;
+  const int np = S.nphases;
+  for (int p = 0; p < np; ++p)
+    k_fwd_phase<TF, MODE><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], p == np - 1, in,
+                                                                            out);
+  for (int p = np - 2; p >= 0; --p)
+    k_bwd_phase<TF, MODE><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], out);
+  return 2 * np - 1;
 }
 
 template <int MODE>
-void launch_apply_p(opm_solver *h, const double *in, double *out, cudaStream_t st) {
-  if (h->fp32) launch_apply<float, MODE>(h, in, out, st);
-  else launch_apply<double, MODE>(h, in, out, st);
+int launch_apply_p(opm_solver *h, const double *in, double *out, cudaStream_t st) {
+  return h->fp32 ? launch_apply<float, MODE>(h, in, out, st) : launch_apply<double, MODE>(h, in, out, st);
 }
 
-void launch_iteration(opm_solver *h, cudaStream_t st) {
+// One BiCGStab iteration: 5 kernels.  With ev (6 events), the kernels are
+// bracketed by event-record nodes (external records, so that they are real
+// graph nodes rather than capture-internal dependencies) for per-kernel
+// timing.
+int launch_iteration(opm_solver *h, cudaStream_t st, cudaEvent_t *ev) {
   const int nb = h->ntiles;
-  launch_apply_p<kModeP>(h, nullptr, nullptr, st);
-  k_spmv_v<<<nb, 256, 0, st>>>(h->sys);
-  launch_apply_p<kModeS>(h, nullptr, nullptr, st);
-  k_spmv_t<<<nb, 256, 0, st>>>(h->sys);
+  auto mark = [&](int q) {
+    if (ev) cudaEventRecordWithFlags(ev[q], st, cudaEventRecordExternal);
+  };
+  int launches = 3;
+  mark(0);
+  launches += launch_apply_p<kModeP>(h, nullptr, nullptr, st);
+  mark(1);
+  k_spmv_v<<<nb, 1024, 0, st>>>(h->sys);
+  mark(2);
+  launches += launch_apply_p<kModeS>(h, nullptr, nullptr, st);
+  mark(3);
+  k_spmv_t<<<nb, 1024, 0, st>>>(h->sys);
+  mark(4);
   k_update<<<nb, 256, 0, st>>>(h->sys);
+  mark(5);
+  return launches;
 }
 
+const int kIterKernel[5] = {OPM_KERNEL_APPLY, OPM_KERNEL_SPMV, OPM_KERNEL_APPLY, OPM_KERNEL_SPMV,
+                            OPM_KERNEL_UPDATE};
+
+void add_kernel_time(opm_solver *h, int kind, cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+    h->timing.kernel_ms[kind] += ms;
+    h->timing.kernel_count[kind] += 1;
+  } else {
+    cudaGetLastError();
+  }
+}
+
+// Clears the error word and the grid-barrier counter before a sweep launch
+// that does not follow k_setup.
 __global__ void k_begin_factor(DevState *st) {
   st->error = 0;
   st->err_row = INT_MAX;
+  st->bar_count = 0;
 }
 
-// Largest co-resident grid of 256-thread CTAs for a kernel, capped by the
-// work (8 slices per CTA).
+// Largest co-resident grid of sweep CTAs for a kernel, capped by the work
+// (one slice per warp).
 template <typename K>
 int resident_grid(K kernel, int device, int items) {
   int sms = 1, occ = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kSweepThreads, 0) != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
   }
-  int want = std::max(1, (items + 7) / 8);
+  const int warps = kSweepThreads / 32;
+  int want = std::max(1, (items + warps - 1) / warps);
   return std::max(1, std::min(sms * occ, want));
 }
 
+// The sweep grids need only as many warps as the largest phase has slices:
+// fewer CTAs make the grid barrier cheaper.
+int max_phase_slices(const Analysis &an) {
+  int m = 1;
+  for (size_t p = 0; p + 1 < an.phase_ptr.size(); ++p) {
+    const int r0 = an.phase_ptr[p], r1 = an.phase_ptr[p + 1];
+    m = std::max(m, (r1 - 1) / kWarp - r0 / kWarp + 1);
+  }
+  return m;
+}
+
 template <typename TF>
-int apply_grid(int device, int ns) {
-  int g = resident_grid(k_apply<TF, kModeP>, device, ns);
-  g = std::min(g, resident_grid(k_apply<TF, kModeS>, device, ns));
-  return std::min(g, resident_grid(k_apply<TF, kModePlain>, device, ns));
+int apply_grid(int device, int slices) {
+  int g = resident_grid(k_apply<TF, kModeP>, device, slices);
+  g = std::min(g, resident_grid(k_apply<TF, kModeS>, device, slices));
+  return std::min(g, resident_grid(k_apply<TF, kModePlain>, device, slices));
 }
 
 opm_status build_graph(opm_solver *h) {
@@ -173,7 +245,9 @@ opm_status build_graph(opm_solver *h) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int it = 0; it < h->chunk; ++it) launch_iteration(h, cap);
+    h->chunk_launches = 0;
+    for (int it = 0; it < h->chunk; ++it)
+      h->chunk_launches += launch_iteration(h, cap, h->kev.empty() ? nullptr : &h->kev[6 * it]);
     e = cudaStreamEndCapture(cap, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->chunk_exec, g, 0);
@@ -227,13 +301,14 @@ opm_status factor_impl(opm_solver *h, const double *vals) {
   }
   k_begin_factor<<<1, 1, 0, h->stream>>>(h->sys.st);
   CK(cudaEventRecord(h->ev[4], h->stream));
-  if (h->fp32) launch_factor<float>(h, dv, h->stream);
-  else launch_factor<double>(h, dv, h->stream);
+  const int nl = h->fp32 ? launch_factor<float>(h, dv, h->stream) : launch_factor<double>(h, dv, h->stream);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[5], h->stream));
+  h->timing.launches += 1 + nl;
   opm_status s = read_state(h);
   if (s != OPM_OK) return s;
   cudaEventElapsedTime(&h->timing.factor_ms, h->ev[4], h->ev[5]);
+  if (h->opt.profile_kernels) add_kernel_time(h, OPM_KERNEL_FACTOR, h->ev[4], h->ev[5]);
   if (h->h_state->error != 0) {
     int32_t r = h->h_state->err_row;
     h->last_err_row = (r >= 0 && r < h->n) ? h->an.perm[r] : -1;
@@ -274,6 +349,8 @@ void opm_destroy(opm_handle h) {
   if (h->h_state) cudaFreeHost(h->h_state);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : h->kev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -289,6 +366,7 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR) return OPM_ERR_ARG;
   if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
   if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
+  if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;
 
   opm_solver *h = new (std::nothrow) opm_solver();
   if (!h) return OPM_ERR_OOM;
@@ -349,10 +427,9 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   S.u_off = 9 * an.nnz_l;
   S.d_off = an.d_off;
   S.spin_limit_ns = (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
-  S.skip_item = o.debug_skip_item;
+  S.skip_cta = o.debug_skip_item;
   int32_t *p_perm, *p_arp, *p_acol, *p_asrc, *p_lrp, *p_lcol, *p_urp, *p_ucol, *p_upd;
-  int32_t *p_fdp, *p_fd, *p_bdp, *p_bd;
-  uint32_t *p_fm, *p_bm;
+  int32_t *p_ph;
   int64_t *p_adst, *p_ud, *p_us;
 #define UP(ptr, vec) \
   if ((s = upload(h, &ptr, vec)) != OPM_OK) return fail(s)
@@ -368,19 +445,10 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   UP(p_upd, an.upd_ptr);
   UP(p_ud, an.upd_dst);
   UP(p_us, an.upd_src);
-  UP(p_fdp, an.fdep_ptr);
-  UP(p_fd, an.fdep);
-  UP(p_bdp, an.bdep_ptr);
-  UP(p_bd, an.bdep);
-  UP(p_fm, an.fmask);
-  UP(p_bm, an.bmask);
+  UP(p_ph, an.phase_ptr);
 #undef UP
-  S.fdep_ptr = p_fdp;
-  S.fdep = p_fd;
-  S.bdep_ptr = p_bdp;
-  S.bdep = p_bd;
-  S.fmask = p_fm;
-  S.bmask = p_bm;
+  S.phase_ptr = p_ph;
+  S.nphases = (int32_t)an.phase_ptr.size() - 1;
   S.perm = p_perm;
   S.a_rp = p_arp;
   S.a_col = p_acol;
@@ -413,26 +481,23 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   for (double **pv : vecs)
     if ((s = dalloc(h, pv, 3 * (size_t)nb)) != OPM_OK) return fail(s);
   if ((s = dalloc(h, &S.partials, 4 * (size_t)h->ntiles)) != OPM_OK) return fail(s);
-  if ((s = dalloc(h, &S.fflag, (size_t)h->nslices)) != OPM_OK) return fail(s);
-  if ((s = dalloc(h, &S.bflag, (size_t)h->nslices)) != OPM_OK) return fail(s);
   if ((s = dalloc(h, &S.st, 1)) != OPM_OK) return fail(s);
-  if (cudaMemsetAsync(S.fflag, 0, sizeof(uint32_t) * std::max(1, h->nslices), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(S.bflag, 0, sizeof(uint32_t) * std::max(1, h->nslices), h->stream) != cudaSuccess)
-    return fail(OPM_ERR_CUDA);
   {
     DevState init{};
     init.status = OPM_OK;
-    init.epoch = 1;
     *h->h_state = init;
     if (cudaMemcpyAsync(S.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
       return fail(OPM_ERR_CUDA);
   }
+  h->cooperative = o.sweep_launch == OPM_SWEEP_COOPERATIVE ||
+                   (o.sweep_launch == OPM_SWEEP_AUTO && S.nphases > kMaxPhaseLaunches);
+  const int mps = max_phase_slices(an);
   if (h->fp32) {
-    h->grid_apply = apply_grid<float>(h->device, h->nslices);
-    h->grid_factor = resident_grid(k_factor<float>, h->device, h->nslices);
+    h->grid_apply = apply_grid<float>(h->device, mps);
+    h->grid_factor = resident_grid(k_factor<float>, h->device, mps);
   } else {
-    h->grid_apply = apply_grid<double>(h->device, h->nslices);
-    h->grid_factor = resident_grid(k_factor<double>, h->device, h->nslices);
+    h->grid_apply = apply_grid<double>(h->device, mps);
+    h->grid_factor = resident_grid(k_factor<double>, h->device, mps);
   }
   // free the host copies the device now holds (keep perm and the factor slots)
   std::vector<int32_t>().swap(an.a_col);
@@ -443,11 +508,16 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   std::vector<int32_t>().swap(an.upd_ptr);
   std::vector<int64_t>().swap(an.upd_dst);
   std::vector<int64_t>().swap(an.upd_src);
-  std::vector<int32_t>().swap(an.fdep);
-  std::vector<int32_t>().swap(an.bdep);
-  std::vector<uint32_t>().swap(an.fmask);
-  std::vector<uint32_t>().swap(an.bmask);
 
+
+  if (o.profile_kernels && nb > 0) {
+    h->kev.assign((size_t)6 * h->chunk, nullptr);
+    for (auto &e : h->kev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OPM_ERR_CUDA);
+      }
+  }
   if (nb > 0 && (s = build_graph(h)) != OPM_OK) return fail(s);
   s = factor_impl(h, nb > 0 ? vals : nullptr);
   if (s == OPM_ERR_ZERO_PIVOT) {
@@ -484,15 +554,26 @@ opm_status opm_bicgstab_solve(opm_handle h, const double *b, double *x, double r
   k_setup<<<h->ntiles, 256, 0, st>>>(h->sys, db, rtol, maxit);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev[1], st));
+  h->timing.launches += 1;
   if ((s = read_state(h)) != OPM_OK) return s;
   while (h->h_state->status == kRunning && h->h_state->error == 0) {
+    const int k_before = h->h_state->k;
     CK(cudaGraphLaunch(h->chunk_exec, st));
+    h->timing.launches += h->chunk_launches;
     if ((s = read_state(h)) != OPM_OK) return s;
+    if (!h->kev.empty()) {
+      // iterations of this chunk that did work
+      int ran = h->chunk;
+      if (h->h_state->status != kRunning || h->h_state->error != 0)
+        ran = std::max(0, std::min(h->chunk, h->h_state->iters - k_before + 1));
+      for (int it = 0; it < ran; ++it)
+        for (int q = 0; q < 5; ++q) add_kernel_time(h, kIterKernel[q], h->kev[6 * it + q], h->kev[6 * it + q + 1]);
+    }
   }
   CK(cudaEventRecord(h->ev[2], st));
   int32_t status = h->h_state->error != 0 ? h->h_state->error : h->h_state->status;
   if (status == OPM_OK || status == OPM_NOT_CONVERGED) {
-    k_finish<<<h->ntiles, 256, 0, st>>>(h->sys, db, dx);
+    k_finish<<<h->ntiles, 1024, 0, st>>>(h->sys, db, dx);
     CK(cudaGetLastError());
     if (!x_dev) CK(cudaMemcpyAsync(x, dx, vbytes, cudaMemcpyDeviceToHost, st));
   } else if (x_dev) {
@@ -501,7 +582,12 @@ opm_status opm_bicgstab_solve(opm_handle h, const double *b, double *x, double r
     memset(x, 0, vbytes);
   }
   CK(cudaEventRecord(h->ev[3], st));
+  if (status == OPM_OK || status == OPM_NOT_CONVERGED) h->timing.launches += 1;
   if ((s = read_state(h)) != OPM_OK) return s;
+  if (h->opt.profile_kernels) {
+    add_kernel_time(h, OPM_KERNEL_SETUP, h->ev[0], h->ev[1]);
+    if (status == OPM_OK || status == OPM_NOT_CONVERGED) add_kernel_time(h, OPM_KERNEL_FINISH, h->ev[2], h->ev[3]);
+  }
   cudaEventElapsedTime(&h->timing.setup_ms, h->ev[0], h->ev[1]);
   cudaEventElapsedTime(&h->timing.iterate_ms, h->ev[1], h->ev[2]);
   cudaEventElapsedTime(&h->timing.finish_ms, h->ev[2], h->ev[3]);
@@ -519,8 +605,9 @@ opm_status opm_spmv(opm_handle h, const double *x, double *y) {
   const bool y_dev = is_device_ptr(y);
   double *dy = y_dev ? y : h->vec_out;
   k_gather<<<h->ntiles, 256, 0, h->stream>>>(h->sys, dx, h->sys.w);
-  k_spmv_plain<<<h->ntiles, 256, 0, h->stream>>>(h->sys, h->sys.w, dy);
+  k_spmv_plain<<<h->ntiles, 1024, 0, h->stream>>>(h->sys, h->sys.w, dy);
   CK(cudaGetLastError());
+  h->timing.launches += 2;
   if (!y_dev) CK(cudaMemcpyAsync(y, dy, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return OPM_OK;
@@ -537,9 +624,10 @@ opm_status opm_ilu_apply(opm_handle h, const double *r, double *z) {
   double *dz = z_dev ? z : h->vec_out;
   k_begin_factor<<<1, 1, 0, h->stream>>>(h->sys.st);
   k_gather<<<h->ntiles, 256, 0, h->stream>>>(h->sys, dr, h->sys.w);
-  launch_apply_p<kModePlain>(h, h->sys.w, h->sys.t, h->stream);
+  const int nl = launch_apply_p<kModePlain>(h, h->sys.w, h->sys.t, h->stream);
   k_scatter<<<h->ntiles, 256, 0, h->stream>>>(h->sys, h->sys.t, dz);
   CK(cudaGetLastError());
+  h->timing.launches += 3 + nl;
   if (!z_dev) CK(cudaMemcpyAsync(z, dz, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
   if ((s = read_state(h)) != OPM_OK) return s;
   if (h->h_state->error != 0) return (opm_status)h->h_state->error;
@@ -558,6 +646,8 @@ opm_status opm_get_info(opm_handle h, opm_info *info) {
   info->nnzb_lower = h->an.nnz_l;
   info->nnzb_upper = h->an.nnz_u;
   info->device_bytes = h->dev_bytes;
+  info->nphases = h->sys.nphases;
+  info->reserved = 0;
   return OPM_OK;
 }
 
@@ -600,6 +690,16 @@ opm_status opm_get_factors(opm_handle h, double *lu, double *dinv) {
 opm_status opm_get_timing(opm_handle h, opm_timing *t) {
   if (!h || !t) return OPM_ERR_ARG;
   *t = h->timing;
+  return OPM_OK;
+}
+
+opm_status opm_reset_timing(opm_handle h) {
+  if (!h) return OPM_ERR_ARG;
+  h->timing.launches = 0;
+  for (int k = 0; k < OPM_KERNEL_COUNT; ++k) {
+    h->timing.kernel_ms[k] = 0.0;
+    h->timing.kernel_count[k] = 0;
+  }
   return OPM_OK;
 }
 

@@ -3,6 +3,7 @@
 // lists.  Runs once per sparsity pattern; the paper reuses its analysis for
 // the whole simulation because the pattern never changes (Section 4.4).
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <numeric>
 #include <utility>
@@ -234,32 +235,26 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     }
   }
 
-  // ---- sweep dependencies per slice and per row
-  auto sweep_deps = [&](bool lower, std::vector<int32_t> &ptr,
-                        std::vector<int32_t> &dep, std::vector<uint32_t> &mask) {
-    const int32_t ns = (n + kWarp - 1) / kWarp;
-    ptr.assign((size_t)ns + 1, 0);
-    dep.clear();
-    mask.assign((size_t)n, 0u);
-    std::vector<int32_t> tmpd;
-    for (int32_t sl = 0; sl < ns; ++sl) {
-      const int32_t r0 = sl * kWarp, r1 = std::min(n, r0 + kWarp);
-      tmpd.clear();
-      for (int32_t i = r0; i < r1; ++i)
-        for (int64_t c = arp[i]; c < arp[i + 1]; ++c) {
-          const int32_t j = pcol[c];
-          if (lower ? !(j < i) : !(j > i)) continue;
-          if (j >= r0 && j < r1) mask[i] |= 1u << (j - r0);
-          else tmpd.push_back(j / kWarp);
-        }
-      std::sort(tmpd.begin(), tmpd.end());
-      tmpd.erase(std::unique(tmpd.begin(), tmpd.end()), tmpd.end());
-      dep.insert(dep.end(), tmpd.begin(), tmpd.end());
-      ptr[sl + 1] = (int32_t)dep.size();
+  // ---- phases.  Row i opens a new phase when it reads a row of the current
+  // run in the forward sweep (an L column >= start) or when an earlier row of
+  // the run reads it in the backward sweep (a U column of the run == i).
+  an.phase_ptr.assign(1, 0);
+  {
+    int32_t start = 0, limit = INT32_MAX;
+    for (int32_t i = 0; i < n; ++i) {
+      bool split = i >= limit;
+      for (int64_t c = arp[i]; c < arp[i + 1] && !split; ++c)
+        if (pcol[c] < i && pcol[c] >= start) split = true;
+      if (split && i > start) {
+        an.phase_ptr.push_back(i);
+        start = i;
+        limit = INT32_MAX;
+      }
+      for (int64_t c = arp[i]; c < arp[i + 1]; ++c)
+        if (pcol[c] > i) limit = std::min(limit, pcol[c]);
     }
-  };
-  sweep_deps(true, an.fdep_ptr, an.fdep, an.fmask);
-  sweep_deps(false, an.bdep_ptr, an.bdep, an.bmask);
+    if (n > 0) an.phase_ptr.push_back(n);
+  }
 
   // ---- ILU0 update lists: for L block (i,k), every j > k present in row i
   // and in row k gives A_ij -= L_ik * U_kj (Algorithm 2's inner loop).

@@ -31,29 +31,41 @@ OPM_ERR_TIMEOUT = -8
 OPM_ERR_CUDA = -9
 
 SCHEDULES = {"auto": 0, "natural": 1, "level": 2, "colour": 3}
+SWEEPS = {"auto": 0, "per_phase": 1, "cooperative": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
 # every symbol include/opm_bsr.h declares
 EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicgstab_solve",
            "opm_spmv", "opm_ilu_apply", "opm_destroy", "opm_status_str", "opm_last_error_row",
-           "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing"]
+           "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
+           "opm_reset_timing"]
 
 
 class opm_options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("precision", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("chunk", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
-                ("debug_skip_item", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("debug_skip_item", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
+                ("sweep_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class opm_info(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int32), ("schedule", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("nsets", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
-                ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("nphases", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+KERNELS = ["factor", "apply", "spmv", "update", "setup", "finish"]
 
 
 class opm_timing(ctypes.Structure):
     _fields_ = [("setup_ms", ctypes.c_float), ("iterate_ms", ctypes.c_float),
-                ("finish_ms", ctypes.c_float), ("factor_ms", ctypes.c_float)]
+                ("finish_ms", ctypes.c_float), ("factor_ms", ctypes.c_float),
+                ("launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double * 6),
+                ("kernel_count", ctypes.c_int64 * 6)]
+
+    def kernels(self):
+        return {k: (self.kernel_ms[q], self.kernel_count[q]) for q, k in enumerate(KERNELS)}
 
 
 _lib = None
@@ -93,6 +105,8 @@ def lib() -> ctypes.CDLL:
         L.opm_get_factors.restype = i32
         L.opm_get_timing.argtypes = [vp, ctypes.POINTER(opm_timing)]
         L.opm_get_timing.restype = i32
+        L.opm_reset_timing.argtypes = [vp]
+        L.opm_reset_timing.restype = i32
         _lib = L
     return _lib
 
@@ -141,6 +155,8 @@ def opm_options_default(**kw) -> opm_options:
             v = SCHEDULES[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "sweep_launch" and isinstance(v, str):
+            v = SWEEPS[v]
         setattr(o, k, v)
     return o
 
@@ -222,15 +238,20 @@ def opm_get_timing(h: Handle) -> opm_timing:
     return t
 
 
+def opm_reset_timing(h: Handle) -> int:
+    return lib().opm_reset_timing(h.ptr)
+
+
 class Solver:
     """Convenience owner of one handle (context manager)."""
 
     def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
-                 spin_limit_us=0, debug_skip_item=-1):
+                 spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto"):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
-                                           spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item)
+                                           spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item,
+                                           profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch)
         self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options)
         self.nb = nb
 
@@ -270,6 +291,9 @@ class Solver:
 
     def timing(self):
         return opm_get_timing(self.h)
+
+    def reset_timing(self):
+        return opm_reset_timing(self.h)
 
     def close(self):
         opm_destroy(self.h)

@@ -83,16 +83,23 @@ def test_spmv_config3_full_size(c3):
     check_spmv(c3, "colour")
 
 
+SWEEPS = ["per_phase", "cooperative"]
+
+
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", list(SMALL))
 @pytest.mark.parametrize("schedule", ["natural", "level", "colour"])
-def test_permutation_and_factors(name, schedule):
+def test_permutation_and_factors(name, schedule, sweep):
     s = SMALL[name]()
     if schedule == "natural" and s.nb > 2000:
         pytest.skip("natural order is a sequential chain")
     perm, nsets, prow, pcol, pval, fac = ref_same_order(s, schedule)
-    with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, schedule=schedule) as sv:
+    with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, schedule=schedule, sweep_launch=sweep) as sv:
         np.testing.assert_array_equal(sv.permutation(), perm)
-        assert sv.info().nsets == nsets
+        info = sv.info()
+        assert info.nsets == nsets
+        if schedule != "natural":
+            assert info.nphases == nsets  # phases are exactly the levels / colours
         lu, dinv = sv.factors()
     check_factors(s.nb, prow, pcol, fac, lu, dinv, 1e-12)
 
@@ -118,26 +125,27 @@ def test_factors_config3_full_size(c3, schedule):
     check_factors(c3.nb, prow, pcol, fac, lu, dinv, 1e-12)
 
 
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", ["c1", "ragged33", "long_rows", "tree"])
 @pytest.mark.parametrize("schedule", ["level", "colour"])
-def test_ilu_apply(name, schedule):
+def test_ilu_apply(name, schedule, sweep):
     s = SMALL[name]()
     perm, nsets, prow, pcol, pval, fac = ref_same_order(s, schedule)
     r = synth.uniform(synth.stream_key(9, 9), np.arange(3 * s.nb, dtype=np.uint64), -1, 1)
     zp = O.ilu_apply(s.nb, prow, pcol, fac, r.reshape(-1, 3)[perm].ravel())
     z_ref = np.empty_like(zp)
     z_ref.reshape(-1, 3)[perm] = zp.reshape(-1, 3)
-    with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, schedule=schedule) as sv:
+    with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, schedule=schedule, sweep_launch=sweep) as sv:
         z = sv.ilu_apply(r)
     np.testing.assert_allclose(z, z_ref, rtol=1e-11, atol=1e-12 * np.abs(z_ref).max())
 
 
-def check_solve(s, schedule, rtol, precision="fp64", maxit=200, xtol=1e-8):
+def check_solve(s, schedule, rtol, precision="fp64", maxit=200, xtol=1e-8, sweep="auto"):
     b = rhs(s)
     x_ref, res, perm, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, rtol, maxit, schedule,
                                          f32=(precision == "fp32"))
     with opm.Solver(s.nb, dev(s.rowptr), dev(s.colidx), dev(s.vals), schedule=schedule,
-                    precision=precision) as sv:
+                    precision=precision, sweep_launch=sweep) as sv:
         xd, st, it, relres = sv.solve(dev(b), rtol=rtol, maxit=maxit)
         x = xd.cpu().numpy()
     assert st == res.status == 0
@@ -154,10 +162,11 @@ def check_solve(s, schedule, rtol, precision="fp64", maxit=200, xtol=1e-8):
     return it
 
 
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", list(SMALL))
 @pytest.mark.parametrize("schedule", ["level", "colour"])
-def test_solve_small(name, schedule):
-    check_solve(SMALL[name](), schedule, 1e-8)
+def test_solve_small(name, schedule, sweep):
+    check_solve(SMALL[name](), schedule, 1e-8, sweep=sweep)
 
 
 @pytest.mark.parametrize("rtol", [1e-2, 1e-6])
@@ -169,9 +178,10 @@ def test_solve_config2_level(c2):
     check_solve(c2, "level", 1e-6)
 
 
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("schedule", ["level", "colour"])
-def test_solve_config3_full_size(c3, schedule):
-    check_solve(c3, schedule, 1e-3)
+def test_solve_config3_full_size(c3, schedule, sweep):
+    check_solve(c3, schedule, 1e-3, sweep=sweep)
 
 
 def test_solve_natural_small():
@@ -260,12 +270,14 @@ def test_zero_pivot_reports_row():
 
 
 def test_bounded_wait_expires_with_timeout_status():
-    # the sweep item with index 3 is never signalled: waits on it must expire
-    # after the 20 ms bound and report OPM_ERR_TIMEOUT, and the context stays usable
+    # CTA 3 of the factorisation never arrives at the grid barrier: the other
+    # CTAs' waits must expire after the 20 ms bound and report OPM_ERR_TIMEOUT,
+    # and the context stays usable
     s = synth.config2()
     st, h = opm.opm_bsr_create(s.nb, s.rowptr, s.colidx, s.vals,
-                               opm.opm_options_default(schedule="level", spin_limit_us=20000,
-                                                       debug_skip_item=3), check=False)
+                               opm.opm_options_default(schedule="colour", spin_limit_us=20000,
+                                                       debug_skip_item=3, sweep_launch="cooperative"),
+                               check=False)
     try:
         assert st == opm.OPM_ERR_TIMEOUT
     finally:
