@@ -235,6 +235,30 @@ opm_status opm_get_timing(opm_handle h, opm_timing *t);
 /* Zero the launch counter and the per-kernel accumulators. */
 opm_status opm_reset_timing(opm_handle h);
 
+/*
+ * Allocation-free true residual (the paper has no counterpart: this is a
+ * library convenience).  For callers that cannot allocate device memory at
+ * the call site -- code running inside a simulator's own device-memory
+ * arena or under a fixed memory budget, or in a process whose allocations
+ * must all go through an allocator this library does not see -- it computes
+ * r = b - A x and norms[0] = ||b - A x||_2, norms[1] = ||b||_2 on the
+ * caller's own BSR arrays, without a handle and without allocating.
+ *   nb <= 2,097,152 block rows, else OPM_ERR_ARG; rowptr, colidx, vals (the
+ *   layout of opm_bsr_create), x, b, r (3*nb doubles) and norms (2 doubles)
+ *   must all be device memory of the current device, else OPM_ERR_ARG.
+ *   Work is issued on stream (NULL = default stream) and has completed when
+ *   the call returns.  Returns OPM_OK, OPM_ERR_ARG or OPM_ERR_CUDA.
+ * Its scratch is a fixed 131,328-byte array in device memory that every GPU
+ * using the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.
+ */
+opm_status opm_bsr_residual_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
+                                    const double *vals, const double *x, const double *b, double *r,
+                                    double *norms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libopm_bsr.so")
-SOURCES = ["solver.cu", "symbolic.cpp"]
+SOURCES = ["solver.cu", "symbolic.cpp", "noalloc.cu"]
 HEADERS = ["kernels.cuh", "opm_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -39,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not os.path.isdir(cuda_lib):
         cuda_lib = "/usr/local/cuda/lib64"
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "--threads", "2",
+    cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "--threads", "3",
            "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
            "-Xlinker", f"-rpath,{cuda_lib}", "-o", tmp]
     if verbose:

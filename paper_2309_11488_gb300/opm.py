@@ -38,7 +38,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicgstab_solve",
            "opm_spmv", "opm_ilu_apply", "opm_destroy", "opm_status_str", "opm_last_error_row",
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
-           "opm_reset_timing"]
+           "opm_reset_timing", "opm_bsr_residual_noalloc"]
 
 
 class opm_options(ctypes.Structure):
@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.opm_get_timing.restype = i32
         L.opm_reset_timing.argtypes = [vp]
         L.opm_reset_timing.restype = i32
+        L.opm_bsr_residual_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.opm_bsr_residual_noalloc.restype = i32
         _lib = L
     return _lib
 
@@ -240,6 +242,16 @@ def opm_get_timing(h: Handle) -> opm_timing:
 
 def opm_reset_timing(h: Handle) -> int:
     return lib().opm_reset_timing(h.ptr)
+
+
+def opm_bsr_residual_noalloc(nb, rowptr, colidx, vals, x, b, r, norms, stream=None) -> int:
+    """r = b - A x and norms = (||b - A x||, ||b||) on device arrays, without
+    allocating (see include/opm_bsr.h)."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    return lib().opm_bsr_residual_noalloc(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
+                                          _ptr(vals, np.float64), _ptr(x, np.float64), _ptr(b, np.float64),
+                                          _ptr(r, np.float64), _ptr(norms, np.float64), stream)
 
 
 class Solver:
