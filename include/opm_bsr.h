@@ -46,6 +46,7 @@ extern "C" {
 #endif
 
 typedef struct opm_solver *opm_handle; /* opaque, owned by the library */
+typedef struct opm_batch_s *opm_batch; /* opaque set of handles solved together */
 
 typedef enum {
   OPM_OK = 0,
@@ -92,8 +93,9 @@ typedef struct opm_options {
   int32_t schedule;      /* OPM_SCHED_*                                       */
   int32_t precision;     /* OPM_PREC_*                                        */
   void *stream;          /* cudaStream_t to issue work on; NULL = default     */
-  int32_t chunk;         /* BiCGStab iterations per graph launch between two
-                            reads of the device status word; 0 = default (8)  */
+  int32_t chunk;         /* BiCGStab iterations per body of the device-side
+                            solve loop (the loop condition is tested after
+                            each body); 0 = default (2)                      */
   int32_t spin_limit_us; /* bound of every device-side wait in microseconds;
                             0 = default (2,000,000)                           */
   int32_t debug_skip_item; /* test hook, -1 = off: the CTA with this index
@@ -219,12 +221,14 @@ enum {
   OPM_KERNEL_COUNT = 6
 };
 
-/* Device time, in milliseconds, of the last solve's phases and of the last
- * factorisation, measured with CUDA events on the handle's stream; the
+/* Device time, in milliseconds, of the last solve (iterate_ms: setup,
+ * iterations and true residual; setup_ms and finish_ms are 0) and of the
+ * last factorisation, measured with CUDA events on the handle's stream; the
  * number of kernels the handle has launched (graph nodes included); and,
  * with opm_options.profile_kernels, per-kernel device time and launch counts
  * accumulated over the iterations that did work since the last
- * opm_reset_timing. */
+ * opm_reset_timing (the iterations then run from a host loop over graphs
+ * with event nodes instead of the device-side loop). */
 typedef struct opm_timing {
   float setup_ms, iterate_ms, finish_ms, factor_ms;
   int64_t launches;
@@ -234,6 +238,55 @@ typedef struct opm_timing {
 opm_status opm_get_timing(opm_handle h, opm_timing *t);
 /* Zero the launch counter and the per-kernel accumulators. */
 opm_status opm_reset_timing(opm_handle h);
+
+/*
+ * Asynchronous refactor + solve (the paper's per-Newton-step pair, Section
+ * 4.4 and 4.2) for serving loops: enqueues, on the handle's stream and
+ * without waiting, an optional refactorisation with vals (device, 9*nnzb
+ * doubles; NULL = keep the factors) and a solve of A x = b (b, x device,
+ * 3*nb doubles, caller's order).  The pointers must stay valid and
+ * untouched until opm_solve_wait returns.  While a launch is pending the
+ * handle accepts only opm_solve_ready and opm_solve_wait.
+ * opm_solve_ready returns 1 when the work has completed (or none is
+ * pending), else 0.  opm_solve_wait blocks until completion and returns
+ * what opm_bicgstab_solve would (a singular pivot of the refactorisation is
+ * returned as OPM_ERR_ZERO_PIVOT).  Not available with profile_kernels.
+ */
+opm_status opm_solve_launch(opm_handle h, const double *vals, const double *b, double *x, double rtol,
+                            int32_t maxit);
+int32_t opm_solve_ready(opm_handle h);
+opm_status opm_solve_wait(opm_handle h, int32_t *iters, double *relres);
+
+/*
+ * Batches: many independent systems (distinct handles of one precision on
+ * one device) factorised and solved by the same kernel launches, each
+ * system with its own convergence state; a system that has converged skips
+ * its work while the others continue.  Every system's arithmetic, including
+ * the order of every reduction, is the same as when its handle is used
+ * alone, so results are bitwise identical.  A batch uses the member
+ * handles' device data and must be destroyed before them; members must not
+ * be used on their own while a batch call on them runs.  Work goes on the
+ * stream of opt (NULL = default stream); opt's schedule and precision are
+ * ignored (the members fix them).
+ *   opm_batch_factor: vals[i] (host or device, NULL = refactor the values
+ *     system i holds; vals itself may be NULL).
+ *   opm_batch_solve: b[i], x[i] host or device; rtol[i] (rtol may be NULL =
+ *     1e-2 for all); per-system iters, relres and st (each may be NULL).
+ *   Both return the first negative per-system status, else
+ *   OPM_NOT_CONVERGED if a system did not converge, else OPM_OK.
+ *   opm_batch_launch / _ready / _wait: the asynchronous form of an optional
+ *   refactorisation (vals NULL = none) followed by a solve; device pointers
+ *   only, valid until opm_batch_wait returns.
+ */
+opm_status opm_batch_create(int32_t nsys, const opm_handle *hs, const opm_options *opt, opm_batch *out);
+opm_status opm_batch_factor(opm_batch b, const double *const *vals, opm_status *st);
+opm_status opm_batch_solve(opm_batch b, const double *const *bv, double *const *xv, const double *rtol,
+                           int32_t maxit, int32_t *iters, double *relres, opm_status *st);
+opm_status opm_batch_launch(opm_batch b, const double *const *vals, const double *const *bv,
+                            double *const *xv, const double *rtol, int32_t maxit);
+int32_t opm_batch_ready(opm_batch b);
+opm_status opm_batch_wait(opm_batch b, int32_t *iters, double *relres, opm_status *st);
+void opm_batch_destroy(opm_batch b);
 
 /*
  * Allocation-free true residual (the paper has no counterpart: this is a

@@ -1,24 +1,30 @@
 // sm_103a kernels of the BSR ILU0-BiCGStab path.
 //
-//  * k_spmv_*      blocked SpMV, y = A x (Section 4.3), one lane per block row
-//                  on the warp-sliced layout, with the dot products the solver
-//                  needs fused into its epilogue.
-//  * k_factor      ILU0 decomposition (Algorithm 2) of the permuted matrix,
-//                  fused with the value permutation (Algorithm 3's index copy).
-//  * k_apply       ILU0 application (Algorithm 1): forward and backward block
-//                  substitution in one launch, fused with the BiCGStab vector
-//                  update that produces its right-hand side.
-//  * k_update      x and r updates of BiCGStab plus the next reductions.
+//  * k_spmv_*        blocked SpMV, y = A x (Section 4.3), one lane per block
+//                    row on the warp-sliced layout, with the dot products the
+//                    solver needs fused into the epilogue.
+//  * k_factor*       ILU0 decomposition (Algorithm 2) of the permuted matrix,
+//                    fused with the value permutation (Algorithm 3's copy).
+//  * k_fwd/bwd_phase ILU0 application (Algorithm 1): forward and backward
+//                    block substitution, phase by phase, fused with the
+//                    BiCGStab update that forms the right-hand side.
+//  * k_update        x and r updates of BiCGStab and the next reductions.
 //
-// The triangular kernels replace the paper's one launch per colour or level
-// (Section 4.4) by one cooperative launch per preconditioner application (or
-// factorisation) that walks the colours or levels with a bounded grid
-// barrier between them.
+// Every kernel works on a batch of independent systems described in device
+// memory (a single solve is a batch of one).  Work is split per system into
+// fixed units -- 32-row slices for the sweeps, 1024-row tiles for the
+// row-parallel kernels -- so a system's arithmetic, including the order of
+// every reduction, is the same alone and inside any batch.
 //
-// Reductions are deterministic: every static-tiled kernel reduces its 256
-// rows in a fixed butterfly, writes one partial per tile, and the last CTA to
-// finish (atomic counter) sums the partials in index order and runs the
-// scalar part of BiCGStab (alpha, omega, beta, the stopping rule).
+// Phases: the schedule's row order is cut into maximal runs of rows none of
+// which reads another row of its run (the levels or the colours, Section
+// 4.4).  The sweeps walk the phases in order, either one launch per phase
+// or one cooperative launch with a bounded grid barrier between phases.
+//
+// Reductions: one partial per tile in a fixed butterfly; the last CTA of a
+// system to finish (atomic counter) sums that system's partials in tile
+// order and runs the scalar part of BiCGStab (alpha, omega, beta, the
+// stopping rule).
 #pragma once
 
 #include <cstdint>
@@ -29,8 +35,9 @@ namespace opm {
 
 enum SweepMode { kModePlain = 0, kModeP = 1, kModeS = 2 };
 
+// One system's device data.  The last group of fields is set per call.
 struct Sys {
-  int32_t n, nslices;
+  int32_t n, nslices, ntiles, nphases;
   const int32_t *perm;
   const int32_t *a_rp, *a_col, *a_src;
   const int64_t *a_dst;
@@ -42,12 +49,34 @@ struct Sys {
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
   void *y;   // forward intermediate (factor precision)
-  const int32_t *phase_ptr;
-  int32_t nphases;
   double *partials;
   DevState *st;
+  // per call
+  const double *b_in;    // right-hand side, or the input of spmv / ilu_apply (caller's order)
+  double *x_out;         // solution, or the output of spmv / ilu_apply (caller's order)
+  const double *vals_in; // new matrix values for the factorisation (NULL: refactor A)
+  double rtol;
+  int32_t maxit;
+  int32_t pad;
+};
+
+// A launchable set of systems (kernel parameter).
+struct Batch {
+  const Sys *sys;         // [nsys]
+  const int4 *ent;        // sweep work: (system, slice, first row, last row + 1 | last-phase bit 31)
+  const int32_t *fwd_ptr; // [nphases + 1]: forward entries of phase c
+  const int32_t *bwd_ptr; // [nphases + 1]: backward entries of phase c
+  const int2 *tiles;      // (system, tile) for the row-parallel kernels
+  uint32_t *bar;          // grid barrier: arrivals at bar[0], generation at bar[32]
+  int32_t nsys, nphases, ntiles;
+  int32_t skip_cta;       // test hook: this CTA never arrives at grid barriers (-1: off)
   uint64_t spin_limit_ns;
-  int32_t skip_cta;  // test hook: this CTA never arrives at grid barriers (-1: off)
+};
+
+// Per-system outcome gathered for the host.
+struct Result {
+  int32_t status, iters, err_row, pad;
+  double relres;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -68,21 +97,10 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ int32_t ld_relaxed_i32(const int32_t *p) {
-  int32_t v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-template <typename T>
-__device__ __forceinline__ T ldcg(const T *p) {
-  return __ldcg(p);
 }
 
 __device__ __forceinline__ bool running(const DevState *st) {
@@ -111,8 +129,8 @@ __device__ __forceinline__ bool inv3(const T (&a)[9], T (&o)[9]) {
   return ok;
 }
 
-// Deterministic reduction of NV values over a 256-thread CTA; the result is
-// valid in thread 0.
+// Deterministic reduction of NV values over a CTA; the result is valid in
+// thread 0.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
 #pragma unroll
@@ -137,20 +155,19 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
   __syncthreads();
 }
 
-// Per-tile partial, then the last CTA sums all partials in tile order.
-// Returns true in the last CTA; tot is then valid in its thread 0.
+// Partial of this tile, then the system's last CTA sums all its partials in
+// tile order.  Returns true in that CTA; tot is then valid in thread 0.
 template <int NV>
-__device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], double *partials, uint32_t *counter,
-                                                double (&tot)[NV]) {
+__device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, int tile, double (&tot)[NV]) {
   __shared__ double sm[32 * NV];
   __shared__ int amlast;
   block_reduce<NV>(v, sm);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) partials[(size_t)blockIdx.x * NV + q] = v[q];
+    for (int q = 0; q < NV; ++q) S.partials[(size_t)tile * NV + q] = v[q];
     __threadfence();
-    unsigned t = atomicAdd(counter, 1u);
-    amlast = (t == gridDim.x - 1);
+    const unsigned t = atomicAdd(&S.st->red_count, 1u);
+    amlast = (t == (unsigned)S.ntiles - 1);
   }
   __syncthreads();
   if (!amlast) return false;
@@ -158,15 +175,15 @@ __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], double *partial
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < S.ntiles; b += blockDim.x) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(partials + (size_t)b * NV + q);
+    for (int q = 0; q < NV; ++q) acc[q] += __ldcg(S.partials + (size_t)b * NV + q);
   }
   block_reduce<NV>(acc, sm);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) tot[q] = acc[q];
-    *counter = 0;
+    S.st->red_count = 0;
   }
   return true;
 }
@@ -201,28 +218,30 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
   }
 }
 
-// ------------------------------------------------------------ static kernels
+// ------------------------------------------------------------ tile kernels
 //
-// Each CTA covers one tile of kTileRows = 1024 rows, so that a reduction
-// costs one partial and one arrival per 1024 rows: streaming kernels use 256
-// threads in 4 passes (thread t handles rows tile + t, + 256, + 512, + 768).
+// One CTA per (system, tile); a tile is kTileRows = 1024 rows of its system.
+// Streaming kernels use 256 threads in 4 passes (thread t: rows t, t + 256,
+// t + 512, t + 768 of the tile); SpMV kernels use 1024 threads, one row each.
 
-#define OPM_TILE_ROWS(i)                                                    \
-  for (int pass_ = 0, i = blockIdx.x * kTileRows + threadIdx.x; pass_ < 4; \
-       ++pass_, i += 256)
+#define OPM_TILE(B, S, lt)                  \
+  const int2 tile_ = (B).tiles[blockIdx.x]; \
+  const Sys &S = (B).sys[tile_.x];          \
+  const int lt = tile_.y
 
-// SpMV-type kernels instead use 1024 threads per CTA, one row each (FP64 FMA
-// throughput wants every warp slot; 4 rows per thread costs registers).
-#define OPM_TILE_ROW1(i) for (int pass_ = 0, i = blockIdx.x * kTileRows + threadIdx.x; pass_ < 1; ++pass_)
+#define OPM_TILE_ROWS(i, lt) \
+  for (int pass_ = 0, i = (lt) * kTileRows + threadIdx.x; pass_ < 4; ++pass_, i += 256)
 
-// r = P b, r^ = r, x = p = v = 0, ||b||^2; the last CTA starts the solve.
-__global__ void __launch_bounds__(256, 6) k_setup(Sys S, const double *__restrict__ b_nat, double rtol,
-                                               int32_t maxit) {
+// Starts a solve: r = P b, r^ = r, x = p = v = 0, ||b||^2; the system's
+// last CTA sets the scalars.  A factorisation error makes the solve fail.
+__global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
+  OPM_TILE(B, S, lt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
   double acc[1] = {0.0};
-  OPM_TILE_ROWS(i) {
+  OPM_TILE_ROWS(i, lt) {
     if (i < S.n) {
       const int o = S.perm[i];
-      const double b0 = b_nat[3ll * o], b1 = b_nat[3ll * o + 1], b2 = b_nat[3ll * o + 2];
+      const double b0 = S.b_in[3ll * o], b1 = S.b_in[3ll * o + 1], b2 = S.b_in[3ll * o + 2];
       double *r = S.r + 3ll * i, *rh = S.rh + 3ll * i;
       r[0] = b0; r[1] = b1; r[2] = b2;
       rh[0] = b0; rh[1] = b1; rh[2] = b2;
@@ -236,35 +255,37 @@ __global__ void __launch_bounds__(256, 6) k_setup(Sys S, const double *__restric
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     const double n0 = sqrt(tot[0]);
     st->n0 = n0;
-    st->tol = rtol * n0;
-    st->maxit = maxit;
+    st->tol = S.rtol * n0;
+    st->maxit = S.maxit;
     st->k = 1;
     st->iters = 0;
     st->half = 0;
     st->error = 0;
-    st->bar_count = 0;
     st->relres = 0.0;
     st->rho = tot[0];
     st->rho_prev = 1.0;
     st->alpha = 1.0;
     st->omega = 1.0;
     st->beta = tot[0];
-    if (!isfinite(n0)) st->status = OPM_ERR_NONFINITE;
+    if (st->ferror != 0) st->status = st->ferror;
+    else if (!isfinite(n0)) st->status = OPM_ERR_NONFINITE;
     else if (n0 == 0.0) st->status = OPM_OK;
-    else if (maxit < 1) st->status = OPM_NOT_CONVERGED;
+    else if (S.maxit < 1) st->status = OPM_NOT_CONVERGED;
     else st->status = kRunning;
   }
 }
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).
-__global__ void __launch_bounds__(1024, 2) k_spmv_v(Sys S) {
+__global__ void __launch_bounds__(1024, 2) k_spmv_v(Batch B) {
+  OPM_TILE(B, S, lt);
   if (!running(S.st)) return;
   double acc[1] = {0.0};
-  OPM_TILE_ROW1(i) {
+  const int i = lt * kTileRows + threadIdx.x;
+  {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     row_spmv(S.a_rp, S.a_col, S.a_val, S.ph, i, S.n, y0, y1, y2);
     if (i < S.n) {
@@ -275,7 +296,7 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_v(Sys S) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     st->rhv = tot[0];
     if (tot[0] == 0.0) {
@@ -288,10 +309,12 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_v(Sys S) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(1024, 2) k_spmv_t(Sys S) {
+__global__ void __launch_bounds__(1024, 2) k_spmv_t(Batch B) {
+  OPM_TILE(B, S, lt);
   if (!running(S.st)) return;
   double acc[3] = {0.0, 0.0, 0.0};
-  OPM_TILE_ROW1(i) {
+  const int i = lt * kTileRows + threadIdx.x;
+  {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     row_spmv(S.a_rp, S.a_col, S.a_val, S.sh, i, S.n, y0, y1, y2);
     if (i < S.n) {
@@ -305,7 +328,7 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_t(Sys S) {
     }
   }
   double tot[3];
-  if (last_cta_reduce<3>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<3>(acc, S, lt, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     st->ts = tot[0];
     st->tt = tot[1];
@@ -328,13 +351,14 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_t(Sys S) {
 
 // x += alpha p^ + omega s^, r = s - omega t, ||r||^2, (r^, r); stopping rule,
 // then beta for the next iteration.
-__global__ void __launch_bounds__(256, 6) k_update(Sys S) {
+__global__ void __launch_bounds__(256, 6) k_update(Batch B) {
+  OPM_TILE(B, S, lt);
   if (!running(S.st)) return;
   const DevState *cst = S.st;
   const double alpha = cst->alpha, omega = cst->omega;
   const int half = cst->half;
   double acc[2] = {0.0, 0.0};
-  OPM_TILE_ROWS(i) {
+  OPM_TILE_ROWS(i, lt) {
     if (i < S.n) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(256, 6) k_update(Sys S) {
     }
   }
   double tot[2];
-  if (last_cta_reduce<2>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<2>(acc, S, lt, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     const int k = st->k;
     if (half) {
@@ -382,96 +406,151 @@ __global__ void __launch_bounds__(256, 6) k_update(Sys S) {
 }
 
 // Final true residual ||b - A x|| / ||b|| in FP64 and x back to the caller's
-// order.
-__global__ void __launch_bounds__(1024, 2) k_finish(Sys S, const double *__restrict__ b_nat,
-                                                double *__restrict__ x_nat) {
+// order (zeros on a failed solve).
+__global__ void __launch_bounds__(1024, 2) k_finish(Batch B) {
+  OPM_TILE(B, S, lt);
+  const int status = S.st->status;
+  const bool ok = (status == OPM_OK || status == OPM_NOT_CONVERGED) && S.st->error == 0;
   double acc[1] = {0.0};
-  OPM_TILE_ROW1(i) {
+  const int i = lt * kTileRows + threadIdx.x;
+  {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
+    if (ok) row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
     if (i < S.n) {
       const int o = S.perm[i];
-      const double d0 = b_nat[3ll * o] - y0, d1 = b_nat[3ll * o + 1] - y1, d2 = b_nat[3ll * o + 2] - y2;
-      acc[0] = fma(d0, d0, fma(d1, d1, fma(d2, d2, acc[0])));
+      if (ok) {
+        const double d0 = S.b_in[3ll * o] - y0, d1 = S.b_in[3ll * o + 1] - y1, d2 = S.b_in[3ll * o + 2] - y2;
+        acc[0] = fma(d0, d0, fma(d1, d1, fma(d2, d2, acc[0])));
+      }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) x_nat[3ll * o + c] = S.x[3ll * i + c];
+      for (int c = 0; c < 3; ++c) S.x_out[3ll * o + c] = ok ? S.x[3ll * i + c] : 0.0;
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S.partials, &S.st->red_count, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
-    st->relres = st->n0 > 0.0 ? sqrt(tot[0]) / st->n0 : 0.0;
+    st->relres = !ok ? nan("") : (st->n0 > 0.0 ? sqrt(tot[0]) / st->n0 : 0.0);
   }
 }
 
-// y = A x in the caller's order (x already permuted).
-__global__ void __launch_bounds__(1024, 2) k_spmv_plain(Sys S, const double *__restrict__ xp,
-                                                    double *__restrict__ y_nat) {
-  OPM_TILE_ROW1(i) {
-    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_spmv(S.a_rp, S.a_col, S.a_val, xp, i, S.n, y0, y1, y2);
-    if (i < S.n) {
-      const int o = S.perm[i];
-      y_nat[3ll * o] = y0;
-      y_nat[3ll * o + 1] = y1;
-      y_nat[3ll * o + 2] = y2;
-    }
+// y = A x in the caller's order (x already permuted into w).
+__global__ void __launch_bounds__(1024, 2) k_spmv_plain(Batch B) {
+  OPM_TILE(B, S, lt);
+  const int i = lt * kTileRows + threadIdx.x;
+  double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+  row_spmv(S.a_rp, S.a_col, S.a_val, S.w, i, S.n, y0, y1, y2);
+  if (i < S.n) {
+    const int o = S.perm[i];
+    S.x_out[3ll * o] = y0;
+    S.x_out[3ll * o + 1] = y1;
+    S.x_out[3ll * o + 2] = y2;
   }
 }
 
-// out[i] = in[perm[i]] (caller's order -> schedule order).
-__global__ void __launch_bounds__(256, 6) k_gather(Sys S, const double *__restrict__ in, double *__restrict__ out) {
-  OPM_TILE_ROWS(i) {
-    if (i < S.n) {
-      const int o = S.perm[i];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) out[3ll * i + c] = in[3ll * o + c];
-    }
-  }
-}
-
-// out[perm[i]] = in[i] (schedule order -> caller's order).
-__global__ void __launch_bounds__(256, 6) k_scatter(Sys S, const double *__restrict__ in, double *__restrict__ out) {
-  OPM_TILE_ROWS(i) {
+// w[i] = b_in[perm[i]] (caller's order -> schedule order).
+__global__ void __launch_bounds__(256, 6) k_gather(Batch B) {
+  OPM_TILE(B, S, lt);
+  OPM_TILE_ROWS(i, lt) {
     if (i < S.n) {
       const int o = S.perm[i];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[3ll * o + c] = in[3ll * i + c];
+      for (int c = 0; c < 3; ++c) S.w[3ll * i + c] = S.b_in[3ll * o + c];
     }
   }
+}
+
+// x_out[perm[i]] = t[i] (schedule order -> caller's order).
+__global__ void __launch_bounds__(256, 6) k_scatter(Batch B) {
+  OPM_TILE(B, S, lt);
+  OPM_TILE_ROWS(i, lt) {
+    if (i < S.n) {
+      const int o = S.perm[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S.x_out[3ll * o + c] = S.t[3ll * i + c];
+    }
+  }
+}
+
+// ------------------------------------------------------------ control
+
+// Clears the error words of every system and the grid barrier before a
+// factorisation or a standalone preconditioner application.
+__global__ void k_begin_factor(Batch B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) B.bar[0] = 0;
+  if (s < B.nsys) {
+    DevState *st = B.sys[s].st;
+    st->ferror = 0;
+    st->error = 0;
+    st->err_row = 0x7fffffff;
+  }
+}
+
+// After a factorisation: a recorded error becomes the factorisation error.
+__global__ void k_end_factor(Batch B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B.nsys) {
+    DevState *st = B.sys[s].st;
+    if (st->error != 0) st->ferror = st->error;
+  }
+}
+
+// Outcome of every system for the host.
+__global__ void k_results(Batch B, Result *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B.nsys) {
+    const DevState *st = B.sys[s].st;
+    Result r;
+    r.status = st->error != 0 ? st->error : st->status;
+    r.iters = st->iters;
+    r.err_row = st->err_row;
+    r.pad = 0;
+    r.relres = st->relres;
+    out[s] = r;
+  }
+}
+
+// While-loop condition of the solve graph: continue while a system runs.
+__global__ void k_loop_cond(Batch B, cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.nsys; s += blockDim.x)
+    if (running(B.sys[s].st)) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // ----------------------------------------------------------- phase sweeps
 //
-// The schedule's row order is cut into phases: maximal runs of rows none of
-// which reads another row of its run (the levels or the colours).  A sweep
-// kernel is one cooperative launch (all CTAs resident) that walks the phases
-// in order, every warp taking 32-row slices of the current phase grid-strided,
-// with a grid barrier between phases.  Values produced in earlier phases by
-// other SMs are read through L2 (ld.global.cg), never from L1.
+// Values produced in earlier phases by other SMs are read through L2
+// (ld.global.cg), never from L1.
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  On timeout
-// it records OPM_ERR_TIMEOUT and lets the CTA continue; once an error is
-// recorded, later barriers do not wait.  The CTA numbered skip_cta (a test
-// hook, normally -1) never arrives, so the others' waits run out.
-__device__ __forceinline__ void grid_sync(DevState *st, uint64_t limit_ns, int skip_cta) {
+// it records OPM_ERR_TIMEOUT in every system and lets the CTA continue;
+// after a timeout later barriers do not wait.  The CTA numbered skip_cta (a
+// test hook, normally -1) never arrives, so the others' waits run out.
+__device__ __forceinline__ void grid_sync(const Batch &B, bool &timed_out) {
   __syncthreads();
-  if (threadIdx.x == 0 && (int)blockIdx.x != skip_cta) {
-    const uint32_t gen = ld_acquire(&st->bar_gen);
-    __threadfence();
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
-      st->bar_count = 0;
+  __shared__ int to;
+  if (threadIdx.x == 0) {
+    to = timed_out ? 1 : 0;
+    if ((int)blockIdx.x != B.skip_cta) {
+      uint32_t *count = B.bar, *genp = B.bar + 32;
+      const uint32_t gen = ld_acquire(genp);
       __threadfence();
-      st_release(&st->bar_gen, gen + 1);
-    } else if (ld_relaxed_i32(&st->error) == 0) {
-      const uint64_t t0 = gtimer();
-      for (uint32_t it = 0;; ++it) {
-        if (ld_acquire(&st->bar_gen) != gen) break;
-        __nanosleep(32);
-        if ((it & 63u) == 63u) {
-          if (ld_relaxed_i32(&st->error) != 0) break;
-          if (gtimer() - t0 > limit_ns) {
-            atomicCAS(&st->error, 0, (int32_t)OPM_ERR_TIMEOUT);
+      if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        *count = 0;
+        __threadfence();
+        st_release(genp, gen + 1);
+      } else if (!to) {
+        const uint64_t t0 = gtimer();
+        for (uint32_t it = 0;; ++it) {
+          if (ld_acquire(genp) != gen) break;
+          __nanosleep(32);
+          if ((it & 63u) == 63u && gtimer() - t0 > B.spin_limit_ns) {
+            for (int s = 0; s < B.nsys; ++s) atomicCAS(&B.sys[s].st->error, 0, (int32_t)OPM_ERR_TIMEOUT);
+            to = 1;
             break;
           }
         }
@@ -479,6 +558,7 @@ __device__ __forceinline__ void grid_sync(DevState *st, uint64_t limit_ns, int s
     }
   }
   __syncthreads();
+  timed_out = to != 0;
 }
 
 template <typename TF>
@@ -493,11 +573,11 @@ __device__ __forceinline__ Vec3<TF> load3cg(const TF *p) {
 
 // a -= B v for one 3x3 block (entry-planar with stride c) in FMA form.
 template <typename TF>
-__device__ __forceinline__ void blk_sub(const TF *__restrict__ B, int c, TF v0, TF v1, TF v2, TF &a0, TF &a1,
+__device__ __forceinline__ void blk_sub(const TF *__restrict__ Bv, int c, TF v0, TF v1, TF v2, TF &a0, TF &a1,
                                         TF &a2) {
-  a0 = fma(-__ldg(B), v0, fma(-__ldg(B + c), v1, fma(-__ldg(B + 2 * c), v2, a0)));
-  a1 = fma(-__ldg(B + 3 * c), v0, fma(-__ldg(B + 4 * c), v1, fma(-__ldg(B + 5 * c), v2, a1)));
-  a2 = fma(-__ldg(B + 6 * c), v0, fma(-__ldg(B + 7 * c), v1, fma(-__ldg(B + 8 * c), v2, a2)));
+  a0 = fma(-__ldg(Bv), v0, fma(-__ldg(Bv + c), v1, fma(-__ldg(Bv + 2 * c), v2, a0)));
+  a1 = fma(-__ldg(Bv + 3 * c), v0, fma(-__ldg(Bv + 4 * c), v1, fma(-__ldg(Bv + 5 * c), v2, a1)));
+  a2 = fma(-__ldg(Bv + 6 * c), v0, fma(-__ldg(Bv + 7 * c), v1, fma(-__ldg(Bv + 8 * c), v2, a2)));
 }
 
 // a -= sum over the lane's row of a sliced part of B_ij v_j, v read through
@@ -531,13 +611,17 @@ __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const T
   }
 }
 
+template <int MODE>
+__device__ __forceinline__ double *sweep_out(const Sys &S) {
+  return (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : S.t;
+}
+
 // Forward substitution for the rows of slice sl inside [r0, r1):
 // y_i = rhs_i - sum_{j<i} L_ij y_j (Algorithm 1, equation 3), the right-hand
-// side formed on the fly.  With also_back (last phase: no U columns past the
-// phase), the backward step z_i = inv(U_ii) y_i follows at once.
+// side formed on the fly.  In the system's last phase (no U columns past
+// the phase) the backward step z_i = inv(U_ii) y_i follows at once.
 template <typename TF, int MODE>
-__device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, double alpha, double beta,
-                                         double omega, const double *in, double *z, bool also_back) {
+__device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, bool also_back) {
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
@@ -549,17 +633,19 @@ __device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, d
   if (act) {
     const size_t e = 3ll * i;
     if (MODE == kModeP) {
+      const double beta = S.st->beta, omega = S.st->omega;
       h0 = fma(beta, fma(-omega, S.v[e], S.p[e]), S.r[e]);
       h1 = fma(beta, fma(-omega, S.v[e + 1], S.p[e + 1]), S.r[e + 1]);
       h2 = fma(beta, fma(-omega, S.v[e + 2], S.p[e + 2]), S.r[e + 2]);
       S.p[e] = h0; S.p[e + 1] = h1; S.p[e + 2] = h2;
     } else if (MODE == kModeS) {
+      const double alpha = S.st->alpha;
       h0 = fma(-alpha, S.v[e], S.r[e]);
       h1 = fma(-alpha, S.v[e + 1], S.r[e + 1]);
       h2 = fma(-alpha, S.v[e + 2], S.r[e + 2]);
       S.s[e] = h0; S.s[e + 1] = h1; S.s[e + 2] = h2;
     } else {
-      h0 = in[e]; h1 = in[e + 1]; h2 = in[e + 2];
+      h0 = S.w[e]; h1 = S.w[e + 1]; h2 = S.w[e + 2];
     }
   }
   const int base0 = (s0 < S.n) ? __ldg(S.l_rp + s0) : 0;
@@ -569,7 +655,7 @@ __device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, d
   if (act) {
     if (also_back) {
       const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
-      double *zi = z + 3ll * i;
+      double *zi = sweep_out<MODE>(S) + 3ll * i;
       zi[0] = (double)fma(__ldg(D), a0, fma(__ldg(D + 32), a1, __ldg(D + 64) * a2));
       zi[1] = (double)fma(__ldg(D + 96), a0, fma(__ldg(D + 128), a1, __ldg(D + 160) * a2));
       zi[2] = (double)fma(__ldg(D + 192), a0, fma(__ldg(D + 224), a1, __ldg(D + 256) * a2));
@@ -582,14 +668,15 @@ __device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, d
 
 // Backward substitution for the rows of slice sl inside [r0, r1):
 // z_i = inv(U_ii)(y_i - sum_{j>i} U_ij z_j) (Algorithm 1, equation 4).
-template <typename TF>
-__device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1, double *z) {
+template <typename TF, int MODE>
+__device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
   const bool act = i >= r0 && i < r1;
   const TF *y = static_cast<const TF *>(S.y);
   const TF *lu = static_cast<const TF *>(S.lu);
+  double *z = sweep_out<MODE>(S);
   const int len = (i < S.n) ? __ldg(S.u_rp + i + 1) - __ldg(S.u_rp + i) : 0;
   TF a0 = TF(0), a1 = TF(0), a2 = TF(0);
   if (act) {
@@ -608,70 +695,68 @@ __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1, d
   }
 }
 
-// ILU0 application z = U^-1 L^-1 rhs (Algorithm 1) in one cooperative
-// launch: forward phases in order, then backward phases in reverse order;
-// the last phase does both sweeps at once.
+// One launch per phase: one sweep entry (a 32-row slice) per warp.
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(1024) k_apply(Sys S, const double *in, double *out) {
-  DevState *st = S.st;
-  if (MODE != kModePlain && !running(st)) return;
-  const double alpha = st->alpha, beta = st->beta, omega = st->omega;
-  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
+__global__ void __launch_bounds__(256) k_fwd_phase(Batch B, int c) {
+  const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= __ldg(B.fwd_ptr + c + 1)) return;
+  const int4 E = B.ent[e];
+  const Sys &S = B.sys[E.x];
+  if (MODE != kModePlain && !running(S.st)) return;
+  fwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff, (E.w >> 31) != 0);
+}
+
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(256) k_bwd_phase(Batch B, int c) {
+  const int e = __ldg(B.bwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= __ldg(B.bwd_ptr + c + 1)) return;
+  const int4 E = B.ent[e];
+  const Sys &S = B.sys[E.x];
+  if (MODE != kModePlain && !running(S.st)) return;
+  bwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff);
+}
+
+// ILU0 application z = U^-1 L^-1 rhs (Algorithm 1) in one cooperative
+// launch: forward phases in order, then backward phases in reverse order.
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(1024) k_apply(Batch B) {
   const int W = gridDim.x * (blockDim.x >> 5);
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int np = S.nphases;
-  for (int ph = 0; ph < np; ++ph) {
-    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
-    const bool last = ph == np - 1;
-    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W)
-      fwd_rows<TF, MODE>(S, sl, r0, r1, alpha, beta, omega, in, z, last);
-    if (!last) grid_sync(st, S.spin_limit_ns, S.skip_cta);
+  bool timed_out = false;
+  for (int c = 0; c < B.nphases; ++c) {
+    if (c > 0) grid_sync(B, timed_out);
+    const int e1 = __ldg(B.fwd_ptr + c + 1);
+    for (int e = __ldg(B.fwd_ptr + c) + g; e < e1; e += W) {
+      const int4 E = B.ent[e];
+      const Sys &S = B.sys[E.x];
+      if (MODE == kModePlain || running(S.st)) fwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff, (E.w >> 31) != 0);
+    }
   }
-  for (int ph = np - 2; ph >= 0; --ph) {
-    grid_sync(st, S.spin_limit_ns, S.skip_cta);
-    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
-    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W) bwd_rows<TF>(S, sl, r0, r1, z);
+  for (int c = B.nphases - 2; c >= 0; --c) {
+    grid_sync(B, timed_out);
+    const int e1 = __ldg(B.bwd_ptr + c + 1);
+    for (int e = __ldg(B.bwd_ptr + c) + g; e < e1; e += W) {
+      const int4 E = B.ent[e];
+      const Sys &S = B.sys[E.x];
+      if (MODE == kModePlain || running(S.st)) bwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff);
+    }
   }
-}
-
-// The same sweeps with one launch per phase (kernel boundaries as the
-// barrier), for schedules with few phases: plain grids of 256-thread CTAs,
-// one 32-row slice per warp, at full occupancy.
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_fwd_phase(Sys S, int r0, int r1, int last, const double *in,
-                                                    double *out) {
-  DevState *st = S.st;
-  if (MODE != kModePlain && !running(st)) return;
-  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (sl > ((r1 - 1) >> 5)) return;
-  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
-  fwd_rows<TF, MODE>(S, sl, r0, r1, st->alpha, st->beta, st->omega, in, z, last != 0);
-}
-
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_bwd_phase(Sys S, int r0, int r1, double *out) {
-  DevState *st = S.st;
-  if (MODE != kModePlain && !running(st)) return;
-  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (sl > ((r1 - 1) >> 5)) return;
-  double *z = (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : out;
-  bwd_rows<TF>(S, sl, r0, r1, z);
 }
 
 // ILU0 decomposition (Algorithm 2) of the permuted matrix, phase by phase,
-// fused with the value permutation: with vals_user, block w of the permuted
+// fused with the value permutation: with vals_in, block w of the permuted
 // matrix is copied from the caller's block a_src[w] (Algorithm 3's index
-// copy) into both A and the factors.  Row i of phase p reads only rows of
+// copy) into both A and the factors.  Row i of a phase reads only rows of
 // earlier phases (its pivots k < i) and updates only its own blocks.
 template <typename TF>
-__device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1,
-                                            const double *__restrict__ vals_user) {
+__device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1) {
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
   const int n = S.n;
   const bool act = i >= r0 && i < r1;
   TF *lu = static_cast<TF *>(S.lu);
+  const double *__restrict__ vals_user = S.vals_in;
   const unsigned lt = lanemask_lt();
   DevState *st = S.st;
   // ---- copy A's row into A (sliced) and into its L / D / U slots
@@ -771,20 +856,25 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
 }
 
 template <typename TF>
-__global__ void __launch_bounds__(256) k_factor_phase(Sys S, int r0, int r1, const double *__restrict__ vals_user) {
-  const int sl = (r0 >> 5) + blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (sl > ((r1 - 1) >> 5)) return;
-  factor_rows<TF>(S, sl, r0, r1, vals_user);
+__global__ void __launch_bounds__(256) k_factor_phase(Batch B, int c) {
+  const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= __ldg(B.fwd_ptr + c + 1)) return;
+  const int4 E = B.ent[e];
+  factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w & 0x7fffffff);
 }
 
 template <typename TF>
-__global__ void __launch_bounds__(1024) k_factor(Sys S, const double *__restrict__ vals_user) {
+__global__ void __launch_bounds__(1024) k_factor(Batch B) {
   const int W = gridDim.x * (blockDim.x >> 5);
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (int ph = 0; ph < S.nphases; ++ph) {
-    if (ph > 0) grid_sync(S.st, S.spin_limit_ns, S.skip_cta);
-    const int r0 = __ldg(S.phase_ptr + ph), r1 = __ldg(S.phase_ptr + ph + 1);
-    for (int sl = (r0 >> 5) + g; sl <= ((r1 - 1) >> 5); sl += W) factor_rows<TF>(S, sl, r0, r1, vals_user);
+  bool timed_out = false;
+  for (int c = 0; c < B.nphases; ++c) {
+    if (c > 0) grid_sync(B, timed_out);
+    const int e1 = __ldg(B.fwd_ptr + c + 1);
+    for (int e = __ldg(B.fwd_ptr + c) + g; e < e1; e += W) {
+      const int4 E = B.ent[e];
+      factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w & 0x7fffffff);
+    }
   }
 }
 

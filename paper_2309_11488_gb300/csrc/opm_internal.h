@@ -65,8 +65,7 @@ struct Analysis {
 opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
                    Analysis &an, int32_t *err_row);
 
-// Krylov scalars and control words, one per system, in device memory.  The
-// grid-barrier counter and generation sit on cache lines of their own.
+// Krylov scalars and control words, one per system, in device memory.
 struct alignas(128) DevState {
   double rho, rho_prev, alpha, omega, beta;
   double n0, tol;
@@ -77,12 +76,10 @@ struct alignas(128) DevState {
   int32_t iters;
   int32_t maxit;
   int32_t half;    // the last half step met the stopping rule
-  int32_t error;   // device-detected error (opm_status) or 0
+  int32_t error;   // error detected during the current operation (opm_status) or 0
+  int32_t ferror;  // error of the last factorisation, kept until the next one
   int32_t err_row; // smallest permuted row with a singular pivot
   uint32_t red_count;            // last-CTA reduction counter
-  alignas(128) uint32_t bar_count;  // grid barrier of the cooperative sweep kernels: arrivals
-  alignas(128) uint32_t bar_gen;    // and generation
-  int32_t pad[31];
 };
 
 }  // namespace opm

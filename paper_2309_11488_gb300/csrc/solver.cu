@@ -1,10 +1,17 @@
 // Host driver and C ABI of the GB300 BSR ILU0-BiCGStab library.
 //
-// A handle owns the schedule-ordered device copy of the matrix, its ILU0
-// factors, the Krylov vectors and a CUDA graph holding `chunk` BiCGStab
-// iterations (5 kernel nodes each).  A solve is: one setup launch, graph
-// launches until the device status word leaves "running" (the host reads it
-// once per chunk), one finishing launch for the true residual.
+// A handle owns one system's schedule-ordered device copy of the matrix, its
+// ILU0 factors and its Krylov vectors.  Work is launched through a Runner: a
+// set of systems (a handle's own set of one, or a batch of handles) with its
+// work lists, its kernel-parameter block and three CUDA graphs:
+//   * factor graph: clear errors -> ILU0 phases -> record errors -> results;
+//   * solve graph: setup -> while (any system running) { `chunk` BiCGStab
+//     iterations; loop condition } -> true residual -> results.  The loop
+//     runs on the device (a conditional graph node): one graph launch per
+//     solve, no host round trip between iterations;
+//   * iteration graph (only with profile_kernels): `chunk` iterations with
+//     event-record nodes between kernels, driven by a host loop, for
+//     per-kernel device times.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -17,6 +24,10 @@
 
 using namespace opm;
 
+namespace opm {
+struct Runner;
+}
+
 struct opm_solver {
   Analysis an;
   opm_options opt{};
@@ -25,23 +36,48 @@ struct opm_solver {
   int32_t n = 0, nslices = 0, ntiles = 0;
   int64_t nnzb = 0;
   bool fp32 = false;
-  Sys sys{};
-  int grid_apply = 1, grid_factor = 1;
-  int chunk = 8;
-  cudaGraphExec_t chunk_exec = nullptr;
-  int chunk_launches = 0;  // kernel nodes in the chunk graph
-  bool cooperative = false;  // sweeps as one cooperative launch
-  DevState *h_state = nullptr;  // pinned
+  Sys sys{};                     // this system's descriptor (host copy)
   std::vector<void *> allocs;
-  double *vals_stage = nullptr;   // caller's values when given from host
-  double *vec_in = nullptr, *vec_out = nullptr;  // caller-order staging
   int64_t dev_bytes = 0;
+  double *vals_stage = nullptr;  // caller's values when given from host
+  double *vec_in = nullptr, *vec_out = nullptr;  // caller-order staging
   int32_t last_err_row = -1;
   bool factors_ok = false;
   opm_timing timing{};
-  cudaEvent_t ev[6] = {};
-  std::vector<cudaEvent_t> kev;  // per-kernel events inside the graph (profiling)
+  cudaEvent_t ev[2] = {};
+  opm::Runner *run = nullptr;    // batch of one
+  bool async_pending = false;
 };
+
+struct opm_batch_s {
+  opm::Runner *run = nullptr;
+  std::vector<opm_solver *> members;
+  bool async_pending = false;
+};
+
+namespace opm {
+
+struct Runner {
+  std::vector<opm_solver *> mem;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool fp32 = false, cooperative = false, profile = false;
+  int chunk = 2, nsys = 0, nphases = 0, ntiles = 0;
+  std::vector<int32_t> fwd_ptr, bwd_ptr;
+  Batch B{};
+  Sys *h_sys = nullptr;      // pinned staging of the descriptors
+  Result *h_res = nullptr;   // pinned results
+  Result *d_res = nullptr;
+  std::vector<void *> allocs;
+  int64_t dev_bytes = 0;
+  int grid_apply = 1, grid_factor = 1;
+  cudaGraphExec_t solve_exec = nullptr, iter_exec = nullptr, factor_exec = nullptr;
+  int iter_launches = 0, factor_launches = 0;
+  std::vector<cudaEvent_t> kev;  // profiling events, 6 per iteration of a chunk
+  cudaEvent_t ev_done = nullptr;
+};
+
+}  // namespace opm
 
 namespace {
 
@@ -59,13 +95,14 @@ const char *const kStatusText[] = {"ok",
                                    "device wait timed out",
                                    "CUDA error"};
 
-#define CK(call)                                      \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) {                          \
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
       fprintf(stderr, "opm_bsr: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
-      return e_ == cudaErrorMemoryAllocation ? OPM_ERR_OOM : OPM_ERR_CUDA; \
-    }                                                 \
+      cudaGetLastError();                                                         \
+      return e_ == cudaErrorMemoryAllocation ? OPM_ERR_OOM : OPM_ERR_CUDA;        \
+    }                                                                             \
   } while (0)
 
 bool is_device_ptr(const void *p) {
@@ -79,28 +116,27 @@ bool is_device_ptr(const void *p) {
 }
 
 template <typename T>
-opm_status dalloc(opm_solver *h, T **p, size_t count) {
+opm_status dalloc(std::vector<void *> &allocs, int64_t &bytes_acc, T **p, size_t count) {
   *p = nullptr;
-  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   cudaError_t e = cudaMalloc((void **)p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? OPM_ERR_OOM : OPM_ERR_CUDA;
   }
-  h->allocs.push_back(*p);
-  h->dev_bytes += (int64_t)bytes;
+  allocs.push_back(*p);
+  bytes_acc += (int64_t)bytes;
   return OPM_OK;
 }
 
 template <typename T>
-opm_status upload(opm_solver *h, T **p, const std::vector<T> &v) {
-  opm_status s = dalloc(h, p, v.size());
+opm_status upload(std::vector<void *> &allocs, int64_t &bytes_acc, cudaStream_t st, T **p,
+                  const std::vector<T> &v) {
+  opm_status s = dalloc(allocs, bytes_acc, p, v.size());
   if (s != OPM_OK) return s;
-  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   return OPM_OK;
 }
-
-int blocks_for(int n) { return std::max(1, (n + kTileRows - 1) / kTileRows); }
 
 // Sweep kernels are launched cooperatively: the launch fails instead of
 // starting when its CTAs cannot all be resident at once.
@@ -119,95 +155,91 @@ cudaError_t launch_coop(void (*kern)(P...), int grid, cudaStream_t st, A... args
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// CTAs of 8 warps covering the slices of rows [r0, r1)
-int phase_blocks(int r0, int r1) { return (((r1 - 1) >> 5) - (r0 >> 5) + 1 + 7) / 8; }
-
 // Schedules with at most this many phases run one launch per phase; more
 // phases run as one cooperative launch with grid barriers.
 constexpr int kMaxPhaseLaunches = 1024;
 
+int blocks8(int entries) { return std::max(1, (entries + 7) / 8); }
+
 template <typename TF>
-int launch_factor(opm_solver *h, const double *vals_user, cudaStream_t st) {
-  const Sys &S = h->sys;
-  if (h->cooperative) {
-    launch_coop(k_factor<TF>, h->grid_factor, st, S, vals_user);
+int launch_factor_t(Runner &R, cudaStream_t st) {
+  if (R.cooperative) {
+    launch_coop(k_factor<TF>, R.grid_factor, st, R.B);
     return 1;
   }
-  const std::vector<int32_t> &pp = h->an.phase_ptr;
-  for (int p = 0; p < S.nphases; ++p)
-    k_factor_phase<TF><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], vals_user);
-  return S.nphases;
+  for (int c = 0; c < R.nphases; ++c)
+    k_factor_phase<TF><<<blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, 0, st>>>(R.B, c);
+  return R.nphases;
 }
 
 template <typename TF, int MODE>
-int launch_apply(opm_solver *h, const double *in, double *out, cudaStream_t st) {
-  const Sys &S = h->sys;
-  if (h->cooperative) {
-    launch_coop(k_apply<TF, MODE>, h->grid_apply, st, S, in, out);
+int launch_apply_t(Runner &R, cudaStream_t st) {
+  if (R.cooperative) {
+    launch_coop(k_apply<TF, MODE>, R.grid_apply, st, R.B);
     return 1;
   }
-  const std::vector<int32_t> &pp = h->an.phase_ptr;
-  const int np = S.nphases;
-  for (int p = 0; p < np; ++p)
-    k_fwd_phase<TF, MODE><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], p == np - 1, in,
-                                                                            out);
-  for (int p = np - 2; p >= 0; --p)
-    k_bwd_phase<TF, MODE><<<phase_blocks(pp[p], pp[p + 1]), 256, 0, st>>>(S, pp[p], pp[p + 1], out);
-  return 2 * np - 1;
+  for (int c = 0; c < R.nphases; ++c)
+    k_fwd_phase<TF, MODE><<<blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, 0, st>>>(R.B, c);
+  int n = R.nphases;
+  for (int c = R.nphases - 2; c >= 0; --c) {
+    const int cnt = R.bwd_ptr[c + 1] - R.bwd_ptr[c];
+    if (cnt == 0) continue;
+    k_bwd_phase<TF, MODE><<<blocks8(cnt), 256, 0, st>>>(R.B, c);
+    ++n;
+  }
+  return n;
 }
 
 template <int MODE>
-int launch_apply_p(opm_solver *h, const double *in, double *out, cudaStream_t st) {
-  return h->fp32 ? launch_apply<float, MODE>(h, in, out, st) : launch_apply<double, MODE>(h, in, out, st);
+int launch_apply(Runner &R, cudaStream_t st) {
+  return R.fp32 ? launch_apply_t<float, MODE>(R, st) : launch_apply_t<double, MODE>(R, st);
 }
 
-// One BiCGStab iteration: 5 kernels.  With ev (6 events), the kernels are
-// bracketed by event-record nodes (external records, so that they are real
-// graph nodes rather than capture-internal dependencies) for per-kernel
-// timing.
-int launch_iteration(opm_solver *h, cudaStream_t st, cudaEvent_t *ev) {
-  const int nb = h->ntiles;
+int launch_factor_seq(Runner &R, cudaStream_t st) {
+  const int sb = std::max(1, (R.nsys + 255) / 256);
+  k_begin_factor<<<sb, 256, 0, st>>>(R.B);
+  const int n = R.fp32 ? launch_factor_t<float>(R, st) : launch_factor_t<double>(R, st);
+  k_end_factor<<<sb, 256, 0, st>>>(R.B);
+  return n + 2;
+}
+
+// One BiCGStab iteration.  With ev (6 events), the kernel groups are
+// bracketed by event-record nodes (external records, so that they become
+// real graph nodes) for per-kernel timing.
+int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
   auto mark = [&](int q) {
     if (ev) cudaEventRecordWithFlags(ev[q], st, cudaEventRecordExternal);
   };
-  int launches = 3;
+  int n = 3;
   mark(0);
-  launches += launch_apply_p<kModeP>(h, nullptr, nullptr, st);
+  n += launch_apply<kModeP>(R, st);
   mark(1);
-  k_spmv_v<<<nb, 1024, 0, st>>>(h->sys);
+  k_spmv_v<<<R.ntiles, 1024, 0, st>>>(R.B);
   mark(2);
-  launches += launch_apply_p<kModeS>(h, nullptr, nullptr, st);
+  n += launch_apply<kModeS>(R, st);
   mark(3);
-  k_spmv_t<<<nb, 1024, 0, st>>>(h->sys);
+  k_spmv_t<<<R.ntiles, 1024, 0, st>>>(R.B);
   mark(4);
-  k_update<<<nb, 256, 0, st>>>(h->sys);
+  k_update<<<R.ntiles, 256, 0, st>>>(R.B);
   mark(5);
-  return launches;
+  return n;
 }
 
 const int kIterKernel[5] = {OPM_KERNEL_APPLY, OPM_KERNEL_SPMV, OPM_KERNEL_APPLY, OPM_KERNEL_SPMV,
                             OPM_KERNEL_UPDATE};
 
-void add_kernel_time(opm_solver *h, int kind, cudaEvent_t a, cudaEvent_t b) {
+void add_kernel_time(opm_timing &t, int kind, cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
-    h->timing.kernel_ms[kind] += ms;
-    h->timing.kernel_count[kind] += 1;
+    t.kernel_ms[kind] += ms;
+    t.kernel_count[kind] += 1;
   } else {
     cudaGetLastError();
   }
 }
 
-// Clears the error word and the grid-barrier counter before a sweep launch
-// that does not follow k_setup.
-__global__ void k_begin_factor(DevState *st) {
-  st->error = 0;
-  st->err_row = INT_MAX;
-  st->bar_count = 0;
-}
+int results_blocks(const Runner &R) { return std::max(1, (R.nsys + 127) / 128); }
 
-// Largest co-resident grid of sweep CTAs for a kernel, capped by the work
-// (one slice per warp).
 template <typename K>
 int resident_grid(K kernel, int device, int items) {
   int sms = 1, occ = 1;
@@ -217,59 +249,334 @@ int resident_grid(K kernel, int device, int items) {
     occ = 1;
   }
   const int warps = kSweepThreads / 32;
-  int want = std::max(1, (items + warps - 1) / warps);
-  return std::max(1, std::min(sms * occ, want));
-}
-
-// The sweep grids need only as many warps as the largest phase has slices:
-// fewer CTAs make the grid barrier cheaper.
-int max_phase_slices(const Analysis &an) {
-  int m = 1;
-  for (size_t p = 0; p + 1 < an.phase_ptr.size(); ++p) {
-    const int r0 = an.phase_ptr[p], r1 = an.phase_ptr[p + 1];
-    m = std::max(m, (r1 - 1) / kWarp - r0 / kWarp + 1);
-  }
-  return m;
+  return std::max(1, std::min(sms * occ, (items + warps - 1) / warps));
 }
 
 template <typename TF>
-int apply_grid(int device, int slices) {
-  int g = resident_grid(k_apply<TF, kModeP>, device, slices);
-  g = std::min(g, resident_grid(k_apply<TF, kModeS>, device, slices));
-  return std::min(g, resident_grid(k_apply<TF, kModePlain>, device, slices));
+void cooperative_grids(Runner &R, int max_entries) {
+  int g = resident_grid(k_apply<TF, kModeP>, R.device, max_entries);
+  g = std::min(g, resident_grid(k_apply<TF, kModeS>, R.device, max_entries));
+  R.grid_apply = std::min(g, resident_grid(k_apply<TF, kModePlain>, R.device, max_entries));
+  R.grid_factor = resident_grid(k_factor<TF>, R.device, max_entries);
 }
 
-opm_status build_graph(opm_solver *h) {
+opm_status add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, size_t ndep,
+                           void *func, int grid, int block, void **args) {
+  cudaKernelNodeParams kp = {};
+  kp.func = func;
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  CK(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+  return OPM_OK;
+}
+
+opm_status build_graphs(Runner &R) {
   cudaStream_t cap;
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  opm_status s = OPM_OK;
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    h->chunk_launches = 0;
-    for (int it = 0; it < h->chunk; ++it)
-      h->chunk_launches += launch_iteration(h, cap, h->kev.empty() ? nullptr : &h->kev[6 * it]);
-    e = cudaStreamEndCapture(cap, &g);
+  // ---- factor graph
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    s = OPM_ERR_CUDA;
+  } else {
+    R.factor_launches = launch_factor_seq(R, cap) + 1;
+    k_results<<<results_blocks(R), 128, 0, cap>>>(R.B, R.d_res);
+    if (cudaStreamEndCapture(cap, &g) != cudaSuccess || cudaGraphInstantiate(&R.factor_exec, g, 0) != cudaSuccess)
+      s = OPM_ERR_CUDA;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->chunk_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  g = nullptr;
+  // ---- solve graph with the device-side iteration loop
+  if (s == OPM_OK) do {
+      if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        s = OPM_ERR_CUDA;
+        break;
+      }
+      void *argsB[] = {&R.B};
+      cudaGraphNode_t n_setup, n_while, n_finish, n_res;
+      if ((s = add_kernel_node(g, &n_setup, nullptr, 0, (void *)k_setup, R.ntiles, 256, argsB)) != OPM_OK) break;
+      cudaGraphConditionalHandle ch;
+      if (cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        s = OPM_ERR_CUDA;
+        break;
+      }
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = ch;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      if (cudaGraphAddNode(&n_while, g, &n_setup, nullptr, 1, &cp) != cudaSuccess) {
+        s = OPM_ERR_CUDA;
+        break;
+      }
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+          cudaSuccess) {
+        s = OPM_ERR_CUDA;
+        break;
+      }
+      R.iter_launches = 0;
+      for (int it = 0; it < R.chunk; ++it) R.iter_launches = launch_iteration(R, cap, nullptr);
+      k_loop_cond<<<1, 256, 0, cap>>>(R.B, ch);
+      if (cudaStreamEndCapture(cap, &body) != cudaSuccess) {
+        s = OPM_ERR_CUDA;
+        break;
+      }
+      if ((s = add_kernel_node(g, &n_finish, &n_while, 1, (void *)k_finish, R.ntiles, 1024, argsB)) != OPM_OK)
+        break;
+      void *argsR[] = {&R.B, &R.d_res};
+      if ((s = add_kernel_node(g, &n_res, &n_finish, 1, (void *)k_results, results_blocks(R), 128, argsR)) !=
+          OPM_OK)
+        break;
+      if (cudaGraphInstantiate(&R.solve_exec, g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+    } while (0);
+  if (g) cudaGraphDestroy(g);
+  g = nullptr;
+  // ---- profiled iteration graph
+  if (s == OPM_OK && R.profile) {
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      s = OPM_ERR_CUDA;
+    } else {
+      for (int it = 0; it < R.chunk; ++it) launch_iteration(R, cap, &R.kev[6 * it]);
+      k_results<<<results_blocks(R), 128, 0, cap>>>(R.B, R.d_res);
+      if (cudaStreamEndCapture(cap, &g) != cudaSuccess || cudaGraphInstantiate(&R.iter_exec, g, 0) != cudaSuccess)
+        s = OPM_ERR_CUDA;
+    }
+  }
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cap);
-  if (e != cudaSuccess) {
-    fprintf(stderr, "opm_bsr: graph capture failed: %s\n", cudaGetErrorString(e));
+  if (s != OPM_OK) {
+    fprintf(stderr, "opm_bsr: graph construction failed: %s\n", cudaGetErrorString(cudaGetLastError()));
     cudaGetLastError();
-    return OPM_ERR_CUDA;
   }
+  return s;
+}
+
+void runner_destroy(Runner *R) {
+  if (!R) return;
+  cudaStreamSynchronize(R->stream);
+  if (R->solve_exec) cudaGraphExecDestroy(R->solve_exec);
+  if (R->iter_exec) cudaGraphExecDestroy(R->iter_exec);
+  if (R->factor_exec) cudaGraphExecDestroy(R->factor_exec);
+  for (void *p : R->allocs) cudaFree(p);
+  if (R->h_sys) cudaFreeHost(R->h_sys);
+  if (R->h_res) cudaFreeHost(R->h_res);
+  for (auto &e : R->kev)
+    if (e) cudaEventDestroy(e);
+  if (R->ev_done) cudaEventDestroy(R->ev_done);
+  delete R;
+}
+
+// Work lists and graphs for a set of analysed, allocated systems.
+opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stream, int chunk, bool profile,
+                         int sweep_launch, uint64_t spin_ns, int skip_cta, Runner **out) {
+  *out = nullptr;
+  Runner *R = new (std::nothrow) Runner();
+  if (!R) return OPM_ERR_OOM;
+  auto fail = [&](opm_status s) {
+    runner_destroy(R);
+    return s;
+  };
+  R->mem = mem;
+  R->stream = stream;
+  R->nsys = (int)mem.size();
+  R->fp32 = mem[0]->fp32;
+  R->chunk = chunk;
+  R->profile = profile;
+  if (cudaGetDevice(&R->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OPM_ERR_CUDA);
+  }
+  int maxp = 0;
+  for (auto *h : mem) maxp = std::max(maxp, (int)h->an.phase_ptr.size() - 1);
+  R->nphases = maxp;
+  // ---- sweep work lists: forward entries of every phase, then backward ones
+  std::vector<int4> ent;
+  R->fwd_ptr.assign(1, 0);
+  int max_entries = 1;
+  for (int c = 0; c < maxp; ++c) {
+    for (int s = 0; s < R->nsys; ++s) {
+      const auto &pp = mem[s]->an.phase_ptr;
+      const int np = (int)pp.size() - 1;
+      if (c >= np) continue;
+      const int r0 = pp[c], r1 = pp[c + 1];
+      const int last = (c == np - 1) ? (int)0x80000000u : 0;
+      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) ent.push_back(make_int4(s, sl, r0, r1 | last));
+    }
+    R->fwd_ptr.push_back((int)ent.size());
+    max_entries = std::max(max_entries, R->fwd_ptr[c + 1] - R->fwd_ptr[c]);
+  }
+  R->bwd_ptr.assign(1, (int)ent.size());
+  for (int c = 0; c < maxp; ++c) {
+    for (int s = 0; s < R->nsys; ++s) {
+      const auto &pp = mem[s]->an.phase_ptr;
+      const int np = (int)pp.size() - 1;
+      if (c > np - 2) continue;
+      const int r0 = pp[c], r1 = pp[c + 1];
+      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) ent.push_back(make_int4(s, sl, r0, r1));
+    }
+    R->bwd_ptr.push_back((int)ent.size());
+  }
+  std::vector<int2> tiles;
+  for (int s = 0; s < R->nsys; ++s)
+    for (int t = 0; t < mem[s]->ntiles; ++t) tiles.push_back(make_int2(s, t));
+  R->ntiles = (int)tiles.size();
+  R->cooperative =
+      sweep_launch == OPM_SWEEP_COOPERATIVE || (sweep_launch == OPM_SWEEP_AUTO && maxp > kMaxPhaseLaunches);
+  // ---- device copies
+  opm_status s;
+  int4 *d_ent;
+  int32_t *d_fwd, *d_bwd;
+  int2 *d_tiles;
+  uint32_t *d_bar;
+  Sys *d_sys;
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_ent, ent)) != OPM_OK) return fail(s);
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_fwd, R->fwd_ptr)) != OPM_OK) return fail(s);
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_bwd, R->bwd_ptr)) != OPM_OK) return fail(s);
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles, tiles)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, &d_bar, 64)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, &d_sys, (size_t)R->nsys)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, &R->d_res, (size_t)R->nsys)) != OPM_OK) return fail(s);
+  if (cudaMemsetAsync(d_bar, 0, 64 * sizeof(uint32_t), stream) != cudaSuccess) return fail(OPM_ERR_CUDA);
+  if (cudaMallocHost((void **)&R->h_sys, sizeof(Sys) * R->nsys) != cudaSuccess ||
+      cudaMallocHost((void **)&R->h_res, sizeof(Result) * R->nsys) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OPM_ERR_OOM);
+  }
+  if (cudaEventCreateWithFlags(&R->ev_done, cudaEventDisableTiming) != cudaSuccess) return fail(OPM_ERR_CUDA);
+  R->B.sys = d_sys;
+  R->B.ent = d_ent;
+  R->B.fwd_ptr = d_fwd;
+  R->B.bwd_ptr = d_bwd;
+  R->B.tiles = d_tiles;
+  R->B.bar = d_bar;
+  R->B.nsys = R->nsys;
+  R->B.nphases = maxp;
+  R->B.ntiles = R->ntiles;
+  R->B.skip_cta = skip_cta;
+  R->B.spin_limit_ns = spin_ns;
+  if (R->fp32) cooperative_grids<float>(*R, max_entries);
+  else cooperative_grids<double>(*R, max_entries);
+  if (profile) {
+    R->kev.assign((size_t)6 * chunk, nullptr);
+    for (auto &e : R->kev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OPM_ERR_CUDA);
+      }
+  }
+  if ((s = build_graphs(*R)) != OPM_OK) return fail(s);
+  if (cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OPM_ERR_CUDA);
+  }
+  *out = R;
   return OPM_OK;
 }
 
-opm_status read_state(opm_solver *h) {
-  CK(cudaMemcpyAsync(h->h_state, h->sys.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+// Copy the members' descriptors (with their per-call fields) to the device.
+opm_status runner_push(Runner &R) {
+  for (int s = 0; s < R.nsys; ++s) R.h_sys[s] = R.mem[s]->sys;
+  CK(cudaMemcpyAsync((void *)R.B.sys, R.h_sys, sizeof(Sys) * R.nsys, cudaMemcpyHostToDevice, R.stream));
   return OPM_OK;
 }
 
-// Copies a caller vector of 3n doubles to device staging when it is host
-// memory; returns the device pointer to read from.
-opm_status stage_in(opm_solver *h, const double *src, const double **dev) {
+opm_status runner_pull_results(Runner &R) {
+  CK(cudaMemcpyAsync(R.h_res, R.d_res, sizeof(Result) * R.nsys, cudaMemcpyDeviceToHost, R.stream));
+  return OPM_OK;
+}
+
+// Enqueue (no host wait): optional factorisation, then an optional solve.
+opm_status runner_enqueue(Runner &R, bool factor, bool solve) {
+  opm_status s = runner_push(R);
+  if (s != OPM_OK) return s;
+  if (factor) CK(cudaGraphLaunch(R.factor_exec, R.stream));
+  if (solve) CK(cudaGraphLaunch(R.solve_exec, R.stream));
+  if ((s = runner_pull_results(R)) != OPM_OK) return s;
+  CK(cudaEventRecord(R.ev_done, R.stream));
+  return OPM_OK;
+}
+
+opm_status runner_wait(Runner &R) {
+  CK(cudaEventSynchronize(R.ev_done));
+  return OPM_OK;
+}
+
+// Kernel launches of one solve-graph execution, for the launch counter.
+int64_t solve_graph_launches(const Runner &R) {
+  int maxit = 1;
+  for (int s = 0; s < R.nsys; ++s) maxit = std::max(maxit, R.h_res[s].iters);
+  const int64_t bodies = (maxit + R.chunk - 1) / R.chunk;
+  return 3 + bodies * ((int64_t)R.iter_launches * R.chunk + 1);
+}
+
+// Host-driven solve with per-kernel events (profiling).
+opm_status runner_solve_profiled(Runner &R, opm_timing &t) {
+  opm_status s = runner_push(R);
+  if (s != OPM_OK) return s;
+  cudaEvent_t e0 = R.kev[0], e1 = R.kev[1];
+  CK(cudaEventRecord(e0, R.stream));
+  k_setup<<<R.ntiles, 256, 0, R.stream>>>(R.B);
+  CK(cudaEventRecord(e1, R.stream));
+  CK(cudaStreamSynchronize(R.stream));
+  add_kernel_time(t, OPM_KERNEL_SETUP, e0, e1);
+  t.launches += 1;
+  std::vector<int> k_before(R.nsys, 0);
+  for (;;) {
+    CK(cudaGraphLaunch(R.iter_exec, R.stream));
+    t.launches += (int64_t)R.iter_launches * R.chunk + 1;
+    if ((s = runner_pull_results(R)) != OPM_OK) return s;
+    CK(cudaStreamSynchronize(R.stream));
+    // iterations of this chunk that did work: up to the last system's finish
+    int ran = 0;
+    bool any = false;
+    for (int q = 0; q < R.nsys; ++q) {
+      if (R.h_res[q].status == kRunning) {
+        any = true;
+        ran = R.chunk;
+      } else {
+        ran = std::max(ran, std::min(R.chunk, R.h_res[q].iters - k_before[q]));
+      }
+    }
+    for (int it = 0; it < ran; ++it)
+      for (int q = 0; q < 5; ++q) add_kernel_time(t, kIterKernel[q], R.kev[6 * it + q], R.kev[6 * it + q + 1]);
+    for (int q = 0; q < R.nsys; ++q) k_before[q] = R.h_res[q].iters;
+    if (!any) break;
+  }
+  CK(cudaEventRecord(e0, R.stream));
+  k_finish<<<R.ntiles, 1024, 0, R.stream>>>(R.B);
+  CK(cudaEventRecord(e1, R.stream));
+  k_results<<<results_blocks(R), 128, 0, R.stream>>>(R.B, R.d_res);
+  t.launches += 2;
+  if ((s = runner_pull_results(R)) != OPM_OK) return s;
+  CK(cudaStreamSynchronize(R.stream));
+  add_kernel_time(t, OPM_KERNEL_FINISH, e0, e1);
+  return OPM_OK;
+}
+
+// ---------------------------------------------------------------- handles
+
+opm_status staged_vals(opm_solver *h, const double *vals, const double **dev) {
+  *dev = nullptr;
+  if (!vals) return OPM_OK;
+  if (is_device_ptr(vals)) {
+    *dev = vals;
+    return OPM_OK;
+  }
+  if (!h->vals_stage) {
+    opm_status s = dalloc(h->allocs, h->dev_bytes, &h->vals_stage, 9 * (size_t)h->nnzb);
+    if (s != OPM_OK) return s;
+  }
+  CK(cudaMemcpyAsync(h->vals_stage, vals, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyHostToDevice,
+                     h->stream));
+  *dev = h->vals_stage;
+  return OPM_OK;
+}
+
+opm_status staged_vec(opm_solver *h, const double *src, const double **dev) {
   if (is_device_ptr(src)) {
     *dev = src;
     return OPM_OK;
@@ -280,42 +587,147 @@ opm_status stage_in(opm_solver *h, const double *src, const double **dev) {
 }
 
 opm_status factor_impl(opm_solver *h, const double *vals) {
-  const double *dv = nullptr;
-  if (vals) {
-    if (is_device_ptr(vals)) {
-      dv = vals;
-    } else {
-      if (!h->vals_stage) {
-        opm_status s = dalloc(h, &h->vals_stage, 9 * (size_t)h->nnzb);
-        if (s != OPM_OK) return s;
-      }
-      CK(cudaMemcpyAsync(h->vals_stage, vals, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyHostToDevice,
-                         h->stream));
-      dv = h->vals_stage;
-    }
-  }
   h->factors_ok = false;
+  h->last_err_row = -1;
   if (h->n == 0) {
     h->factors_ok = true;
     return OPM_OK;
   }
-  k_begin_factor<<<1, 1, 0, h->stream>>>(h->sys.st);
-  CK(cudaEventRecord(h->ev[4], h->stream));
-  const int nl = h->fp32 ? launch_factor<float>(h, dv, h->stream) : launch_factor<double>(h, dv, h->stream);
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[5], h->stream));
-  h->timing.launches += 1 + nl;
-  opm_status s = read_state(h);
+  const double *dv = nullptr;
+  opm_status s = staged_vals(h, vals, &dv);
   if (s != OPM_OK) return s;
-  cudaEventElapsedTime(&h->timing.factor_ms, h->ev[4], h->ev[5]);
-  if (h->opt.profile_kernels) add_kernel_time(h, OPM_KERNEL_FACTOR, h->ev[4], h->ev[5]);
-  if (h->h_state->error != 0) {
-    int32_t r = h->h_state->err_row;
-    h->last_err_row = (r >= 0 && r < h->n) ? h->an.perm[r] : -1;
-    return (opm_status)h->h_state->error;
+  h->sys.vals_in = dv;
+  Runner &R = *h->run;
+  CK(cudaEventRecord(h->ev[0], h->stream));
+  s = runner_enqueue(R, true, false);
+  h->sys.vals_in = nullptr;
+  if (s != OPM_OK) return s;
+  CK(cudaEventRecord(h->ev[1], h->stream));
+  if ((s = runner_wait(R)) != OPM_OK) return s;
+  CK(cudaEventSynchronize(h->ev[1]));
+  cudaEventElapsedTime(&h->timing.factor_ms, h->ev[0], h->ev[1]);
+  h->timing.launches += R.factor_launches;
+  if (h->opt.profile_kernels) add_kernel_time(h->timing, OPM_KERNEL_FACTOR, h->ev[0], h->ev[1]);
+  const Result &r = R.h_res[0];
+  if (r.status < 0) {
+    const int32_t row = r.err_row;
+    h->last_err_row = (row >= 0 && row < h->n) ? h->an.perm[row] : -1;
+    return (opm_status)r.status;
   }
   h->factors_ok = true;
   return OPM_OK;
+}
+
+opm_status alloc_system(opm_solver *h) {
+  Analysis &an = h->an;
+  Sys &S = h->sys;
+  const int32_t nb = h->n;
+  std::vector<void *> &A = h->allocs;
+  int64_t &bytes = h->dev_bytes;
+  cudaStream_t st = h->stream;
+  S.n = nb;
+  S.nslices = h->nslices;
+  S.ntiles = h->ntiles;
+  S.nphases = (int32_t)an.phase_ptr.size() - 1;
+  S.u_off = 9 * an.nnz_l;
+  S.d_off = an.d_off;
+  opm_status s;
+  int32_t *p_perm, *p_arp, *p_acol, *p_asrc, *p_lrp, *p_lcol, *p_urp, *p_ucol, *p_upd;
+  int64_t *p_adst, *p_ud, *p_us;
+#define UP(ptr, vec) \
+  if ((s = upload(A, bytes, st, &ptr, vec)) != OPM_OK) return s
+  UP(p_perm, an.perm);
+  UP(p_arp, an.a_rowptr);
+  UP(p_acol, an.a_col);
+  UP(p_asrc, an.a_src);
+  UP(p_adst, an.a_dst);
+  UP(p_lrp, an.l_rowptr);
+  UP(p_lcol, an.l_col);
+  UP(p_urp, an.u_rowptr);
+  UP(p_ucol, an.u_col);
+  UP(p_upd, an.upd_ptr);
+  UP(p_ud, an.upd_dst);
+  UP(p_us, an.upd_src);
+#undef UP
+  S.perm = p_perm;
+  S.a_rp = p_arp;
+  S.a_col = p_acol;
+  S.a_src = p_asrc;
+  S.a_dst = p_adst;
+  S.l_rp = p_lrp;
+  S.l_col = p_lcol;
+  S.u_rp = p_urp;
+  S.u_col = p_ucol;
+  S.upd_ptr = p_upd;
+  S.upd_dst = p_ud;
+  S.upd_src = p_us;
+  if ((s = dalloc(A, bytes, &S.a_val, 9 * (size_t)h->nnzb)) != OPM_OK) return s;
+  if (h->fp32) {
+    float *lu, *y;
+    if ((s = dalloc(A, bytes, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, &y, 3 * (size_t)nb)) != OPM_OK) return s;
+    S.lu = lu;
+    S.y = y;
+  } else {
+    double *lu, *y;
+    if ((s = dalloc(A, bytes, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, &y, 3 * (size_t)nb)) != OPM_OK) return s;
+    S.lu = lu;
+    S.y = y;
+  }
+  double **vecs[] = {&S.x, &S.r, &S.rh, &S.p, &S.v, &S.ph, &S.s, &S.sh, &S.t, &S.w, &h->vec_in, &h->vec_out};
+  for (double **pv : vecs)
+    if ((s = dalloc(A, bytes, pv, 3 * (size_t)nb)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, &S.partials, 4 * (size_t)h->ntiles)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, &S.st, 1)) != OPM_OK) return s;
+  DevState init{};
+  init.status = OPM_OK;
+  CK(cudaMemcpyAsync(S.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  // free the host copies the device now holds (keep perm, phases and the factor slots)
+  std::vector<int32_t>().swap(an.a_col);
+  std::vector<int32_t>().swap(an.a_src);
+  std::vector<int64_t>().swap(an.a_dst);
+  std::vector<int32_t>().swap(an.l_col);
+  std::vector<int32_t>().swap(an.u_col);
+  std::vector<int32_t>().swap(an.upd_ptr);
+  std::vector<int64_t>().swap(an.upd_dst);
+  std::vector<int64_t>().swap(an.upd_src);
+  return OPM_OK;
+}
+
+opm_status check_options(const opm_options &o) {
+  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR) return OPM_ERR_ARG;
+  if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
+  if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
+  if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;
+  return OPM_OK;
+}
+
+uint64_t spin_ns(const opm_options &o) {
+  return (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
+}
+
+int chunk_of(const opm_options &o) { return o.chunk > 0 ? o.chunk : 2; }
+
+// Fills the handle's per-call fields for a solve; stages host vectors.
+opm_status prepare_solve(opm_solver *h, const double *b, double *x, double rtol, int32_t maxit, bool *x_dev) {
+  const double *db = nullptr;
+  opm_status s = staged_vec(h, b, &db);
+  if (s != OPM_OK) return s;
+  *x_dev = is_device_ptr(x);
+  h->sys.b_in = db;
+  h->sys.x_out = *x_dev ? x : h->vec_out;
+  h->sys.rtol = rtol;
+  h->sys.maxit = maxit;
+  h->sys.vals_in = nullptr;
+  return OPM_OK;
+}
+
+opm_status worst_status(opm_status a, opm_status b) {
+  if (a < 0) return a;
+  if (b < 0) return b;
+  return a != OPM_OK ? a : b;
 }
 
 }  // namespace
@@ -331,10 +743,11 @@ void opm_options_default(opm_options *opt) {
   opt->chunk = 0;
   opt->spin_limit_us = 0;
   opt->debug_skip_item = -1;
+  opt->sweep_launch = OPM_SWEEP_AUTO;
 }
 
 const char *opm_status_str(opm_status s) {
-  int v = (int)s;
+  const int v = (int)s;
   if (v == 0) return kStatusText[0];
   if (v == 1) return kStatusText[1];
   if (v <= -1 && v >= -9) return kStatusText[1 - v];
@@ -343,13 +756,10 @@ const char *opm_status_str(opm_status s) {
 
 void opm_destroy(opm_handle h) {
   if (!h) return;
+  if (h->run) runner_destroy(h->run);
   if (!h->allocs.empty()) cudaStreamSynchronize(h->stream);
-  if (h->chunk_exec) cudaGraphExecDestroy(h->chunk_exec);
   for (void *p : h->allocs) cudaFree(p);
-  if (h->h_state) cudaFreeHost(h->h_state);
   for (auto &e : h->ev)
-    if (e) cudaEventDestroy(e);
-  for (auto &e : h->kev)
     if (e) cudaEventDestroy(e);
   delete h;
 }
@@ -363,17 +773,13 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   opm_options o;
   opm_options_default(&o);
   if (opt) o = *opt;
-  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR) return OPM_ERR_ARG;
-  if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
-  if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
-  if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;
+  if (check_options(o) != OPM_OK) return OPM_ERR_ARG;
 
   opm_solver *h = new (std::nothrow) opm_solver();
   if (!h) return OPM_ERR_OOM;
   h->opt = o;
   h->stream = (cudaStream_t)o.stream;
   h->fp32 = o.precision == OPM_PREC_FP32_FACTORS;
-  h->chunk = o.chunk > 0 ? o.chunk : 8;
   auto fail = [&](opm_status s) {
     opm_destroy(h);
     return s;
@@ -400,6 +806,7 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   opm_status s = analyse(nb, rp, ci, o.schedule, h->an, &err_row);
   t_create_err_row = err_row;
   if (s != OPM_OK) return fail(s);
+
   // ---- CUDA resources (after the host checks, which need no device)
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
@@ -410,116 +817,21 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
       cudaGetLastError();
       return fail(OPM_ERR_CUDA);
     }
-  if (cudaMallocHost((void **)&h->h_state, sizeof(DevState)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(OPM_ERR_OOM);
-  }
-  Analysis &an = h->an;
   h->n = nb;
   h->nnzb = nnzb;
   h->nslices = (nb + kWarp - 1) / kWarp;
-  h->ntiles = blocks_for(nb);
-
-  // ---- device buffers
-  Sys &S = h->sys;
-  S.n = nb;
-  S.nslices = h->nslices;
-  S.u_off = 9 * an.nnz_l;
-  S.d_off = an.d_off;
-  S.spin_limit_ns = (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
-  S.skip_cta = o.debug_skip_item;
-  int32_t *p_perm, *p_arp, *p_acol, *p_asrc, *p_lrp, *p_lcol, *p_urp, *p_ucol, *p_upd;
-  int32_t *p_ph;
-  int64_t *p_adst, *p_ud, *p_us;
-#define UP(ptr, vec) \
-  if ((s = upload(h, &ptr, vec)) != OPM_OK) return fail(s)
-  UP(p_perm, an.perm);
-  UP(p_arp, an.a_rowptr);
-  UP(p_acol, an.a_col);
-  UP(p_asrc, an.a_src);
-  UP(p_adst, an.a_dst);
-  UP(p_lrp, an.l_rowptr);
-  UP(p_lcol, an.l_col);
-  UP(p_urp, an.u_rowptr);
-  UP(p_ucol, an.u_col);
-  UP(p_upd, an.upd_ptr);
-  UP(p_ud, an.upd_dst);
-  UP(p_us, an.upd_src);
-  UP(p_ph, an.phase_ptr);
-#undef UP
-  S.phase_ptr = p_ph;
-  S.nphases = (int32_t)an.phase_ptr.size() - 1;
-  S.perm = p_perm;
-  S.a_rp = p_arp;
-  S.a_col = p_acol;
-  S.a_src = p_asrc;
-  S.a_dst = p_adst;
-  S.l_rp = p_lrp;
-  S.l_col = p_lcol;
-  S.u_rp = p_urp;
-  S.u_col = p_ucol;
-  S.upd_ptr = p_upd;
-  S.upd_dst = p_ud;
-  S.upd_src = p_us;
-  if ((s = dalloc(h, &S.a_val, 9 * (size_t)nnzb)) != OPM_OK) return fail(s);
-  if (h->fp32) {
-    float *lu;
-    if ((s = dalloc(h, &lu, (size_t)an.lu_vals)) != OPM_OK) return fail(s);
-    S.lu = lu;
-    float *y;
-    if ((s = dalloc(h, &y, 3 * (size_t)nb)) != OPM_OK) return fail(s);
-    S.y = y;
-  } else {
-    double *lu;
-    if ((s = dalloc(h, &lu, (size_t)an.lu_vals)) != OPM_OK) return fail(s);
-    S.lu = lu;
-    double *y;
-    if ((s = dalloc(h, &y, 3 * (size_t)nb)) != OPM_OK) return fail(s);
-    S.y = y;
+  h->ntiles = std::max(1, (nb + kTileRows - 1) / kTileRows);
+  if (nb == 0) {
+    h->factors_ok = true;
+    *out = h;
+    return OPM_OK;
   }
-  double **vecs[] = {&S.x, &S.r, &S.rh, &S.p, &S.v, &S.ph, &S.s, &S.sh, &S.t, &S.w, &h->vec_in, &h->vec_out};
-  for (double **pv : vecs)
-    if ((s = dalloc(h, pv, 3 * (size_t)nb)) != OPM_OK) return fail(s);
-  if ((s = dalloc(h, &S.partials, 4 * (size_t)h->ntiles)) != OPM_OK) return fail(s);
-  if ((s = dalloc(h, &S.st, 1)) != OPM_OK) return fail(s);
-  {
-    DevState init{};
-    init.status = OPM_OK;
-    *h->h_state = init;
-    if (cudaMemcpyAsync(S.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-      return fail(OPM_ERR_CUDA);
-  }
-  h->cooperative = o.sweep_launch == OPM_SWEEP_COOPERATIVE ||
-                   (o.sweep_launch == OPM_SWEEP_AUTO && S.nphases > kMaxPhaseLaunches);
-  const int mps = max_phase_slices(an);
-  if (h->fp32) {
-    h->grid_apply = apply_grid<float>(h->device, mps);
-    h->grid_factor = resident_grid(k_factor<float>, h->device, mps);
-  } else {
-    h->grid_apply = apply_grid<double>(h->device, mps);
-    h->grid_factor = resident_grid(k_factor<double>, h->device, mps);
-  }
-  // free the host copies the device now holds (keep perm and the factor slots)
-  std::vector<int32_t>().swap(an.a_col);
-  std::vector<int32_t>().swap(an.a_src);
-  std::vector<int64_t>().swap(an.a_dst);
-  std::vector<int32_t>().swap(an.l_col);
-  std::vector<int32_t>().swap(an.u_col);
-  std::vector<int32_t>().swap(an.upd_ptr);
-  std::vector<int64_t>().swap(an.upd_dst);
-  std::vector<int64_t>().swap(an.upd_src);
-
-
-  if (o.profile_kernels && nb > 0) {
-    h->kev.assign((size_t)6 * h->chunk, nullptr);
-    for (auto &e : h->kev)
-      if (cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(OPM_ERR_CUDA);
-      }
-  }
-  if (nb > 0 && (s = build_graph(h)) != OPM_OK) return fail(s);
-  s = factor_impl(h, nb > 0 ? vals : nullptr);
+  if ((s = alloc_system(h)) != OPM_OK) return fail(s);
+  std::vector<opm_solver *> one{h};
+  if ((s = runner_create(one, h->stream, chunk_of(o), o.profile_kernels != 0, o.sweep_launch, spin_ns(o),
+                         o.debug_skip_item, &h->run)) != OPM_OK)
+    return fail(s);
+  s = factor_impl(h, vals);
   if (s == OPM_ERR_ZERO_PIVOT) {
     // the handle stays usable: the row can be read and new values factored
     *out = h;
@@ -531,106 +843,132 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
 }
 
 opm_status opm_ilu0_factor(opm_handle h, const double *vals) {
-  if (!h) return OPM_ERR_ARG;
-  h->last_err_row = -1;
+  if (!h || h->async_pending) return OPM_ERR_ARG;
   return factor_impl(h, vals);
 }
 
 opm_status opm_bicgstab_solve(opm_handle h, const double *b, double *x, double rtol, int32_t maxit,
                               int32_t *iters, double *relres) {
-  if (!h || (h->n > 0 && (!b || !x)) || !(rtol >= 0.0)) return OPM_ERR_ARG;
+  if (!h || (h->n > 0 && (!b || !x)) || !(rtol >= 0.0) || h->async_pending) return OPM_ERR_ARG;
   if (iters) *iters = 0;
   if (relres) *relres = 0.0;
   if (h->n == 0) return OPM_OK;
   if (!h->factors_ok) return OPM_ERR_ZERO_PIVOT;
-  const size_t vbytes = sizeof(double) * 3 * (size_t)h->n;
-  const double *db = nullptr;
-  opm_status s = stage_in(h, b, &db);
+  bool x_dev = false;
+  opm_status s = prepare_solve(h, b, x, rtol, maxit, &x_dev);
   if (s != OPM_OK) return s;
-  const bool x_dev = is_device_ptr(x);
-  double *dx = x_dev ? x : h->vec_out;
-  cudaStream_t st = h->stream;
-  CK(cudaEventRecord(h->ev[0], st));
-  k_setup<<<h->ntiles, 256, 0, st>>>(h->sys, db, rtol, maxit);
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(h->ev[1], st));
-  h->timing.launches += 1;
-  if ((s = read_state(h)) != OPM_OK) return s;
-  while (h->h_state->status == kRunning && h->h_state->error == 0) {
-    const int k_before = h->h_state->k;
-    CK(cudaGraphLaunch(h->chunk_exec, st));
-    h->timing.launches += h->chunk_launches;
-    if ((s = read_state(h)) != OPM_OK) return s;
-    if (!h->kev.empty()) {
-      // iterations of this chunk that did work
-      int ran = h->chunk;
-      if (h->h_state->status != kRunning || h->h_state->error != 0)
-        ran = std::max(0, std::min(h->chunk, h->h_state->iters - k_before + 1));
-      for (int it = 0; it < ran; ++it)
-        for (int q = 0; q < 5; ++q) add_kernel_time(h, kIterKernel[q], h->kev[6 * it + q], h->kev[6 * it + q + 1]);
-    }
-  }
-  CK(cudaEventRecord(h->ev[2], st));
-  int32_t status = h->h_state->error != 0 ? h->h_state->error : h->h_state->status;
-  if (status == OPM_OK || status == OPM_NOT_CONVERGED) {
-    k_finish<<<h->ntiles, 1024, 0, st>>>(h->sys, db, dx);
-    CK(cudaGetLastError());
-    if (!x_dev) CK(cudaMemcpyAsync(x, dx, vbytes, cudaMemcpyDeviceToHost, st));
-  } else if (x_dev) {
-    CK(cudaMemsetAsync(x, 0, vbytes, st));
+  Runner &R = *h->run;
+  const size_t vbytes = sizeof(double) * 3 * (size_t)h->n;
+  CK(cudaEventRecord(h->ev[0], h->stream));
+  if (R.profile) {
+    if ((s = runner_solve_profiled(R, h->timing)) != OPM_OK) return s;
   } else {
-    memset(x, 0, vbytes);
+    if ((s = runner_enqueue(R, false, true)) != OPM_OK) return s;
+    if ((s = runner_wait(R)) != OPM_OK) return s;
+    h->timing.launches += solve_graph_launches(R);
   }
-  CK(cudaEventRecord(h->ev[3], st));
-  if (status == OPM_OK || status == OPM_NOT_CONVERGED) h->timing.launches += 1;
-  if ((s = read_state(h)) != OPM_OK) return s;
-  if (h->opt.profile_kernels) {
-    add_kernel_time(h, OPM_KERNEL_SETUP, h->ev[0], h->ev[1]);
-    if (status == OPM_OK || status == OPM_NOT_CONVERGED) add_kernel_time(h, OPM_KERNEL_FINISH, h->ev[2], h->ev[3]);
+  if (!x_dev) CK(cudaMemcpyAsync(x, h->vec_out, vbytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaEventRecord(h->ev[1], h->stream));
+  CK(cudaEventSynchronize(h->ev[1]));
+  cudaEventElapsedTime(&h->timing.iterate_ms, h->ev[0], h->ev[1]);
+  h->timing.setup_ms = 0.f;
+  h->timing.finish_ms = 0.f;
+  const Result &r = R.h_res[0];
+  if (iters) *iters = r.iters;
+  if (relres) *relres = r.relres;
+  return (opm_status)r.status;
+}
+
+opm_status opm_solve_launch(opm_handle h, const double *vals, const double *b, double *x, double rtol,
+                            int32_t maxit) {
+  if (!h || h->n == 0 || !b || !x || !(rtol >= 0.0) || h->async_pending || h->run->profile) return OPM_ERR_ARG;
+  if (!is_device_ptr(b) || !is_device_ptr(x) || (vals && !is_device_ptr(vals))) return OPM_ERR_ARG;
+  if (!vals && !h->factors_ok) return OPM_ERR_ZERO_PIVOT;
+  h->sys.b_in = b;
+  h->sys.x_out = x;
+  h->sys.rtol = rtol;
+  h->sys.maxit = maxit;
+  h->sys.vals_in = vals;
+  opm_status s = runner_enqueue(*h->run, vals != nullptr, true);
+  h->sys.vals_in = nullptr;
+  if (s != OPM_OK) return s;
+  h->async_pending = true;
+  h->timing.launches += vals ? h->run->factor_launches : 0;
+  return OPM_OK;
+}
+
+int32_t opm_solve_ready(opm_handle h) {
+  if (!h || !h->async_pending) return 1;
+  const cudaError_t e = cudaEventQuery(h->run->ev_done);
+  if (e == cudaErrorNotReady) return 0;
+  cudaGetLastError();
+  return 1;
+}
+
+opm_status opm_solve_wait(opm_handle h, int32_t *iters, double *relres) {
+  if (!h || !h->async_pending) return OPM_ERR_ARG;
+  Runner &R = *h->run;
+  h->async_pending = false;
+  opm_status s = runner_wait(R);
+  if (s != OPM_OK) return s;
+  const Result &r = R.h_res[0];
+  h->timing.launches += solve_graph_launches(R);
+  if (r.status == OPM_ERR_ZERO_PIVOT) {
+    h->factors_ok = false;
+    h->last_err_row = (r.err_row >= 0 && r.err_row < h->n) ? h->an.perm[r.err_row] : -1;
+  } else {
+    h->factors_ok = true;
   }
-  cudaEventElapsedTime(&h->timing.setup_ms, h->ev[0], h->ev[1]);
-  cudaEventElapsedTime(&h->timing.iterate_ms, h->ev[1], h->ev[2]);
-  cudaEventElapsedTime(&h->timing.finish_ms, h->ev[2], h->ev[3]);
-  if (iters) *iters = h->h_state->iters;
-  if (relres) *relres = (status == OPM_OK || status == OPM_NOT_CONVERGED) ? h->h_state->relres : NAN;
-  return (opm_status)status;
+  if (iters) *iters = r.iters;
+  if (relres) *relres = r.relres;
+  return (opm_status)r.status;
 }
 
 opm_status opm_spmv(opm_handle h, const double *x, double *y) {
-  if (!h || (h->n > 0 && (!x || !y))) return OPM_ERR_ARG;
+  if (!h || (h->n > 0 && (!x || !y)) || h->async_pending) return OPM_ERR_ARG;
   if (h->n == 0) return OPM_OK;
   const double *dx = nullptr;
-  opm_status s = stage_in(h, x, &dx);
+  opm_status s = staged_vec(h, x, &dx);
   if (s != OPM_OK) return s;
   const bool y_dev = is_device_ptr(y);
-  double *dy = y_dev ? y : h->vec_out;
-  k_gather<<<h->ntiles, 256, 0, h->stream>>>(h->sys, dx, h->sys.w);
-  k_spmv_plain<<<h->ntiles, 1024, 0, h->stream>>>(h->sys, h->sys.w, dy);
+  h->sys.b_in = dx;
+  h->sys.x_out = y_dev ? y : h->vec_out;
+  Runner &R = *h->run;
+  if ((s = runner_push(R)) != OPM_OK) return s;
+  k_gather<<<R.ntiles, 256, 0, h->stream>>>(R.B);
+  k_spmv_plain<<<R.ntiles, 1024, 0, h->stream>>>(R.B);
   CK(cudaGetLastError());
   h->timing.launches += 2;
-  if (!y_dev) CK(cudaMemcpyAsync(y, dy, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+  if (!y_dev)
+    CK(cudaMemcpyAsync(y, h->vec_out, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return OPM_OK;
 }
 
 opm_status opm_ilu_apply(opm_handle h, const double *r, double *z) {
-  if (!h || (h->n > 0 && (!r || !z))) return OPM_ERR_ARG;
+  if (!h || (h->n > 0 && (!r || !z)) || h->async_pending) return OPM_ERR_ARG;
   if (h->n == 0) return OPM_OK;
   if (!h->factors_ok) return OPM_ERR_ZERO_PIVOT;
   const double *dr = nullptr;
-  opm_status s = stage_in(h, r, &dr);
+  opm_status s = staged_vec(h, r, &dr);
   if (s != OPM_OK) return s;
   const bool z_dev = is_device_ptr(z);
-  double *dz = z_dev ? z : h->vec_out;
-  k_begin_factor<<<1, 1, 0, h->stream>>>(h->sys.st);
-  k_gather<<<h->ntiles, 256, 0, h->stream>>>(h->sys, dr, h->sys.w);
-  const int nl = launch_apply_p<kModePlain>(h, h->sys.w, h->sys.t, h->stream);
-  k_scatter<<<h->ntiles, 256, 0, h->stream>>>(h->sys, h->sys.t, dz);
+  h->sys.b_in = dr;
+  h->sys.x_out = z_dev ? z : h->vec_out;
+  Runner &R = *h->run;
+  if ((s = runner_push(R)) != OPM_OK) return s;
+  k_gather<<<R.ntiles, 256, 0, h->stream>>>(R.B);
+  const int nl = launch_apply<kModePlain>(R, h->stream);
+  k_scatter<<<R.ntiles, 256, 0, h->stream>>>(R.B);
+  k_results<<<results_blocks(R), 128, 0, h->stream>>>(R.B, R.d_res);
   CK(cudaGetLastError());
   h->timing.launches += 3 + nl;
-  if (!z_dev) CK(cudaMemcpyAsync(z, dz, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
-  if ((s = read_state(h)) != OPM_OK) return s;
-  if (h->h_state->error != 0) return (opm_status)h->h_state->error;
+  if (!z_dev)
+    CK(cudaMemcpyAsync(z, h->vec_out, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+  if ((s = runner_pull_results(R)) != OPM_OK) return s;
+  CK(cudaStreamSynchronize(h->stream));
+  // only an expired bounded wait can fail here
+  if (R.h_res[0].status == OPM_ERR_TIMEOUT) return OPM_ERR_TIMEOUT;
   return OPM_OK;
 }
 
@@ -645,8 +983,8 @@ opm_status opm_get_info(opm_handle h, opm_info *info) {
   info->nnzb = h->nnzb;
   info->nnzb_lower = h->an.nnz_l;
   info->nnzb_upper = h->an.nnz_u;
-  info->device_bytes = h->dev_bytes;
-  info->nphases = h->sys.nphases;
+  info->device_bytes = h->dev_bytes + (h->run ? h->run->dev_bytes : 0);
+  info->nphases = h->n > 0 ? (int32_t)h->an.phase_ptr.size() - 1 : 0;
   info->reserved = 0;
   return OPM_OK;
 }
@@ -658,7 +996,7 @@ opm_status opm_get_permutation(opm_handle h, int32_t *perm) {
 }
 
 opm_status opm_get_factors(opm_handle h, double *lu, double *dinv) {
-  if (!h) return OPM_ERR_ARG;
+  if (!h || h->async_pending) return OPM_ERR_ARG;
   if (h->n == 0) return OPM_OK;
   const Analysis &an = h->an;
   std::vector<double> v((size_t)an.lu_vals);
@@ -701,6 +1039,166 @@ opm_status opm_reset_timing(opm_handle h) {
     h->timing.kernel_count[k] = 0;
   }
   return OPM_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+void opm_batch_destroy(opm_batch b) {
+  if (!b) return;
+  if (b->run) runner_destroy(b->run);
+  delete b;
+}
+
+opm_status opm_batch_create(int32_t nsys, const opm_handle *hs, const opm_options *opt, opm_batch *out) {
+  if (!out) return OPM_ERR_ARG;
+  *out = nullptr;
+  if (nsys < 1 || !hs) return OPM_ERR_ARG;
+  opm_options o;
+  opm_options_default(&o);
+  if (opt) o = *opt;
+  if (check_options(o) != OPM_OK) return OPM_ERR_ARG;
+  std::vector<opm_solver *> mem;
+  for (int i = 0; i < nsys; ++i) {
+    opm_solver *h = hs[i];
+    if (!h || h->n == 0 || !h->run || h->fp32 != hs[0]->fp32 || h->device != hs[0]->device) return OPM_ERR_ARG;
+    for (auto *m : mem)
+      if (m == h) return OPM_ERR_ARG;
+    mem.push_back(h);
+  }
+  opm_batch b = new (std::nothrow) opm_batch_s();
+  if (!b) return OPM_ERR_OOM;
+  b->members = mem;
+  opm_status s = runner_create(mem, (cudaStream_t)o.stream, chunk_of(o), false, o.sweep_launch, spin_ns(o),
+                               o.debug_skip_item, &b->run);
+  if (s != OPM_OK) {
+    opm_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return OPM_OK;
+}
+
+opm_status opm_batch_factor(opm_batch b, const double *const *vals, opm_status *st) {
+  if (!b || b->async_pending) return OPM_ERR_ARG;
+  Runner &R = *b->run;
+  opm_status s;
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    if (h->async_pending) return OPM_ERR_ARG;
+    const double *dv = nullptr;
+    if ((s = staged_vals(h, vals ? vals[i] : nullptr, &dv)) != OPM_OK) return s;
+    h->sys.vals_in = dv;
+  }
+  // host-to-device staging ran on the members' streams: complete it first
+  for (auto *h : b->members) CK(cudaStreamSynchronize(h->stream));
+  s = runner_enqueue(R, true, false);
+  for (auto *h : b->members) h->sys.vals_in = nullptr;
+  if (s != OPM_OK) return s;
+  if ((s = runner_wait(R)) != OPM_OK) return s;
+  opm_status worst = OPM_OK;
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    const Result &r = R.h_res[i];
+    if (r.status < 0) {
+      h->factors_ok = false;
+      h->last_err_row = (r.err_row >= 0 && r.err_row < h->n) ? h->an.perm[r.err_row] : -1;
+      if (st) st[i] = (opm_status)r.status;
+      worst = worst_status(worst, (opm_status)r.status);
+    } else {
+      h->factors_ok = true;
+      h->last_err_row = -1;
+      if (st) st[i] = OPM_OK;
+    }
+  }
+  return worst;
+}
+
+opm_status opm_batch_solve(opm_batch b, const double *const *bv, double *const *xv, const double *rtol,
+                           int32_t maxit, int32_t *iters, double *relres, opm_status *st) {
+  if (!b || !bv || !xv || b->async_pending) return OPM_ERR_ARG;
+  Runner &R = *b->run;
+  std::vector<char> x_dev(R.nsys);
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    if (!bv[i] || !xv[i] || h->async_pending) return OPM_ERR_ARG;
+    const double rt = rtol ? rtol[i] : 1e-2;
+    if (!(rt >= 0.0)) return OPM_ERR_ARG;
+    if (!h->factors_ok) return OPM_ERR_ZERO_PIVOT;
+    bool xd = false;
+    opm_status s = prepare_solve(h, bv[i], xv[i], rt, maxit, &xd);
+    if (s != OPM_OK) return s;
+    x_dev[i] = xd;
+  }
+  for (auto *h : b->members) CK(cudaStreamSynchronize(h->stream));
+  opm_status s = runner_enqueue(R, false, true);
+  if (s != OPM_OK) return s;
+  if ((s = runner_wait(R)) != OPM_OK) return s;
+  opm_status worst = OPM_OK;
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    if (!x_dev[i]) CK(cudaMemcpy(xv[i], h->vec_out, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost));
+    const Result &r = R.h_res[i];
+    if (iters) iters[i] = r.iters;
+    if (relres) relres[i] = r.relres;
+    if (st) st[i] = (opm_status)r.status;
+    worst = worst_status(worst, (opm_status)r.status);
+  }
+  return worst;
+}
+
+opm_status opm_batch_launch(opm_batch b, const double *const *vals, const double *const *bv, double *const *xv,
+                            const double *rtol, int32_t maxit) {
+  if (!b || !bv || !xv || b->async_pending) return OPM_ERR_ARG;
+  Runner &R = *b->run;
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    const double *v = vals ? vals[i] : nullptr;
+    const double rt = rtol ? rtol[i] : 1e-2;
+    if (!bv[i] || !xv[i] || !is_device_ptr(bv[i]) || !is_device_ptr(xv[i]) || (v && !is_device_ptr(v)) ||
+        !(rt >= 0.0) || h->async_pending)
+      return OPM_ERR_ARG;
+    if (!vals && !h->factors_ok) return OPM_ERR_ZERO_PIVOT;
+  }
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    h->sys.b_in = bv[i];
+    h->sys.x_out = xv[i];
+    h->sys.rtol = rtol ? rtol[i] : 1e-2;
+    h->sys.maxit = maxit;
+    h->sys.vals_in = vals ? vals[i] : nullptr;
+  }
+  opm_status s = runner_enqueue(R, vals != nullptr, true);
+  for (auto *h : b->members) h->sys.vals_in = nullptr;
+  if (s != OPM_OK) return s;
+  b->async_pending = true;
+  return OPM_OK;
+}
+
+int32_t opm_batch_ready(opm_batch b) {
+  if (!b || !b->async_pending) return 1;
+  const cudaError_t e = cudaEventQuery(b->run->ev_done);
+  if (e == cudaErrorNotReady) return 0;
+  cudaGetLastError();
+  return 1;
+}
+
+opm_status opm_batch_wait(opm_batch b, int32_t *iters, double *relres, opm_status *st) {
+  if (!b || !b->async_pending) return OPM_ERR_ARG;
+  Runner &R = *b->run;
+  b->async_pending = false;
+  opm_status s = runner_wait(R);
+  if (s != OPM_OK) return s;
+  opm_status worst = OPM_OK;
+  for (int i = 0; i < R.nsys; ++i) {
+    opm_solver *h = b->members[i];
+    const Result &r = R.h_res[i];
+    h->factors_ok = r.status != OPM_ERR_ZERO_PIVOT;
+    if (iters) iters[i] = r.iters;
+    if (relres) relres[i] = r.relres;
+    if (st) st[i] = (opm_status)r.status;
+    worst = worst_status(worst, (opm_status)r.status);
+  }
+  return worst;
 }
 
 }  // extern "C"

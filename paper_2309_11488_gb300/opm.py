@@ -38,7 +38,9 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicgstab_solve",
            "opm_spmv", "opm_ilu_apply", "opm_destroy", "opm_status_str", "opm_last_error_row",
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
-           "opm_reset_timing", "opm_bsr_residual_noalloc"]
+           "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
+           "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy"]
 
 
 class opm_options(ctypes.Structure):
@@ -109,6 +111,26 @@ def lib() -> ctypes.CDLL:
         L.opm_reset_timing.restype = i32
         L.opm_bsr_residual_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.opm_bsr_residual_noalloc.restype = i32
+        L.opm_solve_launch.argtypes = [vp, vp, vp, vp, f64, i32]
+        L.opm_solve_launch.restype = i32
+        L.opm_solve_ready.argtypes = [vp]
+        L.opm_solve_ready.restype = i32
+        L.opm_solve_wait.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+        L.opm_solve_wait.restype = i32
+        L.opm_batch_create.argtypes = [i32, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
+        L.opm_batch_create.restype = i32
+        L.opm_batch_factor.argtypes = [vp, vp, vp]
+        L.opm_batch_factor.restype = i32
+        L.opm_batch_solve.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+        L.opm_batch_solve.restype = i32
+        L.opm_batch_launch.argtypes = [vp, vp, vp, vp, vp, i32]
+        L.opm_batch_launch.restype = i32
+        L.opm_batch_ready.argtypes = [vp]
+        L.opm_batch_ready.restype = i32
+        L.opm_batch_wait.argtypes = [vp, vp, vp, vp]
+        L.opm_batch_wait.restype = i32
+        L.opm_batch_destroy.argtypes = [vp]
+        L.opm_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -254,6 +276,108 @@ def opm_bsr_residual_noalloc(nb, rowptr, colidx, vals, x, b, r, norms, stream=No
                                           _ptr(r, np.float64), _ptr(norms, np.float64), stream)
 
 
+def opm_solve_launch(h: Handle, vals, b, x, rtol=1e-2, maxit=200) -> int:
+    """Enqueue an optional refactorisation and a solve without waiting
+    (device arrays only; keep them alive until opm_solve_wait)."""
+    return lib().opm_solve_launch(h.ptr, _ptr(vals, np.float64), _ptr(b, np.float64), _ptr(x, np.float64),
+                                  float(rtol), int(maxit))
+
+
+def opm_solve_ready(h: Handle) -> bool:
+    return bool(lib().opm_solve_ready(h.ptr))
+
+
+def opm_solve_wait(h: Handle):
+    """Returns (status, iters, relres) of the pending launch."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().opm_solve_wait(h.ptr, ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def _ptr_array(arrays, dtype):
+    if arrays is None:
+        return None, None
+    addrs = (ctypes.c_void_p * len(arrays))(*[_ptr(a, dtype) for a in arrays])
+    return addrs, arrays
+
+
+class Batch:
+    """A set of handles factorised and solved together (see include/opm_bsr.h)."""
+
+    def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto"):
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.handles = list(handles)
+        hs = (ctypes.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
+        o = opm_options_default(stream=stream, chunk=chunk, sweep_launch=sweep_launch)
+        out = ctypes.c_void_p()
+        st = lib().opm_batch_create(len(self.handles), hs, ctypes.byref(o), ctypes.byref(out))
+        if st != OPM_OK:
+            raise OpmError(st, "opm_batch_create")
+        self.ptr = out.value
+        self._keep = None
+
+    def __len__(self):
+        return len(self.handles)
+
+    def factor(self, vals=None):
+        n = len(self)
+        va, keep = _ptr_array(vals, np.float64)
+        st = (ctypes.c_int32 * n)()
+        s = lib().opm_batch_factor(self.ptr, va, st)
+        return s, list(st)
+
+    def solve(self, bs, xs, rtol=1e-2, maxit=200):
+        n = len(self)
+        ba, kb = _ptr_array(bs, np.float64)
+        xa, kx = _ptr_array(xs, np.float64)
+        rt = (ctypes.c_double * n)(*([rtol] * n if np.isscalar(rtol) else list(rtol)))
+        it = (ctypes.c_int32 * n)()
+        rr = (ctypes.c_double * n)()
+        st = (ctypes.c_int32 * n)()
+        s = lib().opm_batch_solve(self.ptr, ba, xa, rt, int(maxit), it, rr, st)
+        return s, list(st), list(it), list(rr)
+
+    def launch(self, vals, bs, xs, rtol=1e-2, maxit=200):
+        n = len(self)
+        va, kv = _ptr_array(vals, np.float64)
+        ba, kb = _ptr_array(bs, np.float64)
+        xa, kx = _ptr_array(xs, np.float64)
+        rt = (ctypes.c_double * n)(*([rtol] * n if np.isscalar(rtol) else list(rtol)))
+        self._keep = (va, ba, xa, rt, kv, kb, kx)
+        return lib().opm_batch_launch(self.ptr, va, ba, xa, rt, int(maxit))
+
+    def ready(self) -> bool:
+        return bool(lib().opm_batch_ready(self.ptr))
+
+    def wait(self):
+        n = len(self)
+        it = (ctypes.c_int32 * n)()
+        rr = (ctypes.c_double * n)()
+        st = (ctypes.c_int32 * n)()
+        s = lib().opm_batch_wait(self.ptr, it, rr, st)
+        self._keep = None
+        return s, list(st), list(it), list(rr)
+
+    def close(self):
+        if self.ptr:
+            lib().opm_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """Convenience owner of one handle (context manager)."""
 
@@ -306,6 +430,17 @@ class Solver:
 
     def reset_timing(self):
         return opm_reset_timing(self.h)
+
+    def launch(self, vals, b, x, rtol=1e-2, maxit=200):
+        st = opm_solve_launch(self.h, vals, b, x, rtol, maxit)
+        if st != OPM_OK:
+            raise OpmError(st, "opm_solve_launch")
+
+    def ready(self) -> bool:
+        return opm_solve_ready(self.h)
+
+    def wait(self):
+        return opm_solve_wait(self.h)
 
     def close(self):
         opm_destroy(self.h)
