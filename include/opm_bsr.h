@@ -6,8 +6,9 @@
  * Comparison of GPU Hardware and Solver Libraries for Accelerating the OPM
  * Flow Reservoir Simulator"):
  *   - matrix format: block-CSR with 3x3 blocks stored contiguously and
- *     row-major inside each block (Section 4.1 and the figure "Memory layout
- *     of blocks in OPM", left panel; Section 4.3 on row-major Dune blocks);
+ *     row-major inside each block (Section 4.1; Section 4.7, figure "Memory
+ *     layout of blocks in OPM", left panel; Section 4.3 on row-major Dune
+ *     blocks);
  *   - preconditioner: ILU0 without fill (Section 2.2, Algorithms 1 and 2);
  *   - parallel schedule: level scheduling or graph colouring of the rows,
  *     with the matrix reordered once (Section 4.4);
@@ -15,7 +16,7 @@
  *     stopping at a relative residual reduction rtol or after maxit
  *     iterations, Dune's defaults being 1e-2 and 200 (Section 4.2);
  *   - a solver failure is reported rather than handled (the paper falls back
- *     to the CPU solver, Section 4.10; this library returns a status).
+ *     to the CPU solver, Section 4.11; this library returns a status).
  *
  * Conventions for every entry point:
  *   - nb = number of block rows (cells); vectors hold 3*nb doubles, the 3

@@ -9,8 +9,9 @@
  * each definition states.  Compiled with -O2 -ffp-contract=off so that no
  * multiply-add is fused.
  *
- * Storage convention (Section 4.1, "Figure: Memory layout of blocks in OPM",
- * left panel): block-CSR with nb block rows, rowptr[nb+1], colidx[nnzb]
+ * Storage convention (Section 4.1 on contiguous blocks; Section 4.7, figure
+ * "Memory layout of blocks in OPM (left) and amgcl (right)", left panel):
+ * block-CSR with nb block rows, rowptr[nb+1], colidx[nnzb]
  * sorted and unique inside every row, and each 3x3 block stored contiguously
  * and row-major: entry (r, c) of block m is vals[9*m + 3*r + c].  Vectors are
  * nb*3 doubles, the 3 unknowns of one cell contiguous (Section 4.1).

@@ -12,8 +12,8 @@ proprietary 1.09M-cell model) are not available, so only their sizes and
 densities are mimicked.  The matrices follow the structure the paper describes
 for OPM Flow (Section 2.1): one block row per active cell, 3 unknowns per cell
 (bs = 3), a two-point-flux (7-point) stencil on a corner grid, blocks stored
-contiguously and row-major inside each block (Section 4.1, Figure "Memory
-layout of blocks in OPM").
+contiguously and row-major inside each block (Section 4.1; Section 4.7,
+figure "Memory layout of blocks in OPM").
 
 Randomness comes from a counter-based generator (SplitMix64 of Steele, Lea and
 Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): value
