@@ -12,7 +12,7 @@
 //
 // Every kernel works on a batch of independent systems described in device
 // memory (a single solve is a batch of one).  Work is split per system into
-// fixed units -- 32-row slices for the sweeps, 1024-row tiles for the
+// fixed units -- 32-row slices for the sweeps, 256- or 1024-row tiles for the
 // row-parallel kernels -- so a system's arithmetic, including the order of
 // every reduction, is the same alone and inside any batch.
 //
@@ -38,6 +38,8 @@ enum SweepMode { kModePlain = 0, kModeP = 1, kModeS = 2 };
 // One system's device data.  The last group of fields is set per call.
 struct Sys {
   int32_t n, nslices, ntiles, nphases;
+  int32_t ntiles_s;  // 256-row tiles of the SpMV kernels
+  int32_t pad0;
   const int32_t *perm;
   const int32_t *a_rp, *a_col, *a_src;
   const int64_t *a_dst;
@@ -66,9 +68,10 @@ struct Batch {
   const int4 *ent;        // sweep work: (system, slice, first row, last row + 1 | last-phase bit 31)
   const int32_t *fwd_ptr; // [nphases + 1]: forward entries of phase c
   const int32_t *bwd_ptr; // [nphases + 1]: backward entries of phase c
-  const int2 *tiles;      // (system, tile) for the row-parallel kernels
+  const int2 *tiles;      // (system, 1024-row tile) for the streaming kernels
+  const int2 *tiles_s;    // (system, 256-row tile) for the SpMV kernels
   uint32_t *bar;          // grid barrier: arrivals at bar[0], generation at bar[32]
-  int32_t nsys, nphases, ntiles;
+  int32_t nsys, nphases, ntiles, ntiles_s;
   int32_t skip_cta;       // test hook: this CTA never arrives at grid barriers (-1: off)
   uint64_t spin_limit_ns;
 };
@@ -101,6 +104,15 @@ __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Programmatic dependent launch: wait until the preceding kernel of the
+// stream has completed and its writes are visible, then let the next kernel
+// begin launching (its CTAs in turn wait here).  Both are no-ops for a
+// kernel launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ bool running(const DevState *st) {
@@ -158,7 +170,8 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
 // Partial of this tile, then the system's last CTA sums all its partials in
 // tile order.  Returns true in that CTA; tot is then valid in thread 0.
 template <int NV>
-__device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, int tile, double (&tot)[NV]) {
+__device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, int tile, int ntiles,
+                                                double (&tot)[NV]) {
   __shared__ double sm[32 * NV];
   __shared__ int amlast;
   block_reduce<NV>(v, sm);
@@ -167,7 +180,7 @@ __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, i
     for (int q = 0; q < NV; ++q) S.partials[(size_t)tile * NV + q] = v[q];
     __threadfence();
     const unsigned t = atomicAdd(&S.st->red_count, 1u);
-    amlast = (t == (unsigned)S.ntiles - 1);
+    amlast = (t == (unsigned)ntiles - 1);
   }
   __syncthreads();
   if (!amlast) return false;
@@ -175,7 +188,7 @@ __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, i
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  for (int b = threadIdx.x; b < S.ntiles; b += blockDim.x) {
+  for (int b = threadIdx.x; b < ntiles; b += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] += __ldcg(S.partials + (size_t)b * NV + q);
   }
@@ -220,13 +233,19 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
 
 // ------------------------------------------------------------ tile kernels
 //
-// One CTA per (system, tile); a tile is kTileRows = 1024 rows of its system.
-// Streaming kernels use 256 threads in 4 passes (thread t: rows t, t + 256,
-// t + 512, t + 768 of the tile); SpMV kernels use 1024 threads, one row each.
+// One CTA per (system, tile).  Streaming kernels use tiles of kTileRows =
+// 1024 rows and 256 threads in 4 passes (thread t: rows t, t + 256, t + 512,
+// t + 768 of the tile); SpMV kernels use tiles of kSpmvRows = 256 rows, one
+// row per thread, so that their last partial wave stays short.
 
 #define OPM_TILE(B, S, lt)                  \
   const int2 tile_ = (B).tiles[blockIdx.x]; \
   const Sys &S = (B).sys[tile_.x];          \
+  const int lt = tile_.y
+
+#define OPM_TILE_S(B, S, lt)                  \
+  const int2 tile_ = (B).tiles_s[blockIdx.x]; \
+  const Sys &S = (B).sys[tile_.x];            \
   const int lt = tile_.y
 
 #define OPM_TILE_ROWS(i, lt) \
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, S.ntiles, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     const double n0 = sqrt(tot[0]);
     st->n0 = n0;
@@ -280,11 +299,12 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
 }
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).
-__global__ void __launch_bounds__(1024, 2) k_spmv_v(Batch B) {
-  OPM_TILE(B, S, lt);
+__global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
+  pdl_enter();
+  OPM_TILE_S(B, S, lt);
   if (!running(S.st)) return;
   double acc[1] = {0.0};
-  const int i = lt * kTileRows + threadIdx.x;
+  const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     row_spmv(S.a_rp, S.a_col, S.a_val, S.ph, i, S.n, y0, y1, y2);
@@ -296,7 +316,7 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_v(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, S.ntiles_s, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     st->rhv = tot[0];
     if (tot[0] == 0.0) {
@@ -309,11 +329,12 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_v(Batch B) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(1024, 2) k_spmv_t(Batch B) {
-  OPM_TILE(B, S, lt);
+__global__ void __launch_bounds__(256, 6) k_spmv_t(Batch B) {
+  pdl_enter();
+  OPM_TILE_S(B, S, lt);
   if (!running(S.st)) return;
   double acc[3] = {0.0, 0.0, 0.0};
-  const int i = lt * kTileRows + threadIdx.x;
+  const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     row_spmv(S.a_rp, S.a_col, S.a_val, S.sh, i, S.n, y0, y1, y2);
@@ -328,7 +349,7 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_t(Batch B) {
     }
   }
   double tot[3];
-  if (last_cta_reduce<3>(acc, S, lt, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<3>(acc, S, lt, S.ntiles_s, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     st->ts = tot[0];
     st->tt = tot[1];
@@ -352,6 +373,7 @@ __global__ void __launch_bounds__(1024, 2) k_spmv_t(Batch B) {
 // x += alpha p^ + omega s^, r = s - omega t, ||r||^2, (r^, r); stopping rule,
 // then beta for the next iteration.
 __global__ void __launch_bounds__(256, 6) k_update(Batch B) {
+  pdl_enter();
   OPM_TILE(B, S, lt);
   if (!running(S.st)) return;
   const DevState *cst = S.st;
@@ -376,7 +398,7 @@ __global__ void __launch_bounds__(256, 6) k_update(Batch B) {
     }
   }
   double tot[2];
-  if (last_cta_reduce<2>(acc, S, lt, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<2>(acc, S, lt, S.ntiles, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     const int k = st->k;
     if (half) {
@@ -407,12 +429,12 @@ __global__ void __launch_bounds__(256, 6) k_update(Batch B) {
 
 // Final true residual ||b - A x|| / ||b|| in FP64 and x back to the caller's
 // order (zeros on a failed solve).
-__global__ void __launch_bounds__(1024, 2) k_finish(Batch B) {
-  OPM_TILE(B, S, lt);
+__global__ void __launch_bounds__(256, 8) k_finish(Batch B) {
+  OPM_TILE_S(B, S, lt);
   const int status = S.st->status;
   const bool ok = (status == OPM_OK || status == OPM_NOT_CONVERGED) && S.st->error == 0;
   double acc[1] = {0.0};
-  const int i = lt * kTileRows + threadIdx.x;
+  const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     if (ok) row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
@@ -427,16 +449,16 @@ __global__ void __launch_bounds__(1024, 2) k_finish(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, tot) && threadIdx.x == 0) {
+  if (last_cta_reduce<1>(acc, S, lt, S.ntiles_s, tot) && threadIdx.x == 0) {
     DevState *st = S.st;
     st->relres = !ok ? nan("") : (st->n0 > 0.0 ? sqrt(tot[0]) / st->n0 : 0.0);
   }
 }
 
 // y = A x in the caller's order (x already permuted into w).
-__global__ void __launch_bounds__(1024, 2) k_spmv_plain(Batch B) {
-  OPM_TILE(B, S, lt);
-  const int i = lt * kTileRows + threadIdx.x;
+__global__ void __launch_bounds__(256, 8) k_spmv_plain(Batch B) {
+  OPM_TILE_S(B, S, lt);
+  const int i = lt * kSpmvRows + threadIdx.x;
   double y0 = 0.0, y1 = 0.0, y2 = 0.0;
   row_spmv(S.a_rp, S.a_col, S.a_val, S.w, i, S.n, y0, y1, y2);
   if (i < S.n) {
@@ -512,6 +534,7 @@ __global__ void k_results(Batch B, Result *out) {
 
 // While-loop condition of the solve graph: continue while a system runs.
 __global__ void k_loop_cond(Batch B, cudaGraphConditionalHandle h) {
+  pdl_enter();
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -698,6 +721,7 @@ __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
 // One launch per phase: one sweep entry (a 32-row slice) per warp.
 template <typename TF, int MODE>
 __global__ void __launch_bounds__(256) k_fwd_phase(Batch B, int c) {
+  pdl_enter();
   const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= __ldg(B.fwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
@@ -708,6 +732,7 @@ __global__ void __launch_bounds__(256) k_fwd_phase(Batch B, int c) {
 
 template <typename TF, int MODE>
 __global__ void __launch_bounds__(256) k_bwd_phase(Batch B, int c) {
+  pdl_enter();
   const int e = __ldg(B.bwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= __ldg(B.bwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
@@ -857,6 +882,7 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
 
 template <typename TF>
 __global__ void __launch_bounds__(256) k_factor_phase(Batch B, int c) {
+  pdl_enter();
   const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= __ldg(B.fwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];

@@ -30,7 +30,8 @@
 namespace opm {
 
 constexpr int kWarp = 32;
-constexpr int kTileRows = 1024;    // rows per CTA of the static-tiled kernels (256 threads x 4)
+constexpr int kTileRows = 1024;    // rows per tile of the streaming kernels (256 threads x 4)
+constexpr int kSpmvRows = 256;     // rows per tile of the SpMV kernels (256 threads x 1)
 constexpr int kSweepThreads = 1024;  // threads per CTA of the cooperative sweep kernels
 constexpr int kSliceVals = 288;  // 32 rows x 9 entries per Dinv slice
 constexpr int32_t kRunning = 0x7fffffff;

@@ -62,7 +62,7 @@ struct Runner {
   cudaStream_t stream = nullptr;
   int device = 0;
   bool fp32 = false, cooperative = false, profile = false;
-  int chunk = 2, nsys = 0, nphases = 0, ntiles = 0;
+  int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
   std::vector<int32_t> fwd_ptr, bwd_ptr;
   Batch B{};
   Sys *h_sys = nullptr;      // pinned staging of the descriptors
@@ -155,6 +155,24 @@ cudaError_t launch_coop(void (*kern)(P...), int grid, cudaStream_t st, A... args
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Kernels inside the iteration graph are launched with programmatic stream
+// serialization: the next kernel's CTAs may be scheduled while the previous
+// kernel drains, and wait in griddepcontrol.wait for its completion.
+template <typename... P, typename... A>
+void launch_pdl(void (*kern)(P...), int grid, int block, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Schedules with at most this many phases run one launch per phase; more
 // phases run as one cooperative launch with grid barriers.
 constexpr int kMaxPhaseLaunches = 1024;
@@ -168,7 +186,7 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
     return 1;
   }
   for (int c = 0; c < R.nphases; ++c)
-    k_factor_phase<TF><<<blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, 0, st>>>(R.B, c);
+    launch_pdl(k_factor_phase<TF>, blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, st, R.B, c);
   return R.nphases;
 }
 
@@ -179,12 +197,12 @@ int launch_apply_t(Runner &R, cudaStream_t st) {
     return 1;
   }
   for (int c = 0; c < R.nphases; ++c)
-    k_fwd_phase<TF, MODE><<<blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, 0, st>>>(R.B, c);
+    launch_pdl(k_fwd_phase<TF, MODE>, blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, st, R.B, c);
   int n = R.nphases;
   for (int c = R.nphases - 2; c >= 0; --c) {
     const int cnt = R.bwd_ptr[c + 1] - R.bwd_ptr[c];
     if (cnt == 0) continue;
-    k_bwd_phase<TF, MODE><<<blocks8(cnt), 256, 0, st>>>(R.B, c);
+    launch_pdl(k_bwd_phase<TF, MODE>, blocks8(cnt), 256, st, R.B, c);
     ++n;
   }
   return n;
@@ -214,13 +232,13 @@ int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
   mark(0);
   n += launch_apply<kModeP>(R, st);
   mark(1);
-  k_spmv_v<<<R.ntiles, 1024, 0, st>>>(R.B);
+  launch_pdl(k_spmv_v, R.ntiles_s, 256, st, R.B);
   mark(2);
   n += launch_apply<kModeS>(R, st);
   mark(3);
-  k_spmv_t<<<R.ntiles, 1024, 0, st>>>(R.B);
+  launch_pdl(k_spmv_t, R.ntiles_s, 256, st, R.B);
   mark(4);
-  k_update<<<R.ntiles, 256, 0, st>>>(R.B);
+  launch_pdl(k_update, R.ntiles, 256, st, R.B);
   mark(5);
   return n;
 }
@@ -325,7 +343,7 @@ opm_status build_graphs(Runner &R) {
         s = OPM_ERR_CUDA;
         break;
       }
-      if ((s = add_kernel_node(g, &n_finish, &n_while, 1, (void *)k_finish, R.ntiles, 1024, argsB)) != OPM_OK)
+      if ((s = add_kernel_node(g, &n_finish, &n_while, 1, (void *)k_finish, R.ntiles_s, 256, argsB)) != OPM_OK)
         break;
       void *argsR[] = {&R.B, &R.d_res};
       if ((s = add_kernel_node(g, &n_res, &n_finish, 1, (void *)k_results, results_blocks(R), 128, argsR)) !=
@@ -420,23 +438,27 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     }
     R->bwd_ptr.push_back((int)ent.size());
   }
-  std::vector<int2> tiles;
-  for (int s = 0; s < R->nsys; ++s)
-    for (int t = 0; t < mem[s]->ntiles; ++t) tiles.push_back(make_int2(s, t));
+  std::vector<int2> tiles, tiles_s;
+  for (int s = 0; s < R->nsys; ++s) {
+    for (int t = 0; t < mem[s]->sys.ntiles; ++t) tiles.push_back(make_int2(s, t));
+    for (int t = 0; t < mem[s]->sys.ntiles_s; ++t) tiles_s.push_back(make_int2(s, t));
+  }
   R->ntiles = (int)tiles.size();
+  R->ntiles_s = (int)tiles_s.size();
   R->cooperative =
       sweep_launch == OPM_SWEEP_COOPERATIVE || (sweep_launch == OPM_SWEEP_AUTO && maxp > kMaxPhaseLaunches);
   // ---- device copies
   opm_status s;
   int4 *d_ent;
   int32_t *d_fwd, *d_bwd;
-  int2 *d_tiles;
+  int2 *d_tiles, *d_tiles_s;
   uint32_t *d_bar;
   Sys *d_sys;
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_ent, ent)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_fwd, R->fwd_ptr)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_bwd, R->bwd_ptr)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles, tiles)) != OPM_OK) return fail(s);
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles_s, tiles_s)) != OPM_OK) return fail(s);
   if ((s = dalloc(R->allocs, R->dev_bytes, &d_bar, 64)) != OPM_OK) return fail(s);
   if ((s = dalloc(R->allocs, R->dev_bytes, &d_sys, (size_t)R->nsys)) != OPM_OK) return fail(s);
   if ((s = dalloc(R->allocs, R->dev_bytes, &R->d_res, (size_t)R->nsys)) != OPM_OK) return fail(s);
@@ -452,6 +474,8 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
   R->B.fwd_ptr = d_fwd;
   R->B.bwd_ptr = d_bwd;
   R->B.tiles = d_tiles;
+  R->B.tiles_s = d_tiles_s;
+  R->B.ntiles_s = R->ntiles_s;
   R->B.bar = d_bar;
   R->B.nsys = R->nsys;
   R->B.nphases = maxp;
@@ -547,7 +571,7 @@ opm_status runner_solve_profiled(Runner &R, opm_timing &t) {
     if (!any) break;
   }
   CK(cudaEventRecord(e0, R.stream));
-  k_finish<<<R.ntiles, 1024, 0, R.stream>>>(R.B);
+  k_finish<<<R.ntiles_s, 256, 0, R.stream>>>(R.B);
   CK(cudaEventRecord(e1, R.stream));
   k_results<<<results_blocks(R), 128, 0, R.stream>>>(R.B, R.d_res);
   t.launches += 2;
@@ -628,6 +652,7 @@ opm_status alloc_system(opm_solver *h) {
   S.n = nb;
   S.nslices = h->nslices;
   S.ntiles = h->ntiles;
+  S.ntiles_s = std::max(1, (nb + kSpmvRows - 1) / kSpmvRows);
   S.nphases = (int32_t)an.phase_ptr.size() - 1;
   S.u_off = 9 * an.nnz_l;
   S.d_off = an.d_off;
@@ -678,7 +703,7 @@ opm_status alloc_system(opm_solver *h) {
   double **vecs[] = {&S.x, &S.r, &S.rh, &S.p, &S.v, &S.ph, &S.s, &S.sh, &S.t, &S.w, &h->vec_in, &h->vec_out};
   for (double **pv : vecs)
     if ((s = dalloc(A, bytes, pv, 3 * (size_t)nb)) != OPM_OK) return s;
-  if ((s = dalloc(A, bytes, &S.partials, 4 * (size_t)h->ntiles)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, &S.partials, 4 * (size_t)S.ntiles_s)) != OPM_OK) return s;
   if ((s = dalloc(A, bytes, &S.st, 1)) != OPM_OK) return s;
   DevState init{};
   init.status = OPM_OK;
@@ -936,7 +961,7 @@ opm_status opm_spmv(opm_handle h, const double *x, double *y) {
   Runner &R = *h->run;
   if ((s = runner_push(R)) != OPM_OK) return s;
   k_gather<<<R.ntiles, 256, 0, h->stream>>>(R.B);
-  k_spmv_plain<<<R.ntiles, 1024, 0, h->stream>>>(R.B);
+  k_spmv_plain<<<R.ntiles_s, 256, 0, h->stream>>>(R.B);
   CK(cudaGetLastError());
   h->timing.launches += 2;
   if (!y_dev)
