@@ -73,6 +73,8 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_closed_first_key.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
+        L.orc_closed_first_key.restype = None
         L.orc_permute.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
         L.orc_permute.restype = None
         _lib = L
@@ -198,8 +200,9 @@ def order_by_key(key, nkeys):
 
 
 def schedule_perm(nb, rowptr, colidx, schedule):
-    """perm[new] = old for 'natural', 'level' or 'colour' (Section 4.4);
-    returns (perm, number of sets)."""
+    """perm[new] = old for 'natural', 'level' or 'colour' (Section 4.4):
+    set-major; inside a set the closed rows (no neighbour in a later set)
+    first, natural order inside each group.  Returns (perm, number of sets)."""
     if schedule == "natural":
         return np.arange(nb, dtype=np.int32), 1
     if schedule == "level":
@@ -208,7 +211,11 @@ def schedule_perm(nb, rowptr, colidx, schedule):
         key, n = colours(nb, rowptr, colidx)
     else:
         raise ValueError(schedule)
-    return order_by_key(key, n), n
+    # inside each set: rows without a neighbour in a later set first
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    key2 = np.empty(nb, dtype=np.int32)
+    lib().orc_closed_first_key(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(_i32(key), _i32p), _p(key2, _i32p))
+    return order_by_key(key2, 2 * n), n
 
 
 def permute(nb, rowptr, colidx, vals, perm):

@@ -528,12 +528,32 @@ int32_t orc_colours(int32_t nb, const int32_t *rowptr, const int32_t *colidx, in
   return ncol;
 }
 
-/* perm[new] = old: rows ordered by key, natural order inside each key */
+/*
+ * Sub-key that orders the rows of each set (level or colour, Section 4.4):
+ * out[i] = 2 key[i] + open[i], where row i is open when some neighbour in
+ * the symmetrised pattern lies in a later set.  Rows of one set share no
+ * edge, so any order inside a set gives the same factors up to the order of
+ * each row's sums; closed rows (no later neighbour, hence no U block) first.
+ */
+void orc_closed_first_key(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *key,
+                          int32_t *out) {
+  for (int32_t i = 0; i < nb; ++i) out[i] = 2 * key[i];
+  for (int32_t i = 0; i < nb; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      int32_t j = colidx[m];
+      if (key[j] > key[i]) out[i] = 2 * key[i] + 1;
+      if (key[i] > key[j]) out[j] = 2 * key[j] + 1;
+    }
+}
+
+/* perm[new] = old: rows ordered by key, natural order inside each key
+   (a stable counting sort) */
 void orc_order_by_key(int32_t nb, const int32_t *key, int32_t nkeys, int32_t *perm) {
-  int32_t pos = 0;
-  for (int32_t k = 0; k < nkeys; ++k)
-    for (int32_t i = 0; i < nb; ++i)
-      if (key[i] == k) perm[pos++] = i;
+  int64_t *start = calloc((size_t)nkeys + 1, sizeof(int64_t));
+  for (int32_t i = 0; i < nb; ++i) start[key[i] + 1]++;
+  for (int32_t k = 0; k < nkeys; ++k) start[k + 1] += start[k];
+  for (int32_t i = 0; i < nb; ++i) perm[start[key[i]]++] = i;
+  free(start);
 }
 
 /*

@@ -47,6 +47,7 @@ struct Sys {
   const int32_t *l_rp, *l_col, *u_rp, *u_col;
   const int32_t *upd_ptr;
   const int64_t *upd_dst, *upd_src;
+  const uint2 *sl_mask;  // per slice: (rows without U blocks, rows whose y is read later)
   void *lu;  // factor values (double or float): [L | U | Dinv slices]
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
@@ -65,7 +66,7 @@ struct Sys {
 // A launchable set of systems (kernel parameter).
 struct Batch {
   const Sys *sys;         // [nsys]
-  const int4 *ent;        // sweep work: (system, slice, first row, last row + 1 | last-phase bit 31)
+  const int4 *ent;        // sweep work: (system, slice, first row, last row + 1)
   const int32_t *fwd_ptr; // [nphases + 1]: forward entries of phase c
   const int32_t *bwd_ptr; // [nphases + 1]: backward entries of phase c
   const int2 *tiles;      // (system, 1024-row tile) for the streaming kernels
@@ -106,13 +107,18 @@ __device__ __forceinline__ uint64_t gtimer() {
   return t;
 }
 
-// Programmatic dependent launch: wait until the preceding kernel of the
-// stream has completed and its writes are visible, then let the next kernel
-// begin launching (its CTAs in turn wait here).  Both are no-ops for a
-// kernel launched without the programmatic-serialization attribute.
+// Programmatic dependent launch.  pdl_trigger lets the next kernel of the
+// stream begin launching at once, so its CTAs become resident while this
+// one runs; pdl_wait blocks until the preceding kernel has completed and its
+// writes are visible.  A kernel reads nothing written by earlier kernels of
+// the solve before its pdl_wait (only data that is constant for the whole
+// solve: factors, index arrays, descriptors).  Both are no-ops for a kernel
+// launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_trigger();
+  pdl_wait();
 }
 
 __device__ __forceinline__ bool running(const DevState *st) {
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(256, 6) k_spmv_t(Batch B) {
+__global__ void __launch_bounds__(256, 7) k_spmv_t(Batch B) {
   pdl_enter();
   OPM_TILE_S(B, S, lt);
   if (!running(S.st)) return;
@@ -594,26 +600,36 @@ __device__ __forceinline__ Vec3<TF> load3cg(const TF *p) {
   return {__ldcg(p), __ldcg(p + 1), __ldcg(p + 2)};
 }
 
-// a -= B v for one 3x3 block (entry-planar with stride c) in FMA form.
+// a -= B v for one 3x3 block held in registers, in FMA form.  Every sweep
+// path goes through this one expression, so all of them round alike.
+template <typename TF>
+__device__ __forceinline__ void blk_sub_r(const TF (&b)[9], TF v0, TF v1, TF v2, TF &a0, TF &a1, TF &a2) {
+  a0 = fma(-b[0], v0, fma(-b[1], v1, fma(-b[2], v2, a0)));
+  a1 = fma(-b[3], v0, fma(-b[4], v1, fma(-b[5], v2, a1)));
+  a2 = fma(-b[6], v0, fma(-b[7], v1, fma(-b[8], v2, a2)));
+}
+
+// The same for a block in memory, entry-planar with stride c.
 template <typename TF>
 __device__ __forceinline__ void blk_sub(const TF *__restrict__ Bv, int c, TF v0, TF v1, TF v2, TF &a0, TF &a1,
                                         TF &a2) {
-  a0 = fma(-__ldg(Bv), v0, fma(-__ldg(Bv + c), v1, fma(-__ldg(Bv + 2 * c), v2, a0)));
-  a1 = fma(-__ldg(Bv + 3 * c), v0, fma(-__ldg(Bv + 4 * c), v1, fma(-__ldg(Bv + 5 * c), v2, a1)));
-  a2 = fma(-__ldg(Bv + 6 * c), v0, fma(-__ldg(Bv + 7 * c), v1, fma(-__ldg(Bv + 8 * c), v2, a2)));
+  TF b[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) b[e] = __ldg(Bv + e * c);
+  blk_sub_r<TF>(b, v0, v1, v2, a0, a1, a2);
 }
 
-// a -= sum over the lane's row of a sliced part of B_ij v_j, v read through
-// L2; two slabs per step for memory-level parallelism.  All lanes call with
-// len = their row's block count (0 past n), which defines the slab layout of
-// the slice; lanes with !act issue no loads.
+// a -= sum over the lane's row of a sliced part of B_ij v_j for the slabs
+// k0, k0+1, ... (base = first block of slab k0), v read through L2; two
+// slabs per step for memory-level parallelism.  All lanes call with len =
+// their row's block count (0 past n), which defines the slab layout of the
+// slice; lanes with !act issue no loads.
 template <typename TF, typename TV>
 __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const TF *__restrict__ vals,
-                                        const TV *vec, int len, int base0, int maxlen, bool act, TF &a0,
+                                        const TV *vec, int len, int base, int k0, int maxlen, bool act, TF &a0,
                                         TF &a1, TF &a2) {
   const unsigned lt = lanemask_lt();
-  int base = base0;
-  for (int k = 0; k < maxlen; k += 2) {
+  for (int k = k0; k < maxlen; k += 2) {
     const unsigned m0 = __ballot_sync(0xffffffffu, len > k);
     const unsigned m1 = __ballot_sync(0xffffffffu, len > k + 1);
     const int b0 = base, b1 = base + __popc(m0);
@@ -634,6 +650,58 @@ __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const T
   }
 }
 
+// The first PRE slabs of the lane's row, loaded ahead: column, block values.
+// Returns the first block of slab PRE.
+template <typename TF, int PRE>
+__device__ __forceinline__ int preload_slabs(const int32_t *__restrict__ col, const TF *__restrict__ vals, int len,
+                                             int base, bool act, int (&jp)[PRE], TF (&bp)[PRE][9]) {
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int k = 0; k < PRE; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, len > k);
+    if (act && len > k) {
+      const int q = __popc(m & lt), cnt = __popc(m);
+      jp[k] = __ldg(col + base + q);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) bp[k][e] = __ldg(vals + 9ll * base + q + e * cnt);
+    }
+    base += __popc(m);
+  }
+  return base;
+}
+
+// Gathers of the preloaded slabs' vector blocks (issued together).
+template <typename TV, int PRE>
+__device__ __forceinline__ void gather_preloaded(const TV *vec, int len, bool act, const int (&jp)[PRE],
+                                                 Vec3<TV> (&vv)[PRE]) {
+#pragma unroll
+  for (int k = 0; k < PRE; ++k)
+    if (act && len > k) vv[k] = load3cg(vec + 3ll * jp[k]);
+}
+
+// a -= B_k v_k over the preloaded slabs, in slab order.
+template <typename TF, typename TV, int PRE>
+__device__ __forceinline__ void preloaded_sub(int len, bool act, const TF (&bp)[PRE][9], const Vec3<TV> (&vv)[PRE],
+                                              TF &a0, TF &a1, TF &a2) {
+#pragma unroll
+  for (int k = 0; k < PRE; ++k)
+    if (act && len > k) blk_sub_r<TF>(bp[k], (TF)vv[k].c0, (TF)vv[k].c1, (TF)vv[k].c2, a0, a1, a2);
+}
+
+// z_i = inv(U_ii) a with the inverse diagonal block (entry-planar, stride 32).
+template <typename TF>
+__device__ __forceinline__ void load_dinv(const TF *D, TF (&d)[9]) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) d[e] = __ldg(D + 32 * e);
+}
+
+template <typename TF>
+__device__ __forceinline__ void store_dinv_product(double *zi, const TF (&d)[9], TF a0, TF a1, TF a2) {
+  zi[0] = (double)fma(d[0], a0, fma(d[1], a1, d[2] * a2));
+  zi[1] = (double)fma(d[3], a0, fma(d[4], a1, d[5] * a2));
+  zi[2] = (double)fma(d[6], a0, fma(d[7], a1, d[8] * a2));
+}
+
 template <int MODE>
 __device__ __forceinline__ double *sweep_out(const Sys &S) {
   return (MODE == kModeP) ? S.ph : (MODE == kModeS) ? S.sh : S.t;
@@ -641,104 +709,150 @@ __device__ __forceinline__ double *sweep_out(const Sys &S) {
 
 // Forward substitution for the rows of slice sl inside [r0, r1):
 // y_i = rhs_i - sum_{j<i} L_ij y_j (Algorithm 1, equation 3), the right-hand
-// side formed on the fly.  In the system's last phase (no U columns past
-// the phase) the backward step z_i = inv(U_ii) y_i follows at once.
-template <typename TF, int MODE>
-__device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1, bool also_back) {
+// side formed on the fly.  A row without U blocks takes its backward step
+// z_i = inv(U_ii) y_i (equation 4) at once; y_i is stored only when a later
+// step reads it.
+//
+// PRE > 0 is the latency-oriented form for small phases: the row's constant
+// data (lengths, first PRE slabs, inverse diagonal) is loaded before the
+// wait for the preceding kernel (programmatic dependent launch), so only the
+// gathers of earlier phases' results remain after it.  PRE == 0 expects the
+// caller to have waited.  Both forms do the same arithmetic in the same order.
+template <typename TF, int MODE, int PRE>
+__device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1) {
+  constexpr int NP = PRE > 0 ? PRE : 1;
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
   const bool act = i >= r0 && i < r1;
+  // constant for the whole solve: safe to read before the wait
   TF *y = static_cast<TF *>(S.y);
   const TF *lu = static_cast<const TF *>(S.lu);
-  double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+  const DevState *st = S.st;
+  const double *rin = (MODE == kModePlain) ? S.w : S.r;
+  const double *vin = S.v;
+  double *hout = (MODE == kModeP) ? S.p : S.s;
+  double *zout = sweep_out<MODE>(S);
+  const uint2 M = __ldg(S.sl_mask + sl);
+  const bool eager = (M.x >> lane) & 1u, ystore = (M.y >> lane) & 1u;
   const int len = (i < S.n) ? __ldg(S.l_rp + i + 1) - __ldg(S.l_rp + i) : 0;
+  int base = (s0 < S.n) ? __ldg(S.l_rp + s0) : 0;
+  const int maxlen = __reduce_max_sync(0xffffffffu, len);
+  const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
+  int jp[NP];
+  TF bp[NP][9], d[9];
+  Vec3<TF> vv[NP];
+  if (PRE > 0) {
+    base = preload_slabs<TF, NP>(S.l_col, lu, len, base, act, jp, bp);
+    if (act && eager) load_dinv<TF>(D, d);
+    pdl_wait();
+  }
+  // after the wait: the solver state, the right-hand side and the results
+  // of earlier phases, all issued before the first use
+  const int status = st->status, err = st->error;
+  const double c1 = (MODE == kModeP) ? st->beta : (MODE == kModeS) ? st->alpha : 0.0;
+  const double c2 = (MODE == kModeP) ? st->omega : 0.0;
+  Vec3<double> rr{0.0, 0.0, 0.0}, vo{0.0, 0.0, 0.0}, po{0.0, 0.0, 0.0};
   if (act) {
-    const size_t e = 3ll * i;
+    rr = load3cg(rin + 3ll * i);
+    if (MODE != kModePlain) vo = load3cg(vin + 3ll * i);
+    if (MODE == kModeP) po = load3cg(hout + 3ll * i);
+  }
+  if (PRE > 0) gather_preloaded<TF, NP>(y, len, act, jp, vv);
+  if (MODE != kModePlain && !(status == kRunning && err == 0)) return;
+  double h0 = rr.c0, h1 = rr.c1, h2 = rr.c2;
+  if (act) {
     if (MODE == kModeP) {
-      const double beta = S.st->beta, omega = S.st->omega;
-      h0 = fma(beta, fma(-omega, S.v[e], S.p[e]), S.r[e]);
-      h1 = fma(beta, fma(-omega, S.v[e + 1], S.p[e + 1]), S.r[e + 1]);
-      h2 = fma(beta, fma(-omega, S.v[e + 2], S.p[e + 2]), S.r[e + 2]);
-      S.p[e] = h0; S.p[e + 1] = h1; S.p[e + 2] = h2;
+      h0 = fma(c1, fma(-c2, vo.c0, po.c0), rr.c0);
+      h1 = fma(c1, fma(-c2, vo.c1, po.c1), rr.c1);
+      h2 = fma(c1, fma(-c2, vo.c2, po.c2), rr.c2);
     } else if (MODE == kModeS) {
-      const double alpha = S.st->alpha;
-      h0 = fma(-alpha, S.v[e], S.r[e]);
-      h1 = fma(-alpha, S.v[e + 1], S.r[e + 1]);
-      h2 = fma(-alpha, S.v[e + 2], S.r[e + 2]);
-      S.s[e] = h0; S.s[e + 1] = h1; S.s[e + 2] = h2;
-    } else {
-      h0 = S.w[e]; h1 = S.w[e + 1]; h2 = S.w[e + 2];
+      h0 = fma(-c1, vo.c0, rr.c0);
+      h1 = fma(-c1, vo.c1, rr.c1);
+      h2 = fma(-c1, vo.c2, rr.c2);
+    }
+    if (MODE != kModePlain) {
+      double *ho = hout + 3ll * i;
+      ho[0] = h0; ho[1] = h1; ho[2] = h2;
     }
   }
-  const int base0 = (s0 < S.n) ? __ldg(S.l_rp + s0) : 0;
-  const int maxlen = __reduce_max_sync(0xffffffffu, len);
   TF a0 = (TF)h0, a1 = (TF)h1, a2 = (TF)h2;
-  row_sub<TF, TF>(S.l_col, lu, y, len, base0, maxlen, act, a0, a1, a2);
+  if (PRE > 0) preloaded_sub<TF, TF, NP>(len, act, bp, vv, a0, a1, a2);
+  row_sub<TF, TF>(S.l_col, lu, y, len, base, PRE, maxlen, act, a0, a1, a2);
   if (act) {
-    if (also_back) {
-      const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
-      double *zi = sweep_out<MODE>(S) + 3ll * i;
-      zi[0] = (double)fma(__ldg(D), a0, fma(__ldg(D + 32), a1, __ldg(D + 64) * a2));
-      zi[1] = (double)fma(__ldg(D + 96), a0, fma(__ldg(D + 128), a1, __ldg(D + 160) * a2));
-      zi[2] = (double)fma(__ldg(D + 192), a0, fma(__ldg(D + 224), a1, __ldg(D + 256) * a2));
-    } else {
+    if (eager) {
+      if (PRE == 0) load_dinv<TF>(D, d);
+      store_dinv_product<TF>(zout + 3ll * i, d, a0, a1, a2);
+    }
+    if (ystore) {
       TF *yi = y + 3ll * i;
       yi[0] = a0; yi[1] = a1; yi[2] = a2;
     }
   }
 }
 
-// Backward substitution for the rows of slice sl inside [r0, r1):
-// z_i = inv(U_ii)(y_i - sum_{j>i} U_ij z_j) (Algorithm 1, equation 4).
-template <typename TF, int MODE>
+// Backward substitution for the rows of slice sl inside [r0, r1) that have
+// U blocks: z_i = inv(U_ii)(y_i - sum_{j>i} U_ij z_j) (Algorithm 1,
+// equation 4).  PRE as for fwd_rows.
+template <typename TF, int MODE, int PRE>
 __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
+  constexpr int NP = PRE > 0 ? PRE : 1;
   const int lane = threadIdx.x & 31;
   const int s0 = sl * 32;
   const int i = s0 + lane;
-  const bool act = i >= r0 && i < r1;
+  const uint2 M = __ldg(S.sl_mask + sl);
+  const bool act = i >= r0 && i < r1 && !((M.x >> lane) & 1u);
   const TF *y = static_cast<const TF *>(S.y);
   const TF *lu = static_cast<const TF *>(S.lu);
+  const DevState *st = S.st;
   double *z = sweep_out<MODE>(S);
   const int len = (i < S.n) ? __ldg(S.u_rp + i + 1) - __ldg(S.u_rp + i) : 0;
-  TF a0 = TF(0), a1 = TF(0), a2 = TF(0);
-  if (act) {
-    const Vec3<TF> yi = load3cg(y + 3ll * i);
-    a0 = yi.c0; a1 = yi.c1; a2 = yi.c2;
-  }
-  const int base0 = (s0 < S.n) ? __ldg(S.u_rp + s0) : 0;
+  int base = (s0 < S.n) ? __ldg(S.u_rp + s0) : 0;
   const int maxlen = __reduce_max_sync(0xffffffffu, len);
-  row_sub<TF, double>(S.u_col, lu + S.u_off, z, len, base0, maxlen, act, a0, a1, a2);
+  const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
+  int jp[NP];
+  TF bp[NP][9], d[9];
+  Vec3<double> vv[NP];
+  if (PRE > 0) {
+    base = preload_slabs<TF, NP>(S.u_col, lu + S.u_off, len, base, act, jp, bp);
+    if (act) load_dinv<TF>(D, d);
+    pdl_wait();
+  }
+  const int status = st->status, err = st->error;
+  Vec3<TF> yi{TF(0), TF(0), TF(0)};
+  if (act) yi = load3cg(y + 3ll * i);
+  if (PRE > 0) gather_preloaded<double, NP>(z, len, act, jp, vv);
+  if (MODE != kModePlain && !(status == kRunning && err == 0)) return;
+  TF a0 = yi.c0, a1 = yi.c1, a2 = yi.c2;
+  if (PRE > 0) preloaded_sub<TF, double, NP>(len, act, bp, vv, a0, a1, a2);
+  row_sub<TF, double>(S.u_col, lu + S.u_off, z, len, base, PRE, maxlen, act, a0, a1, a2);
   if (act) {
-    const TF *D = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
-    double *zi = z + 3ll * i;
-    zi[0] = (double)fma(__ldg(D), a0, fma(__ldg(D + 32), a1, __ldg(D + 64) * a2));
-    zi[1] = (double)fma(__ldg(D + 96), a0, fma(__ldg(D + 128), a1, __ldg(D + 160) * a2));
-    zi[2] = (double)fma(__ldg(D + 192), a0, fma(__ldg(D + 224), a1, __ldg(D + 256) * a2));
+    if (PRE == 0) load_dinv<TF>(D, d);
+    store_dinv_product<TF>(z + 3ll * i, d, a0, a1, a2);
   }
 }
 
-// One launch per phase: one sweep entry (a 32-row slice) per warp.
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_fwd_phase(Batch B, int c) {
-  pdl_enter();
-  const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
+// One launch per phase, one sweep entry (a 32-row slice) per warp.  PRE = 0:
+// throughput form for large phases (256 threads); PRE > 0: latency form for
+// small phases (64 threads, so the few warps spread over all SMs).
+template <typename TF, int MODE, int PRE>
+__global__ void __launch_bounds__(PRE > 0 ? 64 : 256, PRE > 0 ? 1 : 5) k_fwd_phase(Batch B, int c) {
+  pdl_trigger();
+  if (PRE == 0) pdl_wait();
+  const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e >= __ldg(B.fwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
-  const Sys &S = B.sys[E.x];
-  if (MODE != kModePlain && !running(S.st)) return;
-  fwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff, (E.w >> 31) != 0);
+  fwd_rows<TF, MODE, PRE>(B.sys[E.x], E.y, E.z, E.w);
 }
 
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_bwd_phase(Batch B, int c) {
-  pdl_enter();
-  const int e = __ldg(B.bwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
+template <typename TF, int MODE, int PRE>
+__global__ void __launch_bounds__(PRE > 0 ? 64 : 256) k_bwd_phase(Batch B, int c) {
+  pdl_trigger();
+  if (PRE == 0) pdl_wait();
+  const int e = __ldg(B.bwd_ptr + c) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e >= __ldg(B.bwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
-  const Sys &S = B.sys[E.x];
-  if (MODE != kModePlain && !running(S.st)) return;
-  bwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff);
+  bwd_rows<TF, MODE, PRE>(B.sys[E.x], E.y, E.z, E.w);
 }
 
 // ILU0 application z = U^-1 L^-1 rhs (Algorithm 1) in one cooperative
@@ -753,17 +867,16 @@ __global__ void __launch_bounds__(1024) k_apply(Batch B) {
     const int e1 = __ldg(B.fwd_ptr + c + 1);
     for (int e = __ldg(B.fwd_ptr + c) + g; e < e1; e += W) {
       const int4 E = B.ent[e];
-      const Sys &S = B.sys[E.x];
-      if (MODE == kModePlain || running(S.st)) fwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff, (E.w >> 31) != 0);
+      fwd_rows<TF, MODE, 0>(B.sys[E.x], E.y, E.z, E.w);
     }
   }
-  for (int c = B.nphases - 2; c >= 0; --c) {
+  for (int c = B.nphases - 1; c >= 0; --c) {
+    const int e0 = __ldg(B.bwd_ptr + c), e1 = __ldg(B.bwd_ptr + c + 1);
+    if (e0 == e1) continue;  // uniform over the grid: every CTA skips together
     grid_sync(B, timed_out);
-    const int e1 = __ldg(B.bwd_ptr + c + 1);
-    for (int e = __ldg(B.bwd_ptr + c) + g; e < e1; e += W) {
+    for (int e = e0 + g; e < e1; e += W) {
       const int4 E = B.ent[e];
-      const Sys &S = B.sys[E.x];
-      if (MODE == kModePlain || running(S.st)) bwd_rows<TF, MODE>(S, E.y, E.z, E.w & 0x7fffffff);
+      bwd_rows<TF, MODE, 0>(B.sys[E.x], E.y, E.z, E.w);
     }
   }
 }
@@ -886,7 +999,7 @@ __global__ void __launch_bounds__(256) k_factor_phase(Batch B, int c) {
   const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= __ldg(B.fwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
-  factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w & 0x7fffffff);
+  factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w);
 }
 
 template <typename TF>
@@ -899,7 +1012,7 @@ __global__ void __launch_bounds__(1024) k_factor(Batch B) {
     const int e1 = __ldg(B.fwd_ptr + c + 1);
     for (int e = __ldg(B.fwd_ptr + c) + g; e < e1; e += W) {
       const int4 E = B.ent[e];
-      factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w & 0x7fffffff);
+      factor_rows<TF>(B.sys[E.x], E.y, E.z, E.w);
     }
   }
 }

@@ -56,6 +56,10 @@ struct Analysis {
   // phase_ptr[p+1]) form phase p.  For level and colour orders the phases are
   // exactly the levels and colours.
   std::vector<int32_t> phase_ptr;
+  // per 32-row slice, bit r for row 32*slice + r: (x) the row has no U block,
+  // so its backward step runs inside the forward sweep; (y) its forward
+  // result y is read later (by its own backward step or another row's L).
+  std::vector<uint32_t> sl_mask;              // 2 per slice: x, y
   int64_t d_off = 0;                          // first value of Dinv inside the factor values
   int64_t lu_vals = 0;                        // total factor values
   int32_t max_row_len = 0;

@@ -63,6 +63,7 @@ struct Runner {
   int device = 0;
   bool fp32 = false, cooperative = false, profile = false;
   int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
+  int small_entries = 0;  // sweep phases with at most this many slices take the latency form
   std::vector<int32_t> fwd_ptr, bwd_ptr;
   Batch B{};
   Sys *h_sys = nullptr;      // pinned staging of the descriptors
@@ -190,19 +191,44 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
   return R.nphases;
 }
 
+// Slabs a small-phase sweep loads ahead of its wait (register budget).
+template <typename TF>
+constexpr int sweep_preload() {
+  return sizeof(TF) == 8 ? 6 : 8;
+}
+
+// One phase of a sweep: phases of at most R.small_entries slices take the
+// latency form (two warps per CTA, constant data loaded before the wait),
+// larger ones the throughput form.
+template <typename TF, int MODE, bool FWD>
+void launch_sweep_phase(Runner &R, cudaStream_t st, int c, int cnt) {
+  constexpr int P = sweep_preload<TF>();
+  if (cnt <= R.small_entries) {
+    if (FWD) launch_pdl(k_fwd_phase<TF, MODE, P>, (cnt + 1) / 2, 64, st, R.B, c);
+    else launch_pdl(k_bwd_phase<TF, MODE, P>, (cnt + 1) / 2, 64, st, R.B, c);
+  } else {
+    if (FWD) launch_pdl(k_fwd_phase<TF, MODE, 0>, blocks8(cnt), 256, st, R.B, c);
+    else launch_pdl(k_bwd_phase<TF, MODE, 0>, blocks8(cnt), 256, st, R.B, c);
+  }
+}
+
 template <typename TF, int MODE>
 int launch_apply_t(Runner &R, cudaStream_t st) {
   if (R.cooperative) {
     launch_coop(k_apply<TF, MODE>, R.grid_apply, st, R.B);
     return 1;
   }
-  for (int c = 0; c < R.nphases; ++c)
-    launch_pdl(k_fwd_phase<TF, MODE>, blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, st, R.B, c);
-  int n = R.nphases;
-  for (int c = R.nphases - 2; c >= 0; --c) {
+  int n = 0;
+  for (int c = 0; c < R.nphases; ++c) {
+    const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
+    if (cnt == 0) continue;
+    launch_sweep_phase<TF, MODE, true>(R, st, c, cnt);
+    ++n;
+  }
+  for (int c = R.nphases - 1; c >= 0; --c) {
     const int cnt = R.bwd_ptr[c + 1] - R.bwd_ptr[c];
     if (cnt == 0) continue;
-    launch_pdl(k_bwd_phase<TF, MODE>, blocks8(cnt), 256, st, R.B, c);
+    launch_sweep_phase<TF, MODE, false>(R, st, c, cnt);
     ++n;
   }
   return n;
@@ -408,6 +434,12 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     cudaGetLastError();
     return fail(OPM_ERR_CUDA);
   }
+  int sms = 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, R->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OPM_ERR_CUDA);
+  }
+  R->small_entries = 10 * sms;
   int maxp = 0;
   for (auto *h : mem) maxp = std::max(maxp, (int)h->an.phase_ptr.size() - 1);
   R->nphases = maxp;
@@ -421,20 +453,30 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
       const int np = (int)pp.size() - 1;
       if (c >= np) continue;
       const int r0 = pp[c], r1 = pp[c + 1];
-      const int last = (c == np - 1) ? (int)0x80000000u : 0;
-      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) ent.push_back(make_int4(s, sl, r0, r1 | last));
+      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) ent.push_back(make_int4(s, sl, r0, r1));
     }
     R->fwd_ptr.push_back((int)ent.size());
     max_entries = std::max(max_entries, R->fwd_ptr[c + 1] - R->fwd_ptr[c]);
   }
+  // backward entries: per slice, the span of the phase's rows that have U
+  // blocks (the others finish in the forward sweep)
   R->bwd_ptr.assign(1, (int)ent.size());
   for (int c = 0; c < maxp; ++c) {
     for (int s = 0; s < R->nsys; ++s) {
       const auto &pp = mem[s]->an.phase_ptr;
+      const auto &mask = mem[s]->an.sl_mask;
       const int np = (int)pp.size() - 1;
-      if (c > np - 2) continue;
+      if (c >= np) continue;
       const int r0 = pp[c], r1 = pp[c + 1];
-      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) ent.push_back(make_int4(s, sl, r0, r1));
+      for (int sl = r0 >> 5; sl <= (r1 - 1) >> 5; ++sl) {
+        int lo = -1, hi = -1;
+        for (int i = std::max(r0, sl * 32); i < std::min(r1, sl * 32 + 32); ++i)
+          if (!((mask[2 * sl] >> (i & 31)) & 1u)) {
+            if (lo < 0) lo = i;
+            hi = i + 1;
+          }
+        if (lo >= 0) ent.push_back(make_int4(s, sl, lo, hi));
+      }
     }
     R->bwd_ptr.push_back((int)ent.size());
   }
@@ -673,7 +715,10 @@ opm_status alloc_system(opm_solver *h) {
   UP(p_upd, an.upd_ptr);
   UP(p_ud, an.upd_dst);
   UP(p_us, an.upd_src);
+  uint32_t *p_mask;
+  UP(p_mask, an.sl_mask);
 #undef UP
+  S.sl_mask = reinterpret_cast<const uint2 *>(p_mask);
   S.perm = p_perm;
   S.a_rp = p_arp;
   S.a_col = p_acol;

@@ -149,20 +149,37 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   if (schedule == OPM_SCHED_AUTO) schedule = OPM_SCHED_COLOUR;
   an.schedule = schedule;
 
-  // ---- schedule and permutation (perm[new] = old, stable inside a set)
+  // ---- schedule and permutation (perm[new] = old, natural order inside a group)
   std::vector<int32_t> key;
+  int32_t nkeys = 0;
   if (schedule == OPM_SCHED_NATURAL) {
     key.assign(n, 0);
     an.nsets = n > 0 ? 1 : 0;
+    nkeys = an.nsets;
   } else {
     std::vector<int64_t> gp;
     std::vector<int32_t> ga;
     symmetrise(n, rowptr, colidx, gp, ga);
     an.nsets = schedule == OPM_SCHED_LEVEL ? level_sets(n, gp, ga, key) : colour_sets(n, gp, ga, key);
+    // Inside a set, rows with no neighbour in a later set (hence no U block)
+    // come first: they finish within the forward sweep, and the backward
+    // sweep of the set covers a contiguous tail.  Rows of a set share no
+    // edge, so their order does not change the factors.  (Ordering each
+    // group by row length would even out the rows of a warp, but it
+    // scatters the pivot-row gathers of the factorisation by about as much
+    // as it gains in the sweeps and the SpMV.)
+    std::vector<int32_t> sub(n);
+    for (int32_t i = 0; i < n; ++i) {
+      bool open = false;
+      for (int64_t m = gp[i]; m < gp[i + 1] && !open; ++m) open = key[ga[m]] > key[i];
+      sub[i] = 2 * key[i] + (open ? 1 : 0);
+    }
+    key.swap(sub);
+    nkeys = 2 * an.nsets;
   }
-  std::vector<int64_t> count((size_t)an.nsets + 1, 0);
+  std::vector<int64_t> count((size_t)nkeys + 1, 0);
   for (int32_t i = 0; i < n; ++i) count[key[i] + 1]++;
-  for (int32_t s = 0; s < an.nsets; ++s) count[s + 1] += count[s];
+  for (int32_t s = 0; s < nkeys; ++s) count[s + 1] += count[s];
   an.perm.resize(n);
   an.iperm.resize(n);
   for (int32_t i = 0; i < n; ++i) {
@@ -197,6 +214,19 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   }
   an.nnz_l = an.l_rowptr[n];
   an.nnz_u = an.u_rowptr[n];
+  {
+    const int64_t ns = ((int64_t)n + kWarp - 1) / kWarp;
+    an.sl_mask.assign((size_t)(2 * ns), 0u);
+    std::vector<char> read_later((size_t)n, 0);
+    for (int32_t ni = 0; ni < n; ++ni)
+      for (int64_t c = arp[ni]; c < arp[ni] + (an.l_rowptr[ni + 1] - an.l_rowptr[ni]); ++c) read_later[pcol[c]] = 1;
+    for (int32_t ni = 0; ni < n; ++ni) {
+      const bool no_u = an.u_rowptr[ni + 1] == an.u_rowptr[ni];
+      const uint32_t bit = 1u << (ni % kWarp);
+      if (no_u) an.sl_mask[2 * (ni / kWarp)] |= bit;
+      if (!no_u || read_later[ni]) an.sl_mask[2 * (ni / kWarp) + 1] |= bit;
+    }
+  }
 
   // ---- warp-sliced layouts.  Factor values: [L | U | Dinv slices].
   std::vector<int64_t> a_pos, a_slot, l_pos, l_slot, u_pos, u_slot;

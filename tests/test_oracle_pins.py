@@ -336,6 +336,69 @@ def test_order_by_key_is_stable_and_complete():
     np.testing.assert_array_equal(perm, [1, 3, 6, 2, 5, 0, 4])
 
 
+@pytest.mark.parametrize("schedule", ["level", "colour"])
+def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
+    """Brute force on the sets the oracle returns: each set is contiguous in
+    set order; inside it the rows without a neighbour in a later set come
+    first; natural order inside each group."""
+    s = synth.random_pattern_system(60, 90, seed=11)
+    key, n = (O.levels if schedule == "level" else O.colours)(s.nb, s.rowptr, s.colidx)
+    perm, nsets = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
+    assert nsets == n and sorted(perm.tolist()) == list(range(s.nb))
+    nbrs = [set() for _ in range(s.nb)]
+    for i in range(s.nb):
+        for m in range(s.rowptr[i], s.rowptr[i + 1]):
+            j = int(s.colidx[m])
+            if j != i:
+                nbrs[i].add(j)
+                nbrs[j].add(i)
+    expect = []
+    for c in range(n):
+        rows = [i for i in range(s.nb) if key[i] == c]
+        closed = [i for i in rows if all(key[j] <= c for j in nbrs[i])]
+        opened = [i for i in rows if any(key[j] > c for j in nbrs[i])]
+        expect += closed + opened
+    assert perm.tolist() == expect
+    # a closed row has no U block in the permuted matrix
+    prow, pcol, _ = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    for ip in range(s.nb):
+        i = int(perm[ip])
+        if all(key[j] <= key[i] for j in nbrs[i]):
+            assert (pcol[prow[ip]:prow[ip + 1]] <= ip).all()
+
+
+def test_order_inside_a_colour_does_not_change_the_factors():
+    """Rows of one colour share no edge: the colour-major order with and
+    without the closed-first rule gives the same ILU0 factors row by row
+    (only the order of each row's sums may differ)."""
+    s = synth.config2()
+    key, n = O.colours(s.nb, s.rowptr, s.colidx)
+    p1 = O.order_by_key(key, n)
+    p2, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, "colour")
+    assert not np.array_equal(p1, p2)
+    f = []
+    for perm in (p1, p2):
+        prow, pcol, pval = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+        fac = O.ilu0(s.nb, prow, pcol, pval)
+        assert fac.status == 0
+        f.append((perm, prow, pcol, fac))
+    (pa, ra, ca, fa), (pb, rb, cb, fb) = f
+    ia = np.empty_like(pa)
+    ia[pa] = np.arange(s.nb)
+    ib = np.empty_like(pb)
+    ib[pb] = np.arange(s.nb)
+    np.testing.assert_allclose(fb.dinv, fa.dinv[ia[pb]], rtol=1e-12, atol=1e-14)
+    for ipb in range(0, s.nb, 53):
+        i = pb[ipb]
+        ipa = ia[i]
+        # same natural column set, mapped through each order
+        cols_b = {int(pb[c]): m for m, c in zip(range(rb[ipb], rb[ipb + 1]), cb[rb[ipb]:rb[ipb + 1]])}
+        for m in range(ra[ipa], ra[ipa + 1]):
+            j = int(pa[ca[m]])
+            mb = cols_b[j]
+            np.testing.assert_allclose(fb.lu[mb], fa.lu[m], rtol=1e-12, atol=1e-13 * np.abs(fa.lu[m]).max())
+
+
 def test_level_order_gives_the_natural_factors():
     s = synth.config2()
     nat = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
