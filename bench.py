@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--schedule", default="auto")
     p.add_argument("--grid", type=int, default=100, help="grid edge (100 = the 1M-cell workload)")
+    p.add_argument("--no-autotune", action="store_true", help="batched leg: AUTO options instead of the autotuner")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
@@ -130,6 +131,26 @@ def algorithmic_apply_bytes(info, fp32: bool) -> int:
     return factors + vectors
 
 
+# FP64 FMA peak of the GB300: 2 FP64 lanes per SM per clock (the FP64 pipe's
+# issue rate) x 152 SMs x 2.07 GHz maximum SM clock = 629 G FMA/s, i.e.
+# 1.259 TFLOP/s (the nominal 1.25 TFLOP/s FP64 of the part).
+FP64_FMA_PEAK = 2 * 152 * 2.07e9
+
+
+def iteration_work(info, fp32: bool):
+    """Algorithmic work of one BiCGStab + ILU0 iteration: HBM bytes (two
+    matrix passes, two factor passes, 27 fused vector passes of 24 n bytes)
+    and FP64 FMAs (two SpMVs of 9 per block; two preconditioner
+    applications of 9 per factor block when the factors are FP64; the dot
+    products, right-hand sides and vector updates: 36 per block row)."""
+    n, nnzb = info.nb, info.nnzb
+    matrix = 76 * nnzb + 4 * n
+    factor = (40 if fp32 else 76) * nnzb + 4 * n
+    nbytes = 2 * matrix + 2 * factor + 27 * 24 * n
+    fma = 18 * nnzb + (0 if fp32 else 18 * nnzb) + 36 * n
+    return nbytes, fma
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("kernels.cuh", "solver.cu"):
@@ -183,34 +204,63 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def tuned(precision):
+        """Launch options for this workload: the autotuner's choice, or the
+        schedule given on the command line."""
+        if args.schedule != "auto" or args.no_autotune:
+            return {"schedule": args.schedule}, {"candidates": 0}
+        with opm.Solver(s.nb, rp, ci, vals) as h:
+            b = h.spmv(xt)
+        t0 = time.perf_counter()
+        st, kw, cands, bi = opm.autotune(s.nb, rp, ci, vals, b, rtol=RTOL, maxit=200, repeats=2,
+                                         precision=precision)
+        best_of = lambda sc: min((c["ms"] for c in cands if c["schedule"] == sc and c["status"] == 0),
+                                 default=None)
+        rep = {"status": st, "chosen": kw, "candidates": len(cands), "tune_s": round(time.perf_counter() - t0, 1),
+               "ms_per_solve_best_level": best_of("level"), "ms_per_solve_best_colour": best_of("colour")}
+        if st != opm.OPM_OK:
+            return {"schedule": "auto"}, rep
+        return kw, rep
+
     def measure(precision):
-        sv = opm.Solver(s.nb, rp, ci, vals, schedule=args.schedule, precision=precision, profile_kernels=True)
+        kw, tune = tuned(precision)
+        sv = opm.Solver(s.nb, rp, ci, vals, precision=precision, **kw)
         b = sv.spmv(xt)  # b = A x_true on the GPU
         x = torch.empty_like(b)
         info = sv.info()
         stat = {}
 
-        def step():
-            st = sv.factor(vals)
-            _, st2, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+        def step(h):
+            st = h.factor(vals)
+            _, st2, it, rr = h.solve(b, x, rtol=RTOL, maxit=200)
             stat.update(st=st, st2=st2, iters=it, relres=rr)
 
         for _ in range(max(3, args.warmup)):
-            step()
+            step(sv)
         sv.reset_timing()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             e0.record()
             for _ in range(args.steps):
-                step()
+                step(sv)
             e1.record()
             torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1)
-        t = sv.timing()
+        launches = sv.timing().launches
         err = float(np.linalg.norm(x.cpu().numpy() - s.x_true) / np.linalg.norm(s.x_true))
-        return sv, dict(ms=ms, timing=t, info=info, clocks=clk.summary(), err=err, **stat)
+        # per-kernel device time from a second handle that records events
+        # around every kernel group (a host-driven loop, so not the timed one)
+        with opm.Solver(s.nb, rp, ci, vals, precision=precision, profile_kernels=True, **kw) as sp:
+            for _ in range(2):
+                step(sp)
+            sp.reset_timing()
+            for _ in range(max(3, min(args.steps, 30))):
+                step(sp)
+            t = sp.timing()
+        return sv, dict(ms=ms, timing=t, launches=launches, info=info, clocks=clk.summary(), err=err, options=kw,
+                        autotune=tune, **stat)
 
     def max_over_ranks(v):
         if not dist:
@@ -258,6 +308,25 @@ def run_ours(args, rank, world, dist):
                 "bytes_per_launch": int(nbytes), "avg_launch_us": round(avg * 1e3, 2), "launches": int(cnt),
                 "traffic": measured_traffic("apply", precision)}
 
+    def iteration(r, ms_total, precision):
+        """Per-iteration time of the timed run (its refactorisation, setup
+        and final residual taken out at their profiled averages) against the
+        HBM and FP64 FMA rooflines."""
+        t = r["timing"]
+        avg = lambda q: t.kernel_ms[q] / max(t.kernel_count[q], 1)
+        per_step = ms_total / args.steps - avg(0) - avg(4) - avg(5)
+        t_it = per_step / max(r["iters"], 1)
+        nbytes, fma = iteration_work(r["info"], precision == "fp32")
+        peak, src = peaks()
+        gbs = nbytes / (t_it * 1e-3) / 1e9
+        fmas = fma / (t_it * 1e-3)
+        return {"ms": round(t_it, 4), "iters_per_solve": r["iters"],
+                "hbm": {"bytes": int(nbytes), "achieved_gbs": round(gbs, 1), "peak_gbs": peak,
+                        "frac": round(gbs / peak, 4), "peak_source": src},
+                "fp64_fma": {"fmas": int(fma), "achieved_tflops": round(2 * fmas / 1e12, 4),
+                             "peak_tflops": round(2 * FP64_FMA_PEAK / 1e12, 4), "frac": round(fmas / FP64_FMA_PEAK, 4),
+                             "peak_source": "derived: 2 FP64 FMA lanes/SM/clock x 152 SMs x 2.07 GHz"}}
+
     def kernels(r):
         t = r["timing"]
         return {k: {"ms_total": round(t.kernel_ms[q], 3), "launches": int(t.kernel_count[q]),
@@ -277,7 +346,7 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded generator shaped like the paper's 1M-cell model)",
-        "config": {"workload": WORKLOAD, "schedule": args.schedule, "nsets": r64["info"].nsets,
+        "config": {"workload": WORKLOAD, "options": r64["options"], "nsets": r64["info"].nsets,
                    "precision": "fp64 factors and Krylov", "rtol": RTOL, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (A values 456 MB, factors 456 MB)"},
         "iters": r64["iters"], "relres": r64["relres"], "status": [r64["st"], r64["st2"]],
@@ -285,14 +354,17 @@ def run_ours(args, rank, world, dist):
         "roofline": roofline(r64, "fp64"),
         "e2e": {"value": round(world * n_e2e / e2e_s, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(s.vals.nbytes + 24 * s.nb), "d2h_bytes_per_step": int(24 * s.nb)},
-        "gpu_launches": int(r64["timing"].launches),
+        "gpu_launches": int(r64["launches"]),
         "clocks": r64["clocks"],
         "kernels": kernels(r64),
+        "iteration": iteration(r64, ms64, "fp64"),
         "fp32_factors": {"value": round(world * args.steps / (ms32 * 1e-3), 3), "unit": UNIT,
                          "ms_per_step": round(ms32 / args.steps, 4), "iters": r32["iters"],
                          "relres": r32["relres"], "x_err_vs_x_true": r32["err"], "dtype": "f64 Krylov + f32 factors",
-                         "roofline": roofline(r32, "fp32"), "kernels": kernels(r32),
-                         "gpu_launches": int(r32["timing"].launches), "clocks": r32["clocks"]},
+                         "roofline": roofline(r32, "fp32"), "kernels": kernels(r32), "options": r32["options"],
+                         "iteration": iteration(r32, ms32, "fp32"),
+                         "autotune": r32["autotune"], "gpu_launches": int(r32["launches"]), "clocks": r32["clocks"]},
+        "autotune": r64["autotune"],
     }
     sv64.close()
     sv32.close()
@@ -316,14 +388,34 @@ def measure_batched(args, barrier, max_over_ranks, world):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     syss = synth.config4(nsys=args.batch_systems)
     data = [(dev(q.rowptr), dev(q.colidx), dev(q.vals), dev(q.x_true)) for q in syss]
+    # right-hand sides b = A x_true with the library's FP64 SpMV
+    bs = []
+    for q, (rp, ci, va, xt) in zip(syss, data):
+        with opm.Solver(q.nb, rp, ci, va) as h:
+            bs.append(h.spmv(xt))
     res = {}
     for precision in ("fp32", "fp64"):
-        hs = [opm.Solver(q.nb, rp, ci, va, schedule=args.schedule, precision=precision)
+        # launch configuration: the autotuner on every fourth system (or the
+        # schedule given on the command line)
+        if args.schedule == "auto" and not args.no_autotune:
+            sub = list(range(0, len(syss), 4))
+            t_tune = time.perf_counter()
+            tst, kw, cands, bi = opm.autotune_batch(
+                [(syss[k].nb, data[k][0], data[k][1], data[k][2], bs[k]) for k in sub], rtol=[1e-2] * len(sub),
+                maxit=200, repeats=2, precision=precision)
+            tune = {"status": tst, "chosen": kw, "candidates": len(cands), "tuned_on_systems": len(sub),
+                    "tune_s": round(time.perf_counter() - t_tune, 2)}
+            if tst != opm.OPM_OK:
+                kw = {"schedule": "auto", "sweep_launch": "auto", "chunk": 0, "small_phase_slices": 0}
+        else:
+            kw = {"schedule": args.schedule, "sweep_launch": "auto", "chunk": 0, "small_phase_slices": 0}
+            tune = {"chosen": kw, "candidates": 0}
+        hs = [opm.Solver(q.nb, rp, ci, va, schedule=kw["schedule"], precision=precision)
               for q, (rp, ci, va, xt) in zip(syss, data)]
-        bs = [h.spmv(d[3]) for h, d in zip(hs, data)]
         xs = [torch.empty_like(b) for b in bs]
         vals = [d[2] for d in data]
-        with opm.Batch([h.h for h in hs]) as bt:
+        with opm.Batch([h.h for h in hs], chunk=kw["chunk"], sweep_launch=kw["sweep_launch"],
+                       small_phase_slices=kw["small_phase_slices"]) as bt:
             def step():
                 bt.factor(vals)
                 return bt.solve(bs, xs, rtol=1e-2, maxit=200)
@@ -348,7 +440,8 @@ def measure_batched(args, barrier, max_over_ranks, world):
                           "ms_per_batch": round(1e3 * dt / reps, 3),
                           "sequential_solves_per_s": round(world * len(syss) / dt_seq, 2),
                           "iters_mean": float(np.mean(it)), "iters_max": int(max(it)),
-                          "status_ok": int(sum(1 for v in st if v == 0)), "max_rel_err_vs_x_true": err}
+                          "status_ok": int(sum(1 for v in st if v == 0)), "max_rel_err_vs_x_true": err,
+                          "autotune": tune}
         for h in hs:
             h.close()
     cells = sum(q.nb for q in syss)

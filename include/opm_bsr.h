@@ -110,7 +110,13 @@ typedef struct opm_options {
   int32_t sweep_launch;  /* how the factorisation and the triangular sweeps
                             walk the phases: OPM_SWEEP_AUTO, _PER_PHASE or
                             _COOPERATIVE                                     */
-  int32_t reserved[5];
+  int32_t small_phase_slices; /* one launch per phase: phases of at most this
+                            many 32-row slices take the latency form (two
+                            warps per CTA, constant data loaded before the
+                            wait for the preceding kernel), larger ones the
+                            throughput form; 0 = default (10 per SM of the
+                            device), -1 = throughput form for every phase   */
+  int32_t reserved[4];
 } opm_options;
 
 /* Fill *opt with the defaults (AUTO schedule, FP64, default stream). */
@@ -288,6 +294,54 @@ opm_status opm_batch_launch(opm_batch b, const double *const *vals, const double
 int32_t opm_batch_ready(opm_batch b);
 opm_status opm_batch_wait(opm_batch b, int32_t *iters, double *relres, opm_status *st);
 void opm_batch_destroy(opm_batch b);
+
+/*
+ * Autotuner: picks the launch configuration of a pattern, or of a batch of
+ * patterns solved together, by timing one refactorisation plus one solve
+ * (time to solution, host clock around the synchronous calls) for each
+ * candidate configuration.  The paper fixes no schedule (it reports level
+ * scheduling and graph colouring side by side, Section 4.4); the candidates
+ * are searched coordinate-wise:
+ *   1. schedule LEVEL or COLOUR (and NATURAL when every system has at most
+ *      4,096 block rows) x sweep launch PER_PHASE (only when the schedule
+ *      has at most 1,024 phases) or COOPERATIVE;
+ *   2. for the best of 1, iterations per loop body 1, 2 or 4;
+ *   3. for the best of 2 with PER_PHASE, small_phase_slices -1 (throughput
+ *      form everywhere), 0 (default) or 1 << 30 (latency form everywhere).
+ * Each candidate creates its own handles (symbolic analysis included, not
+ * timed), runs one untimed refactorisation + solve, then `repeats` timed
+ * ones (repeats < 1 means 3) and scores their median.  A candidate whose
+ * solve fails is never chosen, nor one that does not converge while
+ * another does.  base (NULL = defaults) supplies the precision, stream and
+ * wait bound; *best receives base with the chosen schedule, sweep_launch,
+ * chunk and small_phase_slices; report (may be NULL) every candidate tried.
+ * Inputs as for opm_bsr_create / opm_bicgstab_solve (host or device).
+ * Returns OPM_OK when some candidate converged, OPM_NOT_CONVERGED when none
+ * did but one ran, else the first candidate's error.
+ */
+#define OPM_TUNE_MAX 24
+typedef struct opm_tune_entry {
+  int32_t schedule, sweep_launch, chunk, small_phase_slices;
+  int32_t status;   /* status of the last timed solve (batch: the worst)  */
+  int32_t iters;    /* iterations of the last timed solve (batch: the max) */
+  double ms;        /* median time of refactorisation + solve             */
+} opm_tune_entry;
+typedef struct opm_tune_report {
+  int32_t ncand;    /* entries filled in cand                             */
+  int32_t best;     /* index of the chosen entry, -1 if none              */
+  opm_tune_entry cand[OPM_TUNE_MAX];
+} opm_tune_report;
+
+opm_status opm_autotune(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                        const double *b, double rtol, int32_t maxit, int32_t repeats,
+                        const opm_options *base, opm_options *best, opm_tune_report *report);
+/* The batch form: system i has nb[i], rowptr[i], colidx[i], vals[i], b[i]
+ * and rtol[i] (rtol may be NULL = 1e-2); the candidates' handles are
+ * solved together through opm_batch_factor / opm_batch_solve. */
+opm_status opm_autotune_batch(int32_t nsys, const int32_t *nb, const int32_t *const *rowptr,
+                              const int32_t *const *colidx, const double *const *vals,
+                              const double *const *b, const double *rtol, int32_t maxit, int32_t repeats,
+                              const opm_options *base, opm_options *best, opm_tune_report *report);
 
 /*
  * Allocation-free true residual (the paper has no counterpart: this is a

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libopm_bsr.so")
-SOURCES = ["solver.cu", "symbolic.cpp", "noalloc.cu"]
+SOURCES = ["solver.cu", "symbolic.cpp", "noalloc.cu", "autotune.cpp"]
 HEADERS = ["kernels.cuh", "opm_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

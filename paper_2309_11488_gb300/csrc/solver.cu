@@ -415,8 +415,16 @@ void runner_destroy(Runner *R) {
 }
 
 // Work lists and graphs for a set of analysed, allocated systems.
-opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stream, int chunk, bool profile,
-                         int sweep_launch, uint64_t spin_ns, int skip_cta, Runner **out) {
+uint64_t spin_ns(const opm_options &o) {
+  return (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
+}
+
+int chunk_of(const opm_options &o) { return o.chunk > 0 ? o.chunk : 2; }
+
+opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stream, const opm_options &o,
+                         Runner **out) {
+  const int chunk = chunk_of(o), sweep_launch = o.sweep_launch, skip_cta = o.debug_skip_item;
+  const bool profile = o.profile_kernels != 0;
   *out = nullptr;
   Runner *R = new (std::nothrow) Runner();
   if (!R) return OPM_ERR_OOM;
@@ -439,7 +447,7 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     cudaGetLastError();
     return fail(OPM_ERR_CUDA);
   }
-  R->small_entries = 10 * sms;
+  R->small_entries = o.small_phase_slices > 0 ? o.small_phase_slices : o.small_phase_slices < 0 ? 0 : 10 * sms;
   int maxp = 0;
   for (auto *h : mem) maxp = std::max(maxp, (int)h->an.phase_ptr.size() - 1);
   R->nphases = maxp;
@@ -523,7 +531,7 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
   R->B.nphases = maxp;
   R->B.ntiles = R->ntiles;
   R->B.skip_cta = skip_cta;
-  R->B.spin_limit_ns = spin_ns;
+  R->B.spin_limit_ns = spin_ns(o);
   if (R->fp32) cooperative_grids<float>(*R, max_entries);
   else cooperative_grids<double>(*R, max_entries);
   if (profile) {
@@ -771,14 +779,9 @@ opm_status check_options(const opm_options &o) {
   if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
   if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
   if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;
+  if (o.small_phase_slices < -1) return OPM_ERR_ARG;
   return OPM_OK;
 }
-
-uint64_t spin_ns(const opm_options &o) {
-  return (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
-}
-
-int chunk_of(const opm_options &o) { return o.chunk > 0 ? o.chunk : 2; }
 
 // Fills the handle's per-call fields for a solve; stages host vectors.
 opm_status prepare_solve(opm_solver *h, const double *b, double *x, double rtol, int32_t maxit, bool *x_dev) {
@@ -898,8 +901,7 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   }
   if ((s = alloc_system(h)) != OPM_OK) return fail(s);
   std::vector<opm_solver *> one{h};
-  if ((s = runner_create(one, h->stream, chunk_of(o), o.profile_kernels != 0, o.sweep_launch, spin_ns(o),
-                         o.debug_skip_item, &h->run)) != OPM_OK)
+  if ((s = runner_create(one, h->stream, o, &h->run)) != OPM_OK)
     return fail(s);
   s = factor_impl(h, vals);
   if (s == OPM_ERR_ZERO_PIVOT) {
@@ -1138,8 +1140,9 @@ opm_status opm_batch_create(int32_t nsys, const opm_handle *hs, const opm_option
   opm_batch b = new (std::nothrow) opm_batch_s();
   if (!b) return OPM_ERR_OOM;
   b->members = mem;
-  opm_status s = runner_create(mem, (cudaStream_t)o.stream, chunk_of(o), false, o.sweep_launch, spin_ns(o),
-                               o.debug_skip_item, &b->run);
+  opm_options ob = o;
+  ob.profile_kernels = 0;
+  opm_status s = runner_create(mem, (cudaStream_t)o.stream, ob, &b->run);
   if (s != OPM_OK) {
     opm_batch_destroy(b);
     return s;

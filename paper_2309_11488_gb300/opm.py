@@ -40,14 +40,28 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch"]
 
 
 class opm_options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("precision", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("chunk", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
                 ("debug_skip_item", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
-                ("sweep_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("sweep_launch", ctypes.c_int32), ("small_phase_slices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+OPM_TUNE_MAX = 24
+
+
+class opm_tune_entry(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("sweep_launch", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("small_phase_slices", ctypes.c_int32), ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
+
+
+class opm_tune_report(ctypes.Structure):
+    _fields_ = [("ncand", ctypes.c_int32), ("best", ctypes.c_int32), ("cand", opm_tune_entry * OPM_TUNE_MAX)]
 
 
 class opm_info(ctypes.Structure):
@@ -131,6 +145,12 @@ def lib() -> ctypes.CDLL:
         L.opm_batch_wait.restype = i32
         L.opm_batch_destroy.argtypes = [vp]
         L.opm_batch_destroy.restype = None
+        L.opm_autotune.argtypes = [i32, vp, vp, vp, vp, f64, i32, i32, ctypes.POINTER(opm_options),
+                                   ctypes.POINTER(opm_options), ctypes.POINTER(opm_tune_report)]
+        L.opm_autotune.restype = i32
+        L.opm_autotune_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(opm_options),
+                                         ctypes.POINTER(opm_options), ctypes.POINTER(opm_tune_report)]
+        L.opm_autotune_batch.restype = i32
         _lib = L
     return _lib
 
@@ -305,12 +325,13 @@ def _ptr_array(arrays, dtype):
 class Batch:
     """A set of handles factorised and solved together (see include/opm_bsr.h)."""
 
-    def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto"):
+    def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto", small_phase_slices=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.handles = list(handles)
         hs = (ctypes.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
-        o = opm_options_default(stream=stream, chunk=chunk, sweep_launch=sweep_launch)
+        o = opm_options_default(stream=stream, chunk=chunk, sweep_launch=sweep_launch,
+                                small_phase_slices=small_phase_slices)
         out = ctypes.c_void_p()
         st = lib().opm_batch_create(len(self.handles), hs, ctypes.byref(o), ctypes.byref(out))
         if st != OPM_OK:
@@ -382,12 +403,14 @@ class Solver:
     """Convenience owner of one handle (context manager)."""
 
     def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
-                 spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto"):
+                 spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto",
+                 small_phase_slices=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
                                            spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item,
-                                           profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch)
+                                           profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch,
+                                           small_phase_slices=small_phase_slices)
         self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options)
         self.nb = nb
 
@@ -456,3 +479,51 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ autotuner
+
+def _tune_result(st, best, rep):
+    names = {v: k for k, v in SCHEDULES.items()}
+    sweeps = {v: k for k, v in SWEEPS.items()}
+    cands = [{"schedule": names[e.schedule], "sweep_launch": sweeps[e.sweep_launch], "chunk": e.chunk,
+              "small_phase_slices": e.small_phase_slices, "status": e.status, "iters": e.iters, "ms": e.ms}
+             for e in rep.cand[:rep.ncand]]
+    kw = {"schedule": names[best.schedule], "sweep_launch": sweeps[best.sweep_launch], "chunk": best.chunk,
+          "small_phase_slices": best.small_phase_slices}
+    return st, kw, cands, rep.best
+
+
+def autotune(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, repeats=3, precision="fp64", stream=None):
+    """opm_autotune: returns (status, best keyword options for Solver,
+    candidates tried, index of the chosen candidate)."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    base = opm_options_default(precision=precision, stream=stream)
+    best = opm_options()
+    rep = opm_tune_report()
+    st = lib().opm_autotune(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32), _ptr(vals, np.float64),
+                            _ptr(b, np.float64), float(rtol), int(maxit), int(repeats), ctypes.byref(base),
+                            ctypes.byref(best), ctypes.byref(rep))
+    return _tune_result(st, best, rep)
+
+
+def autotune_batch(systems, rtol=None, maxit=200, repeats=3, precision="fp64", stream=None):
+    """opm_autotune_batch over systems = [(nb, rowptr, colidx, vals, b), ...];
+    returns (status, best keyword options (schedule for the members' Solver,
+    the rest for Batch), candidates tried, index of the chosen candidate)."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    n = len(systems)
+    nbs = (ctypes.c_int32 * n)(*[int(s[0]) for s in systems])
+    rp, k1 = _ptr_array([s[1] for s in systems], np.int32)
+    ci, k2 = _ptr_array([s[2] for s in systems], np.int32)
+    va, k3 = _ptr_array([s[3] for s in systems], np.float64)
+    bv, k4 = _ptr_array([s[4] for s in systems], np.float64)
+    rt = (ctypes.c_double * n)(*rtol) if rtol is not None else None
+    base = opm_options_default(precision=precision, stream=stream)
+    best = opm_options()
+    rep = opm_tune_report()
+    st = lib().opm_autotune_batch(n, nbs, rp, ci, va, bv, rt, int(maxit), int(repeats), ctypes.byref(base),
+                                  ctypes.byref(best), ctypes.byref(rep))
+    return _tune_result(st, best, rep)

@@ -92,3 +92,45 @@ def test_product_package_never_imports_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.c" not in txt and "liboracle" not in txt, f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets a C
+    compiler gives the header's structures (plain gcc on this host)."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    checks = {"opm_options": opm.opm_options, "opm_info": opm.opm_info, "opm_timing": opm.opm_timing,
+              "opm_tune_entry": opm.opm_tune_entry, "opm_tune_report": opm.opm_tune_report}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "opm_bsr.h"', 'int main(void) {']
+    for cname, cls in checks.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('  return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, cls in checks.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_autotune_rejects_bad_arguments_on_the_host():
+    s = synth.config1()
+    st, kw, cands, best = opm.autotune(-1, s.rowptr, s.colidx, s.vals, np.zeros(3))
+    assert st == opm.OPM_ERR_ARG and cands == [] and best == -1
+    st, kw, cands, best = opm.autotune(s.nb, s.rowptr, s.colidx, s.vals, np.zeros(3 * s.nb), maxit=-1)
+    assert st == opm.OPM_ERR_ARG
+    st, kw, cands, best = opm.autotune_batch([], maxit=10)
+    assert st == opm.OPM_ERR_ARG
