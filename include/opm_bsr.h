@@ -70,7 +70,14 @@ enum {
   OPM_SCHED_AUTO = 0,    /* the library picks (currently: colouring)          */
   OPM_SCHED_NATURAL = 1, /* caller's order; sequential dependency chains      */
   OPM_SCHED_LEVEL = 2,   /* level scheduling: same factors as natural order   */
-  OPM_SCHED_COLOUR = 3   /* greedy graph colouring: a different ILU0          */
+  OPM_SCHED_COLOUR = 3,  /* greedy graph colouring, rows in natural order: a
+                            different ILU0                                    */
+  OPM_SCHED_COLOUR_SL = 4 /* greedy graph colouring, rows in smallest-last
+                            order (Matula & Beck 1983: repeatedly remove a row
+                            of least remaining degree, ties to the lowest row;
+                            colour in reverse removal order): at most one more
+                            colour than the pattern's degeneracy, usually
+                            fewer colours than natural order                 */
 };
 
 /* Storage precision of the ILU0 factors.  The Krylov recurrences, dots,

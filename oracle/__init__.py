@@ -15,7 +15,8 @@ Section references are to arXiv 2309.11488:
   * ILU0 application            -- Section 2.2, Algorithm 1, equations 3-4
   * BiCGStab and stopping rule  -- Section 4.2 (method: van der Vorst 1992,
                                    right preconditioning, x0 = 0)
-  * level scheduling / colouring-- Section 4.4
+  * level scheduling / colouring-- Section 4.4 (greedy colouring in natural or
+                                   smallest-last order)
 """
 from __future__ import annotations
 
@@ -73,6 +74,8 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_colours_sl.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        L.orc_colours_sl.restype = ctypes.c_int32
         L.orc_closed_first_key.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
         L.orc_closed_first_key.restype = None
         L.orc_permute.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _f64p]
@@ -192,6 +195,13 @@ def colours(nb, rowptr, colidx):
     return col, int(n)
 
 
+def colours_sl(nb, rowptr, colidx):
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    col = np.empty(nb, dtype=np.int32)
+    n = lib().orc_colours_sl(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(col, _i32p))
+    return col, int(n)
+
+
 def order_by_key(key, nkeys):
     key = _i32(key)
     perm = np.empty(key.shape[0], dtype=np.int32)
@@ -200,22 +210,31 @@ def order_by_key(key, nkeys):
 
 
 def schedule_perm(nb, rowptr, colidx, schedule):
-    """perm[new] = old for 'natural', 'level' or 'colour' (Section 4.4):
+    """perm[new] = old for 'natural', 'level', 'colour' or 'colour_sl' (Section 4.4):
     set-major; inside a set the closed rows (no neighbour in a later set)
-    first, natural order inside each group.  Returns (perm, number of sets)."""
+    first; inside each of these groups the rows longer than the most common
+    row length last; natural order inside each part.  Returns (perm, number
+    of sets)."""
     if schedule == "natural":
         return np.arange(nb, dtype=np.int32), 1
     if schedule == "level":
         key, n = levels(nb, rowptr, colidx)
     elif schedule == "colour":
         key, n = colours(nb, rowptr, colidx)
+    elif schedule == "colour_sl":
+        key, n = colours_sl(nb, rowptr, colidx)
     else:
         raise ValueError(schedule)
-    # inside each set: rows without a neighbour in a later set first
+    # inside each set: rows without a neighbour in a later set first; inside
+    # each of these two groups, rows with more blocks than the most common
+    # count (ties to the smaller count) last
     rowptr, colidx = _i32(rowptr), _i32(colidx)
     key2 = np.empty(nb, dtype=np.int32)
     lib().orc_closed_first_key(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(_i32(key), _i32p), _p(key2, _i32p))
-    return order_by_key(key2, 2 * n), n
+    lens = np.diff(rowptr)
+    common = int(np.argmax(np.bincount(lens))) if nb else 0
+    key3 = 2 * key2 + (lens > common).astype(np.int32)
+    return order_by_key(key3, 4 * n), n
 
 
 def permute(nb, rowptr, colidx, vals, perm):

@@ -546,6 +546,114 @@ void orc_closed_first_key(int32_t nb, const int32_t *rowptr, const int32_t *coli
     }
 }
 
+/* binary min-heap of int64 keys (smallest-last colouring below) */
+typedef struct {
+  int64_t *k;
+  int64_t n, cap;
+} orc_heap;
+
+static void heap_push(orc_heap *h, int64_t key) {
+  if (h->n == h->cap) {
+    h->cap = h->cap ? 2 * h->cap : 1024;
+    h->k = realloc(h->k, sizeof(int64_t) * (size_t)h->cap);
+  }
+  int64_t i = h->n++;
+  while (i > 0 && h->k[(i - 1) / 2] > key) {
+    h->k[i] = h->k[(i - 1) / 2];
+    i = (i - 1) / 2;
+  }
+  h->k[i] = key;
+}
+
+static int64_t heap_pop(orc_heap *h) {
+  int64_t top = h->k[0], last = h->k[--h->n], i = 0;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= h->n) break;
+    if (c + 1 < h->n && h->k[c + 1] < h->k[c]) ++c;
+    if (h->k[c] >= last) break;
+    h->k[i] = h->k[c];
+    i = c;
+  }
+  if (h->n > 0) h->k[i] = last;
+  return top;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Greedy colouring in smallest-last order (Matula & Beck 1983, one of the
+ * colouring reorders Section 4.4 leaves open): the rows are removed one at a
+ * time from the symmetrised pattern, each time a row of least degree
+ * (distinct neighbours still present; ties to the lowest row), and then
+ * coloured first-fit in the reverse order of removal.  Returns the number
+ * of colours.
+ */
+int32_t orc_colours_sl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *colour) {
+  int64_t *gptr;
+  int32_t *gadj;
+  sym_graph(nb, rowptr, colidx, &gptr, &gadj);
+  /* distinct neighbours, sorted, packed in place */
+  int64_t *dptr = malloc(sizeof(int64_t) * ((size_t)nb + 1));
+  int64_t w = 0;
+  dptr[0] = 0;
+  for (int32_t i = 0; i < nb; ++i) {
+    int64_t a = gptr[i], b = gptr[i + 1];
+    qsort(gadj + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+    for (int64_t m = a; m < b; ++m)
+      if (m == a || gadj[m] != gadj[m - 1]) gadj[w++] = gadj[m];
+    dptr[i + 1] = w;
+  }
+  int32_t *deg = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1));
+  char *gone = calloc((size_t)(nb ? nb : 1), 1);
+  int32_t *order = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1));
+  orc_heap h = {0, 0, 0};
+  for (int32_t i = 0; i < nb; ++i) {
+    deg[i] = (int32_t)(dptr[i + 1] - dptr[i]);
+    heap_push(&h, ((int64_t)deg[i] << 32) | (int64_t)i);
+  }
+  int32_t cnt = 0;
+  while (h.n > 0) {
+    int64_t key = heap_pop(&h);
+    int32_t v = (int32_t)(key & 0xffffffff), d = (int32_t)(key >> 32);
+    if (gone[v] || d != deg[v]) continue; /* a stale entry */
+    gone[v] = 1;
+    order[cnt++] = v;
+    for (int64_t m = dptr[v]; m < dptr[v + 1]; ++m) {
+      int32_t u = gadj[m];
+      if (!gone[u]) {
+        deg[u]--;
+        heap_push(&h, ((int64_t)deg[u] << 32) | (int64_t)u);
+      }
+    }
+  }
+  int32_t ncol = 0;
+  int32_t *stamp = malloc(sizeof(int32_t) * ((size_t)nb + 1));
+  for (int32_t i = 0; i <= nb; ++i) stamp[i] = -1;
+  for (int32_t i = 0; i < nb; ++i) colour[i] = -1;
+  for (int32_t t = cnt - 1; t >= 0; --t) {
+    int32_t v = order[t];
+    for (int64_t m = dptr[v]; m < dptr[v + 1]; ++m)
+      if (colour[gadj[m]] >= 0) stamp[colour[gadj[m]]] = v;
+    int32_t c = 0;
+    while (stamp[c] == v) ++c;
+    colour[v] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  free(h.k);
+  free(stamp);
+  free(order);
+  free(gone);
+  free(deg);
+  free(dptr);
+  free(gptr);
+  free(gadj);
+  return ncol;
+}
+
 /* perm[new] = old: rows ordered by key, natural order inside each key
    (a stable counting sort) */
 void orc_order_by_key(int32_t nb, const int32_t *key, int32_t nkeys, int32_t *perm) {

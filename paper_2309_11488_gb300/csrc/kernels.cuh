@@ -21,10 +21,9 @@
 // 4.4).  The sweeps walk the phases in order, either one launch per phase
 // or one cooperative launch with a bounded grid barrier between phases.
 //
-// Reductions: one partial per tile in a fixed butterfly; the last CTA of a
-// system to finish (atomic counter) sums that system's partials in tile
-// order and runs the scalar part of BiCGStab (alpha, omega, beta, the
-// stopping rule).
+// Reductions: per system in a fixed order (see red_end and
+// last_cta_reduce); the warp or CTA that completes a system's sum runs the
+// scalar part of BiCGStab (alpha, omega, beta, the stopping rule).
 #pragma once
 
 #include <cstdint>
@@ -52,7 +51,9 @@ struct Sys {
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
   void *y;   // forward intermediate (factor precision)
-  double *partials;
+  double *partials;      // per tile: up to 4 partial sums
+  double *grp_partials;  // per group of 32 tiles: up to 4 partial sums
+  uint32_t *grp_count;   // per group of 32 tiles: tiles done (0 between kernels)
   DevState *st;
   // per call
   const double *b_in;    // right-hand side, or the input of spmv / ilu_apply (caller's order)
@@ -147,38 +148,147 @@ __device__ __forceinline__ bool inv3(const T (&a)[9], T (&o)[9]) {
   return ok;
 }
 
-// Deterministic reduction of NV values over a CTA; the result is valid in
-// thread 0.
+// ------------------------------------------------------------ reductions
+//
+// A per-system sum of NV values without CTA-wide barriers, in a fixed order:
+// every warp sums its lanes (xor butterfly); the last warp of the CTA to
+// finish adds the CTA's warp sums in warp order (the tile's partial); the
+// last tile of each group of 32 tiles adds the group's tile partials (xor
+// butterfly over 32 lanes); the last group of the system adds the group
+// partials (strided over the lanes, then the butterfly).  Warps that are not
+// last simply exit, so no warp idles at a barrier, and the system's final
+// sum is one warp's work.  The order depends only on the tile index, so a
+// system's sums are the same alone and inside any batch.
+
+constexpr int kMaxWarps = 8;  // warps per CTA of the reducing kernels (256 threads)
+
 template <int NV>
-__device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
+struct RedShared {
+  double wsum[kMaxWarps][NV];
+  unsigned count;
+};
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
   }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sm[w * NV + q] = v[q];
-  }
+}
+
+// Called by every thread at kernel start (one CTA barrier).
+template <int NV>
+__device__ __forceinline__ void red_begin(RedShared<NV> &rs) {
+  if (threadIdx.x == 0) rs.count = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
+}
+
+// The CTA's last warp: tile partial, group partial, system sum (kept out of
+// line: it runs once per CTA, and inlined it raises the register count of
+// the whole kernel).
+template <int NV>
+__device__ __noinline__ bool red_tail(RedShared<NV> &rs, const Sys &S, int tile, int ntiles, int nw, int lane,
+                                      double (&tot)[NV]) {
+  unsigned t = 0;
+  // the tile's partial, warps in order
+  const int g = tile >> 5, ng = (ntiles + 31) >> 5, gsize = min(32, ntiles - 32 * g);
+  if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double acc = 0.0;
-      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) acc += sm[ww * NV + q];
-      v[q] = acc;
+      double p = 0.0;
+#pragma unroll 1
+      for (int ww = 0; ww < nw; ++ww) p += rs.wsum[ww][q];
+      S.partials[(size_t)tile * NV + q] = p;
     }
+    __threadfence();
+    t = atomicAdd(&S.grp_count[g], 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)gsize - 1) return false;
+  __threadfence();
+  // the group's partial: lane l holds tile 32 g + l
+  double gp[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) gp[q] = lane < gsize ? __ldcg(S.partials + (size_t)(32 * g + lane) * NV + q) : 0.0;
+  warp_sum<NV>(gp);
+  if (lane == 0) {
+    S.grp_count[g] = 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) S.grp_partials[(size_t)g * NV + q] = gp[q];
+    __threadfence();
+    t = atomicAdd(&S.st->red_count, 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)ng - 1) return false;
+  __threadfence();
+  // the system's sum: groups strided over the lanes, then the butterfly
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = 0.0;
+#pragma unroll 1
+  for (int gg = lane; gg < ng; gg += 32) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] += __ldcg(S.grp_partials + (size_t)gg * NV + q);
+  }
+  warp_sum<NV>(tot);
+  if (lane == 0) S.st->red_count = 0;
+  return true;
+}
+
+// Adds the calling warp's values v to tile `tile` of a system with ntiles
+// tiles.  Returns true in every lane of the one warp that completes the
+// system's sum; tot is then valid in all its lanes.
+template <int NV>
+__device__ __forceinline__ bool red_end(double (&v)[NV], RedShared<NV> &rs, const Sys &S, int tile, int ntiles,
+                                        double (&tot)[NV]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  warp_sum<NV>(v);
+  unsigned t = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) rs.wsum[w][q] = v[q];
+    __threadfence_block();
+    t = atomicAdd(&rs.count, 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)nw - 1) return false;
+  __threadfence_block();
+  return red_tail<NV>(rs, S, tile, ntiles, nw, lane, tot);
+}
+
+// The second form: a CTA-wide tree in shared memory (values leave the
+// registers at once), then the system's last CTA sums the tile partials in
+// tile order.  k_spmv_t's three sums use it: measured on GB300 its launch
+// takes 147 us this way against 172 us with red_end (same arithmetic order
+// class, both deterministic), while the one- and two-value kernels are
+// faster with red_end (k_spmv_v 135 against 140 us).
+constexpr int kRedThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double *sm) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sm[q * kRedThreads + t] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (t < h) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) sm[q * kRedThreads + t] += sm[q * kRedThreads + t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = sm[q * kRedThreads];
   }
   __syncthreads();
 }
 
-// Partial of this tile, then the system's last CTA sums all its partials in
-// tile order.  Returns true in that CTA; tot is then valid in thread 0.
 template <int NV>
 __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, int tile, int ntiles,
                                                 double (&tot)[NV]) {
-  __shared__ double sm[32 * NV];
+  __shared__ double sm[kRedThreads * NV];
   __shared__ int amlast;
   block_reduce<NV>(v, sm);
   if (threadIdx.x == 0) {
@@ -194,6 +304,7 @@ __device__ __forceinline__ bool last_cta_reduce(double (&v)[NV], const Sys &S, i
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+#pragma unroll 8
   for (int b = threadIdx.x; b < ntiles; b += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] += __ldcg(S.partials + (size_t)b * NV + q);
@@ -260,6 +371,8 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
 // Starts a solve: r = P b, r^ = r, x = p = v = 0, ||b||^2; the system's
 // last CTA sets the scalars.  A factorisation error makes the solve fail.
 __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
+  __shared__ RedShared<1> rs_;
+  red_begin<1>(rs_);
   OPM_TILE(B, S, lt);
   if (blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
   double acc[1] = {0.0};
@@ -280,7 +393,7 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, S.ntiles, tot) && threadIdx.x == 0) {
+  if (red_end<1>(acc, rs_, S, lt, S.ntiles, tot) && (threadIdx.x & 31) == 0) {
     DevState *st = S.st;
     const double n0 = sqrt(tot[0]);
     st->n0 = n0;
@@ -306,6 +419,8 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).
 __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
+  __shared__ RedShared<1> rs_;
+  red_begin<1>(rs_);
   pdl_enter();
   OPM_TILE_S(B, S, lt);
   if (!running(S.st)) return;
@@ -322,7 +437,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, S.ntiles_s, tot) && threadIdx.x == 0) {
+  if (red_end<1>(acc, rs_, S, lt, S.ntiles_s, tot) && (threadIdx.x & 31) == 0) {
     DevState *st = S.st;
     st->rhv = tot[0];
     if (tot[0] == 0.0) {
@@ -335,7 +450,8 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(256, 7) k_spmv_t(Batch B) {
+__global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
+
   pdl_enter();
   OPM_TILE_S(B, S, lt);
   if (!running(S.st)) return;
@@ -378,7 +494,9 @@ __global__ void __launch_bounds__(256, 7) k_spmv_t(Batch B) {
 
 // x += alpha p^ + omega s^, r = s - omega t, ||r||^2, (r^, r); stopping rule,
 // then beta for the next iteration.
-__global__ void __launch_bounds__(256, 6) k_update(Batch B) {
+__global__ void __launch_bounds__(256, 8) k_update(Batch B) {
+  __shared__ RedShared<2> rs_;
+  red_begin<2>(rs_);
   pdl_enter();
   OPM_TILE(B, S, lt);
   if (!running(S.st)) return;
@@ -404,7 +522,7 @@ __global__ void __launch_bounds__(256, 6) k_update(Batch B) {
     }
   }
   double tot[2];
-  if (last_cta_reduce<2>(acc, S, lt, S.ntiles, tot) && threadIdx.x == 0) {
+  if (red_end<2>(acc, rs_, S, lt, S.ntiles, tot) && (threadIdx.x & 31) == 0) {
     DevState *st = S.st;
     const int k = st->k;
     if (half) {
@@ -436,6 +554,8 @@ __global__ void __launch_bounds__(256, 6) k_update(Batch B) {
 // Final true residual ||b - A x|| / ||b|| in FP64 and x back to the caller's
 // order (zeros on a failed solve).
 __global__ void __launch_bounds__(256, 8) k_finish(Batch B) {
+  __shared__ RedShared<1> rs_;
+  red_begin<1>(rs_);
   OPM_TILE_S(B, S, lt);
   const int status = S.st->status;
   const bool ok = (status == OPM_OK || status == OPM_NOT_CONVERGED) && S.st->error == 0;
@@ -455,7 +575,7 @@ __global__ void __launch_bounds__(256, 8) k_finish(Batch B) {
     }
   }
   double tot[1];
-  if (last_cta_reduce<1>(acc, S, lt, S.ntiles_s, tot) && threadIdx.x == 0) {
+  if (red_end<1>(acc, rs_, S, lt, S.ntiles_s, tot) && (threadIdx.x & 31) == 0) {
     DevState *st = S.st;
     st->relres = !ok ? nan("") : (st->n0 > 0.0 ? sqrt(tot[0]) / st->n0 : 0.0);
   }

@@ -757,6 +757,10 @@ opm_status alloc_system(opm_solver *h) {
   for (double **pv : vecs)
     if ((s = dalloc(A, bytes, pv, 3 * (size_t)nb)) != OPM_OK) return s;
   if ((s = dalloc(A, bytes, &S.partials, 4 * (size_t)S.ntiles_s)) != OPM_OK) return s;
+  const size_t ngroups = ((size_t)S.ntiles_s + 31) / 32;
+  if ((s = dalloc(A, bytes, &S.grp_partials, 4 * ngroups)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, &S.grp_count, ngroups)) != OPM_OK) return s;
+  CK(cudaMemsetAsync(S.grp_count, 0, sizeof(uint32_t) * ngroups, st));
   if ((s = dalloc(A, bytes, &S.st, 1)) != OPM_OK) return s;
   DevState init{};
   init.status = OPM_OK;
@@ -775,7 +779,7 @@ opm_status alloc_system(opm_solver *h) {
 }
 
 opm_status check_options(const opm_options &o) {
-  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR) return OPM_ERR_ARG;
+  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR_SL) return OPM_ERR_ARG;
   if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
   if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
   if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;

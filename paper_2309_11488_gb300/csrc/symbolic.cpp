@@ -6,6 +6,7 @@
 #include <climits>
 #include <cstring>
 #include <numeric>
+#include <queue>
 #include <utility>
 
 #include "opm_internal.h"
@@ -75,6 +76,59 @@ int32_t colour_sets(int32_t n, const std::vector<int64_t> &gp, const std::vector
     int32_t c = 0;
     while ((size_t)c < stamp.size() && stamp[c] == i) ++c;
     key[i] = c;
+    nsets = std::max(nsets, c + 1);
+  }
+  return nsets;
+}
+
+// Greedy first-fit colouring in smallest-last order (Matula & Beck): rows
+// are removed one at a time, each time one of least degree among those left
+// (distinct neighbours still present; ties to the lowest row), then coloured
+// in the reverse order of removal.
+int32_t colour_sets_sl(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                       std::vector<int32_t> &key) {
+  // distinct neighbour lists
+  std::vector<int64_t> dp((size_t)n + 1, 0);
+  std::vector<int32_t> da;
+  da.reserve(ga.size());
+  std::vector<int32_t> tmp;
+  for (int32_t i = 0; i < n; ++i) {
+    tmp.assign(ga.begin() + gp[i], ga.begin() + gp[i + 1]);
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    da.insert(da.end(), tmp.begin(), tmp.end());
+    dp[i + 1] = (int64_t)da.size();
+  }
+  std::vector<int32_t> deg(n), order;
+  order.reserve(n);
+  std::vector<char> gone(n, 0);
+  std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> heap;
+  for (int32_t i = 0; i < n; ++i) {
+    deg[i] = (int32_t)(dp[i + 1] - dp[i]);
+    heap.push(((int64_t)deg[i] << 32) | i);
+  }
+  while (!heap.empty()) {
+    const int64_t k = heap.top();
+    heap.pop();
+    const int32_t v = (int32_t)(k & 0xffffffff), d = (int32_t)(k >> 32);
+    if (gone[v] || d != deg[v]) continue;  // stale entry
+    gone[v] = 1;
+    order.push_back(v);
+    for (int64_t m = dp[v]; m < dp[v + 1]; ++m) {
+      const int32_t u = da[m];
+      if (!gone[u]) heap.push(((int64_t)(--deg[u]) << 32) | u);
+    }
+  }
+  key.assign(n, -1);
+  std::vector<int32_t> stamp((size_t)n + 1, -1);
+  int32_t nsets = n > 0 ? 1 : 0;
+  for (auto it = order.rbegin(); it != order.rend(); ++it) {
+    const int32_t v = *it;
+    for (int64_t m = dp[v]; m < dp[v + 1]; ++m)
+      if (key[da[m]] >= 0) stamp[key[da[m]]] = v;
+    int32_t c = 0;
+    while (stamp[c] == v) ++c;
+    key[v] = c;
     nsets = std::max(nsets, c + 1);
   }
   return nsets;
@@ -160,22 +214,32 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     std::vector<int64_t> gp;
     std::vector<int32_t> ga;
     symmetrise(n, rowptr, colidx, gp, ga);
-    an.nsets = schedule == OPM_SCHED_LEVEL ? level_sets(n, gp, ga, key) : colour_sets(n, gp, ga, key);
+    an.nsets = schedule == OPM_SCHED_LEVEL    ? level_sets(n, gp, ga, key)
+               : schedule == OPM_SCHED_COLOUR ? colour_sets(n, gp, ga, key)
+                                              : colour_sets_sl(n, gp, ga, key);
     // Inside a set, rows with no neighbour in a later set (hence no U block)
     // come first: they finish within the forward sweep, and the backward
     // sweep of the set covers a contiguous tail.  Rows of a set share no
-    // edge, so their order does not change the factors.  (Ordering each
-    // group by row length would even out the rows of a warp, but it
-    // scatters the pivot-row gathers of the factorisation by about as much
-    // as it gains in the sweeps and the SpMV.)
+    // edge, so their order does not change the factors.
+    // Inside each of those two groups the few rows longer than the most
+    // common row length (fault connections, ties to the smaller length) go
+    // last, so that most warps hold rows of nearly equal length.
+    std::vector<int64_t> hist;
+    for (int32_t i = 0; i < n; ++i) {
+      const int32_t len = rowptr[i + 1] - rowptr[i];
+      if ((size_t)len >= hist.size()) hist.resize((size_t)len + 1, 0);
+      hist[len]++;
+    }
+    const int32_t common = (int32_t)(std::max_element(hist.begin(), hist.end()) - hist.begin());
     std::vector<int32_t> sub(n);
     for (int32_t i = 0; i < n; ++i) {
       bool open = false;
       for (int64_t m = gp[i]; m < gp[i + 1] && !open; ++m) open = key[ga[m]] > key[i];
-      sub[i] = 2 * key[i] + (open ? 1 : 0);
+      const bool longer = rowptr[i + 1] - rowptr[i] > common;
+      sub[i] = 2 * (2 * key[i] + (open ? 1 : 0)) + (longer ? 1 : 0);
     }
     key.swap(sub);
-    nkeys = 2 * an.nsets;
+    nkeys = 4 * an.nsets;
   }
   std::vector<int64_t> count((size_t)nkeys + 1, 0);
   for (int32_t i = 0; i < n; ++i) count[key[i] + 1]++;

@@ -330,19 +330,65 @@ def test_schedule_sets_are_independent_and_minimal(maker):
     assert nl == lev.max() + 1 and nc == col.max() + 1
 
 
+@pytest.mark.parametrize("maker", [lambda: synth.random_pattern_system(120, 4, 9),
+                                   lambda: synth.random_pattern_system(200, 2, 3), synth.config1])
+def test_smallest_last_colouring_brute_force(maker):
+    """Smallest-last greedy colouring (Matula & Beck 1983) by its definition,
+    quadratic and plain: remove a least-degree row (ties to the lowest row)
+    until none is left, colour first-fit in reverse removal order; the
+    colour count is at most one more than the largest degree met at a
+    removal (the degeneracy bound)."""
+    s = maker()
+    a, b = _edges(s)
+    nbrs = [set() for _ in range(s.nb)]
+    for x, y in zip(a.tolist(), b.tolist()):
+        nbrs[x].add(y)
+        nbrs[y].add(x)
+    left = set(range(s.nb))
+    order, worst = [], 0
+    while left:
+        v = min(left, key=lambda i: (len(nbrs[i] & left), i))
+        worst = max(worst, len(nbrs[v] & left))
+        order.append(v)
+        left.remove(v)
+    expect = np.full(s.nb, -1)
+    for v in reversed(order):
+        used = {int(expect[u]) for u in nbrs[v] if expect[u] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        expect[v] = c
+    col, n = O.colours_sl(s.nb, s.rowptr, s.colidx)
+    np.testing.assert_array_equal(col, expect)
+    assert n == expect.max() + 1 <= worst + 1
+    assert np.all(col[a] != col[b])
+
+
+def test_smallest_last_colours_a_grid_with_two_colours_and_faults_with_few():
+    s = grid_pattern(6, 5, 4)
+    col, n = O.colours_sl(s.nb, s.rowptr, s.colidx)
+    a, b = _edges(s)
+    assert n == 2 and np.all(col[a] != col[b])
+    c2 = synth.config2()
+    _, n_nat = O.colours(c2.nb, c2.rowptr, c2.colidx)
+    _, n_sl = O.colours_sl(c2.nb, c2.rowptr, c2.colidx)
+    assert n_sl <= n_nat
+
+
 def test_order_by_key_is_stable_and_complete():
     key = np.array([2, 0, 1, 0, 2, 1, 0])
     perm = O.order_by_key(key, 3)
     np.testing.assert_array_equal(perm, [1, 3, 6, 2, 5, 0, 4])
 
 
-@pytest.mark.parametrize("schedule", ["level", "colour"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
 def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
     """Brute force on the sets the oracle returns: each set is contiguous in
     set order; inside it the rows without a neighbour in a later set come
-    first; natural order inside each group."""
+    first; inside each of those groups the rows with more blocks than the
+    most common count come last; natural order inside each part."""
     s = synth.random_pattern_system(60, 90, seed=11)
-    key, n = (O.levels if schedule == "level" else O.colours)(s.nb, s.rowptr, s.colidx)
+    key, n = {"level": O.levels, "colour": O.colours, "colour_sl": O.colours_sl}[schedule](s.nb, s.rowptr, s.colidx)
     perm, nsets = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
     assert nsets == n and sorted(perm.tolist()) == list(range(s.nb))
     nbrs = [set() for _ in range(s.nb)]
@@ -353,11 +399,17 @@ def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
                 nbrs[i].add(j)
                 nbrs[j].add(i)
     expect = []
+    lens = [int(s.rowptr[i + 1] - s.rowptr[i]) for i in range(s.nb)]
+    counts = {}
+    for v in lens:
+        counts[v] = counts.get(v, 0) + 1
+    common = min(v for v in counts if counts[v] == max(counts.values()))
     for c in range(n):
         rows = [i for i in range(s.nb) if key[i] == c]
         closed = [i for i in rows if all(key[j] <= c for j in nbrs[i])]
         opened = [i for i in rows if any(key[j] > c for j in nbrs[i])]
-        expect += closed + opened
+        for grp in (closed, opened):
+            expect += [i for i in grp if lens[i] <= common] + [i for i in grp if lens[i] > common]
     assert perm.tolist() == expect
     # a closed row has no U block in the permuted matrix
     prow, pcol, _ = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
