@@ -191,10 +191,12 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
   return R.nphases;
 }
 
-// Slabs a small-phase sweep loads ahead of its wait (register budget).
+// Slabs a small-phase sweep loads ahead of its wait: 8 covers nearly every
+// row of the small colours (high-degree rows) and fits the 255-register
+// budget without spills for FP64 blocks.
 template <typename TF>
 constexpr int sweep_preload() {
-  return sizeof(TF) == 8 ? 6 : 8;
+  return 8;
 }
 
 // One phase of a sweep: phases of at most R.small_entries slices take the
