@@ -160,13 +160,15 @@ def kernel_source_hash() -> str:
 
 
 def measured_traffic(kernel: str, precision: str):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary (the
+    JSON block of profiles/apply_traffic_c3_949871cells.md), if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "apply_traffic_c3_949871cells.md")
     try:
         with open(path) as f:
-            d = json.load(f)
-    except (OSError, ValueError):
+            txt = f.read()
+        d = json.loads(txt.split("```json", 1)[1].split("```", 1)[0])
+    except (OSError, ValueError, IndexError):
         return None
     e = d.get(f"{kernel}_{precision}")
     if not e or e.get("source_hash") != kernel_source_hash():
