@@ -15,6 +15,8 @@ Section references are to arXiv 2309.11488:
   * ILU0 application            -- Section 2.2, Algorithm 1, equations 3-4
   * BiCGStab and stopping rule  -- Section 4.2 (method: van der Vorst 1992,
                                    right preconditioning, x0 = 0)
+  * block-Jacobi ILU0           -- Section 4.5 (partition-internal blocks
+                                   only; copy by an index vector)
   * level scheduling / colouring-- Section 4.4 (greedy colouring in natural or
                                    smallest-last order)
 """
@@ -74,6 +76,9 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_bicgstab_pc.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p, _f32p,
+                                      _f32p, _f64p, _f64p, ctypes.c_double, ctypes.c_int32, _i32p, _f64p, _f64p]
+        L.orc_bicgstab_pc.restype = ctypes.c_int
         L.orc_colours_sl.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
         L.orc_colours_sl.restype = ctypes.c_int32
         L.orc_closed_first_key.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
@@ -157,8 +162,12 @@ class SolveResult:
     res_hist: np.ndarray
 
 
-def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200) -> SolveResult:
+def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mpattern=None) -> SolveResult:
+    """Right-preconditioned BiCGStab (Section 4.2); the factors live on
+    mpattern = (rowptr, colidx) when given (block-Jacobi, Section 4.5), else
+    on the matrix's own pattern."""
     rowptr, colidx, vals, b = _i32(rowptr), _i32(colidx), _f64(vals), _f64(b)
+    mrp, mci = (rowptr, colidx) if mpattern is None else (_i32(mpattern[0]), _i32(mpattern[1]))
     x = np.empty(3 * nb)
     it = np.zeros(1, dtype=np.int32)
     rr = np.zeros(1)
@@ -167,10 +176,11 @@ def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200) ->
     d64 = fac.dinv if not fac.f32 else None
     lu32 = fac.lu if fac.f32 else None
     d32 = fac.dinv if fac.f32 else None
-    st = lib().orc_bicgstab(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
-                            _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
-                            _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
-                            _p(hist, _f64p))
+    st = lib().orc_bicgstab_pc(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+                               _p(mrp, _i32p), _p(mci, _i32p),
+                               _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
+                               _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
+                               _p(hist, _f64p))
     return SolveResult(x, int(st), int(it[0]), float(rr[0]), hist)
 
 
@@ -259,16 +269,40 @@ def to_dense(nb, rowptr, colidx, vals):
     return a
 
 
-def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False):
+def jacobi_pattern(nb, rowptr, colidx, vals, part):
+    """Block-Jacobi matrix of Section 4.5: the blocks of A that join two rows
+    of the same partition (part[i] == part[j]), same rows; its values are
+    gathered from A's by an index vector (the paper's copy-indexes loop:
+    jvals[k] = vals[indices[k]]).  Returns (rowptr, colidx, vals, indices)."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    part = np.asarray(part)
+    rows = np.repeat(np.arange(nb), np.diff(rowptr))
+    keep = part[rows] == part[colidx]
+    indices = np.flatnonzero(keep)
+    jrowptr = np.zeros(nb + 1, dtype=np.int32)
+    jrowptr[1:] = np.cumsum(np.bincount(rows[keep], minlength=nb))
+    jvals = np.asarray(vals).reshape(-1, 9)[indices]
+    return jrowptr, colidx[indices].copy(), jvals, indices
+
+
+def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False, part=None):
     """Same-ordering reference: ILU0 + BiCGStab on P A P^T with the oracle's
-    own schedule permutation; returns (x in natural order, SolveResult, perm, nsets)."""
-    perm, nsets = schedule_perm(nb, rowptr, colidx, schedule)
+    own schedule permutation; with part, the preconditioner is the
+    block-Jacobi ILU0 (Section 4.5): the schedule and the factors come from
+    the partition-internal blocks, the SpMV uses all of A.  Returns (x in
+    natural order, SolveResult, perm, nsets)."""
+    if part is None:
+        mrp, mci, mvals = rowptr, colidx, vals
+    else:
+        mrp, mci, mvals, _ = jacobi_pattern(nb, rowptr, colidx, vals, part)
+    perm, nsets = schedule_perm(nb, mrp, mci, schedule)
     prow, pcol, pval = permute(nb, rowptr, colidx, vals, perm)
+    mprow, mpcol, mpval = permute(nb, mrp, mci, mvals, perm)
     pb = np.asarray(b).reshape(nb, 3)[perm].ravel()
-    fac = ilu0(nb, prow, pcol, pval, f32=f32)
+    fac = ilu0(nb, mprow, mpcol, mpval, f32=f32)
     if fac.status != 0:
         raise ArithmeticError(f"oracle ILU0 failed with status {fac.status}")
-    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit)
+    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit, mpattern=(mprow, mpcol))
     x = np.empty(3 * nb)
     x.reshape(nb, 3)[perm] = res.x.reshape(nb, 3)
     return x, res, perm, nsets

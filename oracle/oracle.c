@@ -310,10 +310,28 @@ static double dot(size_t n, const double *a, const double *b) {
   return s;
 }
 
+/*
+ * The same iteration with a preconditioner on its own pattern (mrowptr,
+ * mcolidx): the block-Jacobi ILU0 of Section 4.5 factorises only the blocks
+ * inside a partition while the SpMV keeps the whole matrix.
+ */
+int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                    const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
+                    const float *lu32, const float *dinv32, const double *b, double *x, double rtol,
+                    int32_t maxit, int32_t *iters, double *relres, double *res_hist);
+
 int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                  const double *lu, const double *dinv, const float *lu32, const float *dinv32,
                  const double *b, double *x, double rtol, int32_t maxit, int32_t *iters,
                  double *relres, double *res_hist) {
+  return orc_bicgstab_pc(nb, rowptr, colidx, vals, rowptr, colidx, lu, dinv, lu32, dinv32, b, x, rtol, maxit,
+                         iters, relres, res_hist);
+}
+
+int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                    const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
+                    const float *lu32, const float *dinv32, const double *b, double *x, double rtol,
+                    int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
   size_t n = (size_t)BS * nb;
   double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double));
   double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
@@ -347,8 +365,8 @@ int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const
     }
     double beta = (rho / rho_prev) * (alpha / omega);
     for (size_t e = 0; e < n; ++e) p[e] = r[e] + beta * (p[e] - omega * v[e]);
-    if (lu32) orc_ilu_apply_f32(nb, rowptr, colidx, lu32, dinv32, p, ph);
-    else orc_ilu_apply(nb, rowptr, colidx, lu, dinv, p, ph);
+    if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, p, ph);
+    else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, p, ph);
     orc_spmv(nb, rowptr, colidx, vals, ph, v);
     double rhv = dot(n, rh, v);
     if (rhv == 0.0) {
@@ -364,8 +382,8 @@ int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const
       status = 0;
       break;
     }
-    if (lu32) orc_ilu_apply_f32(nb, rowptr, colidx, lu32, dinv32, s, sh);
-    else orc_ilu_apply(nb, rowptr, colidx, lu, dinv, s, sh);
+    if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, s, sh);
+    else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, s, sh);
     orc_spmv(nb, rowptr, colidx, vals, sh, t);
     double tt = dot(n, t, t);
     if (tt == 0.0) {

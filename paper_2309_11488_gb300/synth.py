@@ -97,6 +97,10 @@ class BsrSystem:
     vals: np.ndarray    # float64 [nnzb, 9]
     x_true: np.ndarray  # float64 [nb*3]
     meta: dict = field(default_factory=dict)
+    # grid systems: cell coordinates (k, j, i) of the active cells [nb, 3] and
+    # the face transmissibilities per axis (0 where a face joins an inactive
+    # cell); used only to partition the grid
+    geom: dict | None = None
 
     @property
     def nnzb(self) -> int:
@@ -158,6 +162,7 @@ def grid_system(nx, ny, nz, logk, active=None, faults=None, seed=SEED_BASE, meta
     kx = np.exp(np.asarray(logk, dtype=np.float64)).reshape(shape)
     kz = 0.1 * kx
     conn_a, conn_b, conn_t = [], [], []
+    tface = {}
     for axis, kk in ((2, kx), (1, kx), (0, kz)):
         sl_lo = [slice(None)] * 3
         sl_hi = [slice(None)] * 3
@@ -171,6 +176,10 @@ def grid_system(nx, ny, nz, logk, active=None, faults=None, seed=SEED_BASE, meta
         conn_a.append(a[ok])
         conn_b.append(b[ok])
         conn_t.append(2.0 * ka[ok] * kb[ok] / (ka[ok] + kb[ok]))
+        tf = np.where(ok, 2.0 * ka * kb / (ka + kb), 0.0)
+        fshape = list(shape)
+        fshape[axis] -= 1
+        tface[axis] = tf.reshape(fshape)
     if faults is not None:
         fa, fb, ft = faults
         conn_a.append(np.asarray(fa, dtype=np.int64))
@@ -185,7 +194,9 @@ def grid_system(nx, ny, nz, logk, active=None, faults=None, seed=SEED_BASE, meta
     md = {"grid": [nx, ny, nz], "seed": seed, "n_connections": int(ca.shape[0])}
     if meta:
         md.update(meta)
-    return BsrSystem(nb, rowptr, colidx, vals, x_true, md)
+    kk, jj, ii = np.nonzero(active)
+    geom = {"shape": shape, "kji": np.stack([kk, jj, ii], axis=1).astype(np.int32), "tface": tface}
+    return BsrSystem(nb, rowptr, colidx, vals, x_true, md, geom)
 
 
 def _lognormal_field(seed, shape, sigma):
@@ -436,3 +447,57 @@ def block_diagonal_system(nb, seed) -> BsrSystem:
         nb, e, e, np.zeros(0), stream_key(seed, _S_M), stream_key(seed, _S_ACC),
         stream_key(seed, _S_DNOISE), stream_key(seed, _S_X))
     return BsrSystem(nb, rowptr, colidx, vals, x_true, {"config": f"blockdiag nb={nb}", "seed": seed})
+
+
+def partition_grid(system: BsrSystem, nparts: int) -> np.ndarray:
+    """Partition of a grid system's cells into nparts connected boxes,
+    weighted by transmissibility (the input the block-Jacobi preconditioner
+    of the paper's Section 4.5 takes from the simulator's partitioner):
+    recursive bisection; each cut is the grid plane, among those within 5%
+    of the balanced position (by active cells), whose faces carry the least
+    total transmissibility inside the box (ties to the balanced position,
+    then the lower plane), across the box's longest side (ties: x, y, z).
+    Returns part[nb] with labels 0..nparts-1."""
+    g = system.geom
+    if g is None:
+        raise ValueError("partition_grid needs a grid system")
+    kji = g["kji"]
+    part = np.zeros(system.nb, dtype=np.int32)
+
+    def rec(lo, hi, cells, p0, npart):
+        if npart <= 1 or cells.size == 0:
+            part[cells] = p0
+            return
+        n1 = npart // 2
+        ext = [hi[a] - lo[a] for a in range(3)]
+        axis = max((2, 1, 0), key=lambda a: ext[a])  # longest side, ties to x then y then z
+        if ext[axis] < 2:
+            part[cells] = p0
+            return
+        coord = kji[cells, axis] - lo[axis]
+        layer = np.bincount(coord, minlength=ext[axis])
+        cum = np.cumsum(layer)[:-1]  # cells at or below plane c (cut after layer c)
+        target = cells.size * n1 / npart
+        dev = np.abs(cum - target)
+        cand = np.flatnonzero(dev <= max(0.05 * cells.size, dev.min()))
+        tf = g["tface"][axis]
+        other = [a for a in range(3) if a != axis]
+        costs = []
+        for c in cand:
+            sl = [slice(None)] * 3
+            sl[axis] = lo[axis] + c
+            for a in other:
+                sl[a] = slice(lo[a], hi[a])
+            costs.append(float(tf[tuple(sl)].sum()))
+        best = min(range(len(cand)), key=lambda q: (costs[q], dev[cand[q]], cand[q]))
+        cut = lo[axis] + int(cand[best])
+        low = kji[cells, axis] <= cut
+        hi1 = list(hi)
+        hi1[axis] = cut + 1
+        lo2 = list(lo)
+        lo2[axis] = cut + 1
+        rec(lo, hi1, cells[low], p0, n1)
+        rec(lo2, hi, cells[~low], p0 + n1, npart - n1)
+
+    rec([0, 0, 0], list(g["shape"]), np.arange(system.nb), 0, int(nparts))
+    return part

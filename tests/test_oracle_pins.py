@@ -520,3 +520,95 @@ def test_generator_rows_are_diagonally_dominant_up_to_noise():
     d = v[diag]
     for r in range(3):
         assert np.all(d[:, r, r] >= off_sum[:, r] + 0.1 - 0.05)
+
+
+# ------------------------------------------------------- block-Jacobi ILU0
+
+def test_jacobi_pattern_keeps_exactly_the_partition_internal_blocks():
+    """Brute force on the copy-index gather (Section 4.5): kept blocks are
+    those with part[i] == part[j], in row order, values gathered by index."""
+    s = synth.random_pattern_system(90, 4, 21)
+    part = np.arange(s.nb) % 7
+    jrp, jci, jv, idx = O.jacobi_pattern(s.nb, s.rowptr, s.colidx, s.vals, part)
+    k = 0
+    for i in range(s.nb):
+        for m in range(s.rowptr[i], s.rowptr[i + 1]):
+            j = s.colidx[m]
+            if part[i] == part[j]:
+                assert idx[k] == m and jci[k] == j
+                np.testing.assert_array_equal(jv[k], s.vals[m])
+                k += 1
+        assert jrp[i + 1] == k
+    assert k == len(idx)
+
+
+def test_jacobi_with_one_partition_is_plain_ilu0():
+    s = synth.config1()
+    b = rhs(s)
+    x0, r0, p0, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 200, "colour")
+    x1, r1, p1, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 200, "colour",
+                                   part=np.zeros(s.nb, dtype=np.int32))
+    np.testing.assert_array_equal(p0, p1)
+    assert r0.iters == r1.iters
+    np.testing.assert_array_equal(x0, x1)
+
+
+def test_jacobi_with_one_row_per_partition_is_block_diagonal_jacobi():
+    """Every row its own partition: the preconditioner is block-diagonal and
+    applies z_i = inv(A_ii) r_i (closed form)."""
+    s = synth.config1()
+    part = np.arange(s.nb, dtype=np.int32)
+    jrp, jci, jv, _ = O.jacobi_pattern(s.nb, s.rowptr, s.colidx, s.vals, part)
+    assert np.all(np.diff(jrp) == 1) and np.all(jci == np.arange(s.nb))
+    fac = O.ilu0(s.nb, jrp, jci, jv)
+    r = np.random.default_rng(3).standard_normal(3 * s.nb)
+    z = O.ilu_apply(s.nb, jrp, jci, fac, r)
+    for i in range(0, s.nb, 7):
+        blk = jv[i].reshape(3, 3)
+        np.testing.assert_allclose(z[3 * i:3 * i + 3], np.linalg.solve(blk, r[3 * i:3 * i + 3]), rtol=1e-12,
+                                   atol=1e-13)
+
+
+def test_jacobi_on_a_cut_chain_is_the_exact_block_inverse():
+    """A chain (block-tridiagonal, no fill) cut into two partitions: each
+    part's ILU0 is its exact LU, so the preconditioner is the exact inverse of
+    blockdiag(A_11, A_22), compared with dense solves of the two parts."""
+    s = synth.chain_system(40)
+    h = 17
+    part = (np.arange(s.nb) >= h).astype(np.int32)
+    jrp, jci, jv, _ = O.jacobi_pattern(s.nb, s.rowptr, s.colidx, s.vals, part)
+    fac = O.ilu0(s.nb, jrp, jci, jv)
+    assert fac.status == 0
+    r = np.random.default_rng(5).standard_normal(3 * s.nb)
+    z = O.ilu_apply(s.nb, jrp, jci, fac, r)
+    a = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    for lo, hi in ((0, h), (h, s.nb)):
+        sl = slice(3 * lo, 3 * hi)
+        np.testing.assert_allclose(z[sl], np.linalg.solve(a[sl, sl], r[sl]), rtol=1e-10, atol=1e-12)
+    # and the block coupling the parts is indeed absent from the preconditioner
+    assert not np.any((jci < h) & (np.repeat(np.arange(s.nb), np.diff(jrp)) >= h))
+
+
+def test_partition_grid_gives_balanced_boxes():
+    s = synth.config2()
+    part = synth.partition_grid(s, 16)
+    counts = np.bincount(part)
+    assert len(counts) == 16 and counts.min() > 0
+    assert counts.max() <= 2.5 * counts.min()
+    kji = s.geom["kji"]
+    for p in range(16):
+        c = kji[part == p]
+        lo, hi = c.min(axis=0), c.max(axis=0)
+        # every active cell inside the part's bounding box belongs to the part
+        inside = np.all((kji >= lo) & (kji <= hi), axis=1)
+        assert np.all(part[inside] == p)
+
+
+def test_jacobi_solve_converges_on_the_44k_cell_system():
+    s = synth.config2()
+    b = rhs(s)
+    part = synth.partition_grid(s, 16)
+    x, res, perm, nsets = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-6, 200, "level", part=part)
+    assert res.status == 0 and res.relres <= 1e-6 * (1 + 1e-6)
+    _, nlev_full = O.levels(s.nb, s.rowptr, s.colidx)
+    assert nsets < nlev_full  # the partition cuts the dependency chains (Section 4.5)
