@@ -148,6 +148,25 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
                           const double *vals, const opm_options *opt, opm_handle *out);
 
 /*
+ * Block-Jacobi ILU0 (Section 4.5): as opm_bsr_create, but the preconditioner
+ * keeps only the blocks that join two rows of the same partition; blocks
+ * between partitions stay in the matrix (SpMV, true residual) and out of
+ * the factors.  Schedule, permutation and factors follow the reduced
+ * pattern, so fewer blocks give more parallelism (fewer levels or colours)
+ * at the cost of a weaker preconditioner.  Each refactorisation copies the
+ * kept blocks from the caller's values by a precomputed index gather (the
+ * paper's copy-indexes loop), fused into the factorisation.
+ *   part: nb partition labels (any int32 values; rows with equal labels
+ *   form a partition), host or device, read during the call only; the
+ *   paper takes the partition from the simulator's transmissibility-
+ *   weighted grid partitioner.  Other arguments and returns as
+ *   opm_bsr_create; part == NULL with nb > 0 is OPM_ERR_ARG.
+ */
+opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
+                                 const double *vals, const int32_t *part, const opm_options *opt,
+                                 opm_handle *out);
+
+/*
  * ILU0 refactorisation in place (Algorithm 2) with the analysis kept
  * (Section 4.4: the pattern, hence the schedule, does not change during a
  * simulation).  vals (host or device, 9*nnzb doubles, the caller's block
@@ -219,8 +238,9 @@ opm_status opm_get_permutation(opm_handle h, int32_t *perm);
  * U's strictly-upper blocks in the pattern of P A P^T with columns
  * ascending; the diagonal-block positions of lu receive inv(U_ii), which the
  * library stores instead of U_ii.  dinv (host, 9*nb doubles, schedule order)
- * also receives inv(U_ii).  FP32 factors are widened exactly.  Either pointer
- * may be NULL.
+ * also receives inv(U_ii).  FP32 factors are widened exactly.  For a
+ * block-Jacobi handle the blocks outside the preconditioner's pattern read
+ * as zero.  Either pointer may be NULL.
  */
 opm_status opm_get_factors(opm_handle h, double *lu, double *dinv);
 

@@ -1044,8 +1044,10 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
 #pragma unroll
           for (int c = 0; c < 9; ++c) e[c] = av[c * cnt];
         }
+        if (dst >= 0) {  // blocks outside the preconditioner's pattern have no slot
 #pragma unroll
-        for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
+          for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
+        }
       }
       base += __popc(m);
     }

@@ -42,12 +42,13 @@ inline int64_t slot_pack(int64_t off, int stride) { return (off << 6) | (int64_t
 struct Analysis {
   int32_t n = 0;
   int64_t nnzb = 0, nnz_l = 0, nnz_u = 0;
+  int64_t nnzb_kept = 0;                      // blocks of the preconditioner's pattern
   int32_t schedule = 0, nsets = 0;
   std::vector<int32_t> perm, iperm;           // perm[new] = old
   std::vector<int32_t> a_rowptr, l_rowptr, u_rowptr;
   std::vector<int32_t> a_col, l_col, u_col;   // warp-sliced order
   std::vector<int32_t> a_src;                 // per A block (sliced order): caller's block index
-  std::vector<int64_t> a_dst;                 // per A block (sliced order): slot in the factor values
+  std::vector<int64_t> a_dst;                 // per A block (sliced order): slot in the factor values, -1 if none
   std::vector<int64_t> a_csr_slot;            // per A block in permuted CSR order: slot in the factor values
   std::vector<int32_t> upd_ptr;               // per L block (CSR order of L) into the update lists
   std::vector<int64_t> upd_dst, upd_src;      // slots: A_ij -= L_ik * U_kj
@@ -67,8 +68,10 @@ struct Analysis {
 
 // Validates and analyses the pattern; returns OPM_OK or a pattern error with
 // *err_row set to the offending row (caller's numbering).
-opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
-                   Analysis &an, int32_t *err_row);
+// part (may be NULL): partition label of every row; blocks joining rows of
+// different partitions stay out of the preconditioner (block-Jacobi).
+opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                   int32_t schedule, Analysis &an, int32_t *err_row);
 
 // Krylov scalars and control words, one per system, in device memory.
 struct alignas(128) DevState {

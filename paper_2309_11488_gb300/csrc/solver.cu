@@ -843,8 +843,10 @@ void opm_destroy(opm_handle h) {
   delete h;
 }
 
-opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
-                          const opm_options *opt, opm_handle *out) {
+namespace {
+
+opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                       const int32_t *part, const opm_options *opt, opm_handle *out) {
   if (!out) return OPM_ERR_ARG;
   *out = nullptr;
   t_create_err_row = -1;
@@ -881,8 +883,16 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
       return fail(OPM_ERR_CUDA);
     ci = hci.data();
   }
+  std::vector<int32_t> hpart;
+  const int32_t *pt = part;
+  if (part && nb > 0 && is_device_ptr(part)) {
+    hpart.resize((size_t)nb);
+    if (cudaMemcpy(hpart.data(), part, sizeof(int32_t) * hpart.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(OPM_ERR_CUDA);
+    pt = hpart.data();
+  }
   int32_t err_row = -1;
-  opm_status s = analyse(nb, rp, ci, o.schedule, h->an, &err_row);
+  opm_status s = analyse(nb, rp, ci, pt, o.schedule, h->an, &err_row);
   t_create_err_row = err_row;
   if (s != OPM_OK) return fail(s);
 
@@ -918,6 +928,20 @@ opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *coli
   if (s != OPM_OK) return fail(s);
   *out = h;
   return OPM_OK;
+}
+
+}  // namespace
+
+opm_status opm_bsr_create(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                          const opm_options *opt, opm_handle *out) {
+  return create_impl(nb, rowptr, colidx, vals, nullptr, opt, out);
+}
+
+opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                                 const int32_t *part, const opm_options *opt, opm_handle *out) {
+  if (out) *out = nullptr;
+  if (nb > 0 && !part) return OPM_ERR_ARG;
+  return create_impl(nb, rowptr, colidx, vals, part, opt, out);
 }
 
 opm_status opm_ilu0_factor(opm_handle h, const double *vals) {
@@ -1090,6 +1114,10 @@ opm_status opm_get_factors(opm_handle h, double *lu, double *dinv) {
   if (lu) {
     for (int64_t c = 0; c < h->nnzb; ++c) {
       const int64_t slot = an.a_csr_slot[c];
+      if (slot < 0) {  // outside the preconditioner's pattern
+        for (int e = 0; e < 9; ++e) lu[9 * c + e] = 0.0;
+        continue;
+      }
       const int64_t off = slot >> 6;
       const int st = (int)(slot & 63);
       for (int e = 0; e < 9; ++e) lu[9 * c + e] = v[off + (int64_t)e * st];

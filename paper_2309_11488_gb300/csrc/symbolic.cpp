@@ -165,8 +165,8 @@ void slice_layout(int32_t n, const std::vector<int32_t> &rp, std::vector<int64_t
 
 }  // namespace
 
-opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t schedule,
-                   Analysis &an, int32_t *err_row) {
+opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                   int32_t schedule, Analysis &an, int32_t *err_row) {
   *err_row = -1;
   if (n < 0) return OPM_ERR_ARG;
   if (rowptr[0] != 0) {
@@ -203,6 +203,29 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   if (schedule == OPM_SCHED_AUTO) schedule = OPM_SCHED_COLOUR;
   an.schedule = schedule;
 
+  // ---- the preconditioner's pattern.  With a partition (block-Jacobi ILU0,
+  // Section 4.5) only the blocks joining two rows of the same partition are
+  // factorised; the SpMV keeps every block.  Schedule, factors, phases and
+  // update lists all follow this pattern (mrp, mci; the full one otherwise).
+  std::vector<char> keep((size_t)nnzb, 1);
+  std::vector<int32_t> jrp, jci;
+  const int32_t *mrp = rowptr, *mci = colidx;
+  if (part) {
+    jrp.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+        keep[m] = part[i] == part[colidx[m]];
+        if (keep[m]) jci.push_back(colidx[m]);
+      }
+      jrp[i + 1] = (int32_t)jci.size();
+    }
+    mrp = jrp.data();
+    mci = jci.data();
+    an.nnzb_kept = (int64_t)jci.size();
+  } else {
+    an.nnzb_kept = nnzb;
+  }
+
   // ---- schedule and permutation (perm[new] = old, natural order inside a group)
   std::vector<int32_t> key;
   int32_t nkeys = 0;
@@ -213,7 +236,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   } else {
     std::vector<int64_t> gp;
     std::vector<int32_t> ga;
-    symmetrise(n, rowptr, colidx, gp, ga);
+    symmetrise(n, mrp, mci, gp, ga);
     an.nsets = schedule == OPM_SCHED_LEVEL    ? level_sets(n, gp, ga, key)
                : schedule == OPM_SCHED_COLOUR ? colour_sets(n, gp, ga, key)
                                               : colour_sets_sl(n, gp, ga, key);
@@ -226,7 +249,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     // last, so that most warps hold rows of nearly equal length.
     std::vector<int64_t> hist;
     for (int32_t i = 0; i < n; ++i) {
-      const int32_t len = rowptr[i + 1] - rowptr[i];
+      const int32_t len = mrp[i + 1] - mrp[i];
       if ((size_t)len >= hist.size()) hist.resize((size_t)len + 1, 0);
       hist[len]++;
     }
@@ -235,7 +258,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     for (int32_t i = 0; i < n; ++i) {
       bool open = false;
       for (int64_t m = gp[i]; m < gp[i + 1] && !open; ++m) open = key[ga[m]] > key[i];
-      const bool longer = rowptr[i + 1] - rowptr[i] > common;
+      const bool longer = mrp[i + 1] - mrp[i] > common;
       sub[i] = 2 * (2 * key[i] + (open ? 1 : 0)) + (longer ? 1 : 0);
     }
     key.swap(sub);
@@ -257,6 +280,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   arp.assign((size_t)n + 1, 0);
   for (int32_t ni = 0; ni < n; ++ni) arp[ni + 1] = arp[ni] + (rowptr[an.perm[ni] + 1] - rowptr[an.perm[ni]]);
   std::vector<int32_t> pcol((size_t)nnzb), psrc((size_t)nnzb);
+  std::vector<char> pk((size_t)nnzb);  // block kept in the preconditioner
   std::vector<std::pair<int32_t, int32_t>> tmp;
   an.l_rowptr.assign((size_t)n + 1, 0);
   an.u_rowptr.assign((size_t)n + 1, 0);
@@ -269,6 +293,8 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     for (size_t q = 0; q < tmp.size(); ++q) {
       pcol[arp[ni] + q] = tmp[q].first;
       psrc[arp[ni] + q] = tmp[q].second;
+      pk[arp[ni] + q] = keep[tmp[q].second];
+      if (!keep[tmp[q].second]) continue;
       nl += tmp[q].first < ni;
       nu += tmp[q].first > ni;
     }
@@ -283,7 +309,8 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     an.sl_mask.assign((size_t)(2 * ns), 0u);
     std::vector<char> read_later((size_t)n, 0);
     for (int32_t ni = 0; ni < n; ++ni)
-      for (int64_t c = arp[ni]; c < arp[ni] + (an.l_rowptr[ni + 1] - an.l_rowptr[ni]); ++c) read_later[pcol[c]] = 1;
+      for (int64_t c = arp[ni]; c < arp[ni + 1] && pcol[c] < ni; ++c)
+        if (pk[c]) read_later[pcol[c]] = 1;
     for (int32_t ni = 0; ni < n; ++ni) {
       const bool no_u = an.u_rowptr[ni + 1] == an.u_rowptr[ni];
       const uint32_t bit = 1u << (ni % kWarp);
@@ -313,7 +340,9 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     for (int64_t c = arp[ni]; c < arp[ni + 1]; ++c) {
       int32_t j = pcol[c];
       int64_t dst;
-      if (j < ni) {
+      if (!pk[c]) {
+        dst = -1;  // outside the preconditioner: no factor slot
+      } else if (j < ni) {
         an.l_col[l_pos[lc]] = j;
         dst = l_slot[lc++];
       } else if (j > ni) {
@@ -338,14 +367,14 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
     for (int32_t i = 0; i < n; ++i) {
       bool split = i >= limit;
       for (int64_t c = arp[i]; c < arp[i + 1] && !split; ++c)
-        if (pcol[c] < i && pcol[c] >= start) split = true;
+        if (pk[c] && pcol[c] < i && pcol[c] >= start) split = true;
       if (split && i > start) {
         an.phase_ptr.push_back(i);
         start = i;
         limit = INT32_MAX;
       }
       for (int64_t c = arp[i]; c < arp[i + 1]; ++c)
-        if (pcol[c] > i) limit = std::min(limit, pcol[c]);
+        if (pk[c] && pcol[c] > i) limit = std::min(limit, pcol[c]);
     }
     if (n > 0) an.phase_ptr.push_back(n);
   }
@@ -357,28 +386,32 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, int3
   an.upd_src.clear();
   for (int32_t ni = 0; ni < n; ++ni) {
     int64_t lc = an.l_rowptr[ni];
-    for (int64_t c = arp[ni]; c < arp[ni + 1] && pcol[c] < ni; ++c, ++lc) {
+    for (int64_t c = arp[ni]; c < arp[ni + 1] && pcol[c] < ni; ++c) {
+      if (!pk[c]) continue;
       int32_t k = pcol[c];
-      // row k's upper blocks, permuted CSR positions
+      // row k's kept upper blocks (permuted CSR positions; ku counts them)
       int64_t ku = an.u_rowptr[k];
       int64_t kc = arp[k];
       while (kc < arp[k + 1] && pcol[kc] <= k) ++kc;  // first upper block of row k
+      while (kc < arp[k + 1] && !pk[kc]) ++kc;
       int64_t ic = c + 1;
+      while (ic < arp[ni + 1] && !pk[ic]) ++ic;
       while (ic < arp[ni + 1] && kc < arp[k + 1]) {
         if (pcol[ic] < pcol[kc]) {
-          ++ic;
+          do ++ic; while (ic < arp[ni + 1] && !pk[ic]);
         } else if (pcol[ic] > pcol[kc]) {
-          ++kc;
+          do ++kc; while (kc < arp[k + 1] && !pk[kc]);
           ++ku;
         } else {
           an.upd_dst.push_back(an.a_csr_slot[ic]);
           an.upd_src.push_back(u_slot[ku]);
-          ++ic;
-          ++kc;
+          do ++ic; while (ic < arp[ni + 1] && !pk[ic]);
+          do ++kc; while (kc < arp[k + 1] && !pk[kc]);
           ++ku;
         }
       }
       an.upd_ptr[lc + 1] = (int32_t)an.upd_dst.size();
+      ++lc;
     }
   }
   if (an.upd_dst.size() >= ((size_t)1 << 31)) return OPM_ERR_ARG;

@@ -40,7 +40,7 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi"]
 
 
 class opm_options(ctypes.Structure):
@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
         L.opm_options_default.argtypes = [ctypes.POINTER(opm_options)]
         L.opm_options_default.restype = None
         L.opm_bsr_create.argtypes = [i32, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
+        L.opm_bsr_create_jacobi.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
+        L.opm_bsr_create_jacobi.restype = i32
         L.opm_bsr_create.restype = i32
         L.opm_ilu0_factor.argtypes = [vp, vp]
         L.opm_ilu0_factor.restype = i32
@@ -205,11 +207,16 @@ def opm_options_default(**kw) -> opm_options:
     return o
 
 
-def opm_bsr_create(nb, rowptr, colidx, vals, options: opm_options | None = None, check=True):
-    """Returns (status, Handle or None)."""
+def opm_bsr_create(nb, rowptr, colidx, vals, options: opm_options | None = None, check=True, part=None):
+    """Returns (status, Handle or None); with part, opm_bsr_create_jacobi."""
     out = ctypes.c_void_p()
-    st = lib().opm_bsr_create(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32), _ptr(vals, np.float64),
-                              ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    opt = ctypes.byref(options) if options is not None else None
+    if part is None:
+        st = lib().opm_bsr_create(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32), _ptr(vals, np.float64),
+                                  opt, ctypes.byref(out))
+    else:
+        st = lib().opm_bsr_create_jacobi(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
+                                         _ptr(vals, np.float64), _ptr(part, np.int32), opt, ctypes.byref(out))
     nnzb = int(rowptr[-1]) if nb >= 0 and len(rowptr) else 0
     h = Handle(out.value or 0, int(nb), nnzb) if out.value else None
     if check and st != OPM_OK:
@@ -404,14 +411,14 @@ class Solver:
 
     def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
                  spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto",
-                 small_phase_slices=0):
+                 small_phase_slices=0, part=None):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
                                            spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item,
                                            profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch,
                                            small_phase_slices=small_phase_slices)
-        self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options)
+        self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options, part=part)
         self.nb = nb
 
     def factor(self, vals=None) -> int:

@@ -134,3 +134,12 @@ def test_autotune_rejects_bad_arguments_on_the_host():
     assert st == opm.OPM_ERR_ARG
     st, kw, cands, best = opm.autotune_batch([], maxit=10)
     assert st == opm.OPM_ERR_ARG
+
+
+def test_jacobi_create_needs_a_partition():
+    import ctypes
+    s = synth.config1()
+    out = ctypes.c_void_p()
+    st = opm.lib().opm_bsr_create_jacobi(s.nb, s.rowptr.ctypes.data, s.colidx.ctypes.data, s.vals.ctypes.data,
+                                         None, None, ctypes.byref(out))
+    assert st == opm.OPM_ERR_ARG and not out.value
