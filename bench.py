@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--schedule", default="auto")
     p.add_argument("--grid", type=int, default=100, help="grid edge (100 = the 1M-cell workload)")
     p.add_argument("--no-autotune", action="store_true", help="batched leg: AUTO options instead of the autotuner")
+    p.add_argument("--no-jacobi", action="store_true", help="skip the block-Jacobi ILU0 leg")
+    p.add_argument("--partitions", type=int, default=150, help="block-Jacobi partitions")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
@@ -371,6 +373,8 @@ def run_ours(args, rank, world, dist):
     sv64.close()
     sv32.close()
     del vals_h, b_h, x_h
+    if not args.no_jacobi:
+        out["block_jacobi"] = measure_jacobi(args, s, barrier, max_over_ranks, world)
     if not args.no_batched:
         out["batched"] = measure_batched(args, barrier, max_over_ranks, world)
     if not args.no_serving:
@@ -378,6 +382,43 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s, n_solves=2)
     return out
+
+
+def measure_jacobi(args, s, barrier, max_over_ranks, world):
+    """Block-Jacobi ILU0 (Section 4.5) on the same system: the preconditioner
+    keeps the blocks inside each of args.partitions transmissibility-weighted
+    partitions (the paper's 150-partition configurations), the SpMV all of A;
+    refactor + solve to the same rtol, against the plain preconditioner, for
+    level scheduling and smallest-last colouring."""
+    import torch
+    from paper_2309_11488_gb300 import opm, synth
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals, xt = dev(s.rowptr), dev(s.colidx), dev(s.vals), dev(s.x_true)
+    part = synth.partition_grid(s, args.partitions)
+    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
+    dropped = int((part[rows] != part[s.colidx]).sum())
+    res = {"partitions": int(args.partitions), "blocks_dropped": dropped,
+           "blocks_dropped_frac": round(dropped / s.nnzb, 4)}
+    reps = max(3, args.steps // 20)
+    for sched in ("level", "colour_sl"):
+        for name, p in (("plain", None), ("jacobi", part)):
+            with opm.Solver(s.nb, rp, ci, vals, schedule=sched, part=p) as sv:
+                b = sv.spmv(xt)
+                x = torch.empty_like(b)
+                for _ in range(2):
+                    sv.factor(vals)
+                    _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    sv.factor(vals)
+                    _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+                torch.cuda.synchronize()
+                dt = max_over_ranks(time.perf_counter() - t0)
+                info = sv.info()
+            res[f"{sched}_{name}"] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st,
+                                      "relres": rr, "nsets": info.nsets, "nphases": info.nphases}
+    return res
 
 
 def measure_batched(args, barrier, max_over_ranks, world):
