@@ -17,6 +17,7 @@ Section references are to arXiv 2309.11488:
                                    right preconditioning, x0 = 0)
   * block-Jacobi ILU0           -- Section 4.5 (partition-internal blocks
                                    only; copy by an index vector)
+  * standard wells, separate    -- Section 4.6 (y -= C^T inv(D) B x)
   * level scheduling / colouring-- Section 4.4 (greedy colouring in natural or
                                    smallest-last order)
 """
@@ -76,6 +77,12 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_apply_wells.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_apply_wells.restype = None
+        L.orc_bicgstab_w.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p, _f32p,
+                                     _f32p, ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                     ctypes.c_double, ctypes.c_int32, _i32p, _f64p, _f64p]
+        L.orc_bicgstab_w.restype = ctypes.c_int
         L.orc_bicgstab_pc.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p, _f32p,
                                       _f32p, _f64p, _f64p, ctypes.c_double, ctypes.c_int32, _i32p, _f64p, _f64p]
         L.orc_bicgstab_pc.restype = ctypes.c_int
@@ -162,12 +169,35 @@ class SolveResult:
     res_hist: np.ndarray
 
 
-def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mpattern=None) -> SolveResult:
+def apply_wells(wells, x, y):
+    """y -= sum over wells of C^T inv(D) B x (Section 4.6, in place); wells
+    is an object with ptr, cells, B, C, Dinv (cells in the numbering of x)."""
+    y = _f64(y)
+    lib().orc_apply_wells(int(wells.ptr.shape[0] - 1), _p(_i32(wells.ptr), _i32p), _p(_i32(wells.cells), _i32p),
+                          _p(_f64(wells.B), _f64p), _p(_f64(wells.C), _f64p), _p(_f64(wells.Dinv), _f64p),
+                          _p(_f64(x), _f64p), _p(y, _f64p))
+    return y
+
+
+def spmv_wells(nb, rowptr, colidx, vals, wells, x):
+    """y = A x - sum over wells of C^T inv(D) B x."""
+    return apply_wells(wells, x, spmv(nb, rowptr, colidx, vals, x))
+
+
+def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mpattern=None,
+             wells=None) -> SolveResult:
     """Right-preconditioned BiCGStab (Section 4.2); the factors live on
     mpattern = (rowptr, colidx) when given (block-Jacobi, Section 4.5), else
-    on the matrix's own pattern."""
+    on the matrix's own pattern; with wells (Section 4.6) every product with
+    the system operator subtracts their contributions."""
     rowptr, colidx, vals, b = _i32(rowptr), _i32(colidx), _f64(vals), _f64(b)
     mrp, mci = (rowptr, colidx) if mpattern is None else (_i32(mpattern[0]), _i32(mpattern[1]))
+    if wells is None:
+        nw, wp, wc, wb, wcc, wd = 0, None, None, None, None, None
+    else:
+        nw = int(wells.ptr.shape[0] - 1)
+        wp, wc, wb, wcc, wd = (_i32(wells.ptr), _i32(wells.cells), _f64(wells.B), _f64(wells.C),
+                               _f64(wells.Dinv))
     x = np.empty(3 * nb)
     it = np.zeros(1, dtype=np.int32)
     rr = np.zeros(1)
@@ -176,11 +206,12 @@ def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mp
     d64 = fac.dinv if not fac.f32 else None
     lu32 = fac.lu if fac.f32 else None
     d32 = fac.dinv if fac.f32 else None
-    st = lib().orc_bicgstab_pc(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
-                               _p(mrp, _i32p), _p(mci, _i32p),
-                               _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
-                               _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
-                               _p(hist, _f64p))
+    st = lib().orc_bicgstab_w(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+                              _p(mrp, _i32p), _p(mci, _i32p),
+                              _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
+                              nw, _p(wp, _i32p), _p(wc, _i32p), _p(wb, _f64p), _p(wcc, _f64p), _p(wd, _f64p),
+                              _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
+                              _p(hist, _f64p))
     return SolveResult(x, int(st), int(it[0]), float(rr[0]), hist)
 
 
@@ -285,12 +316,14 @@ def jacobi_pattern(nb, rowptr, colidx, vals, part):
     return jrowptr, colidx[indices].copy(), jvals, indices
 
 
-def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False, part=None):
+def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False, part=None,
+                 wells=None):
     """Same-ordering reference: ILU0 + BiCGStab on P A P^T with the oracle's
     own schedule permutation; with part, the preconditioner is the
     block-Jacobi ILU0 (Section 4.5): the schedule and the factors come from
     the partition-internal blocks, the SpMV uses all of A.  Returns (x in
-    natural order, SolveResult, perm, nsets)."""
+    natural order, SolveResult, perm, nsets).  With wells (Section 4.6) the
+    system operator is A - sum C^T inv(D) B, preconditioned by ILU0 of A."""
     if part is None:
         mrp, mci, mvals = rowptr, colidx, vals
     else:
@@ -302,7 +335,12 @@ def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="na
     fac = ilu0(nb, mprow, mpcol, mpval, f32=f32)
     if fac.status != 0:
         raise ArithmeticError(f"oracle ILU0 failed with status {fac.status}")
-    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit, mpattern=(mprow, mpcol))
+    pw = None
+    if wells is not None:
+        iperm = np.empty(nb, dtype=np.int64)
+        iperm[perm] = np.arange(nb)
+        pw = type(wells)(**{**wells.__dict__, "cells": iperm[np.asarray(wells.cells)].astype(np.int32)})
+    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit, mpattern=(mprow, mpcol), wells=pw)
     x = np.empty(3 * nb)
     x.reshape(nb, 3)[perm] = res.x.reshape(nb, 3)
     return x, res, perm, nsets

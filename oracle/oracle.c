@@ -119,6 +119,38 @@ void orc_spmv(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const do
   }
 }
 
+/*
+ * Standard-well contributions kept separate (Section 4.6, the algorithm
+ * "adding the wellcontributions separately"): for every well, t1 = B x
+ * (B: one row of 4x3 blocks, one per perforated cell), t2 = inv(D) t1 (D a
+ * single 4x4 block, given inverted), y -= C^T t2.  Blocks row-major.
+ */
+void orc_apply_wells(int32_t nwells, const int32_t *wptr, const int32_t *wcells, const double *B,
+                     const double *C, const double *Dinv, const double *x, double *y) {
+  for (int32_t w = 0; w < nwells; ++w) {
+    double t1[4] = {0.0, 0.0, 0.0, 0.0}, t2[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int32_t p = wptr[w]; p < wptr[w + 1]; ++p)
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < BS; ++c) t1[r] += B[12 * (int64_t)p + 3 * r + c] * x[(int64_t)BS * wcells[p] + c];
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) t2[r] += Dinv[16 * (int64_t)w + 4 * r + c] * t1[c];
+    for (int32_t p = wptr[w]; p < wptr[w + 1]; ++p)
+      for (int c = 0; c < BS; ++c) {
+        double acc = 0.0;
+        for (int r = 0; r < 4; ++r) acc += C[12 * (int64_t)p + 3 * r + c] * t2[r];
+        y[(int64_t)BS * wcells[p] + c] -= acc;
+      }
+  }
+}
+
+/* y = A x - sum over wells of C^T inv(D) B x */
+void orc_spmv_wells(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                    int32_t nwells, const int32_t *wptr, const int32_t *wcells, const double *B,
+                    const double *C, const double *Dinv, const double *x, double *y) {
+  orc_spmv(nb, rowptr, colidx, vals, x, y);
+  orc_apply_wells(nwells, wptr, wcells, B, C, Dinv, x, y);
+}
+
 /* ------------------------------------------------------------------------ */
 /* ILU0 decomposition (Section 2.2, Algorithm 2), block version.            */
 /*                                                                          */
@@ -315,10 +347,19 @@ static double dot(size_t n, const double *a, const double *b) {
  * mcolidx): the block-Jacobi ILU0 of Section 4.5 factorises only the blocks
  * inside a partition while the SpMV keeps the whole matrix.
  */
+int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                   const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
+                   const float *lu32, const float *dinv32, int32_t nwells, const int32_t *wptr,
+                   const int32_t *wcells, const double *B, const double *C, const double *Dinv, const double *b,
+                   double *x, double rtol, int32_t maxit, int32_t *iters, double *relres, double *res_hist);
+
 int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                     const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
                     const float *lu32, const float *dinv32, const double *b, double *x, double rtol,
-                    int32_t maxit, int32_t *iters, double *relres, double *res_hist);
+                    int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
+  return orc_bicgstab_w(nb, rowptr, colidx, vals, mrowptr, mcolidx, lu, dinv, lu32, dinv32, 0, NULL, NULL, NULL,
+                        NULL, NULL, b, x, rtol, maxit, iters, relres, res_hist);
+}
 
 int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                  const double *lu, const double *dinv, const float *lu32, const float *dinv32,
@@ -328,10 +369,17 @@ int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const
                          iters, relres, res_hist);
 }
 
-int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
-                    const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
-                    const float *lu32, const float *dinv32, const double *b, double *x, double rtol,
-                    int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
+/*
+ * The general form: preconditioner on its own pattern (block-Jacobi,
+ * Section 4.5) and standard wells applied separately in every product with
+ * the system operator (Section 4.6; nwells = 0: none).  The preconditioner
+ * is the ILU0 of the cell matrix only.
+ */
+int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                   const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
+                   const float *lu32, const float *dinv32, int32_t nwells, const int32_t *wptr,
+                   const int32_t *wcells, const double *B, const double *C, const double *Dinv, const double *b,
+                   double *x, double rtol, int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
   size_t n = (size_t)BS * nb;
   double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double));
   double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
@@ -367,7 +415,7 @@ int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, co
     for (size_t e = 0; e < n; ++e) p[e] = r[e] + beta * (p[e] - omega * v[e]);
     if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, p, ph);
     else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, p, ph);
-    orc_spmv(nb, rowptr, colidx, vals, ph, v);
+    orc_spmv_wells(nb, rowptr, colidx, vals, nwells, wptr, wcells, B, C, Dinv, ph, v);
     double rhv = dot(n, rh, v);
     if (rhv == 0.0) {
       status = -5;
@@ -384,7 +432,7 @@ int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, co
     }
     if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, s, sh);
     else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, s, sh);
-    orc_spmv(nb, rowptr, colidx, vals, sh, t);
+    orc_spmv_wells(nb, rowptr, colidx, vals, nwells, wptr, wcells, B, C, Dinv, sh, t);
     double tt = dot(n, t, t);
     if (tt == 0.0) {
       status = -5;
@@ -413,7 +461,7 @@ done:
   } else if (n0 == 0.0) {
     *relres = 0.0;
   } else {
-    orc_spmv(nb, rowptr, colidx, vals, x, t);
+    orc_spmv_wells(nb, rowptr, colidx, vals, nwells, wptr, wcells, B, C, Dinv, x, t);
     double nres = 0.0;
     for (size_t e = 0; e < n; ++e) nres += (b[e] - t[e]) * (b[e] - t[e]);
     *relres = sqrt(nres) / n0;

@@ -50,7 +50,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 SEED_BASE = 2309114880
 
 # stream identifiers (any distinct constants)
-_S_PERM, _S_LAYER, _S_MASK, _S_FAULT, _S_M, _S_ACC, _S_DNOISE, _S_X, _S_DIMS, _S_SCALE = range(1, 11)
+_S_PERM, _S_LAYER, _S_MASK, _S_FAULT, _S_M, _S_ACC, _S_DNOISE, _S_X, _S_DIMS, _S_SCALE, _S_WELL = range(1, 12)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -501,3 +501,87 @@ def partition_grid(system: BsrSystem, nparts: int) -> np.ndarray:
 
     rec([0, 0, 0], list(g["shape"]), np.arange(system.nb), 0, int(nparts))
     return part
+
+
+@dataclass
+class Wells:
+    """Standard wells in the separate form of Section 4.6: per well a 4x4
+    block D (and its inverse, which the simulator hands over instead of D),
+    and one row of 4x3 blocks B and C with a block for every perforated cell.
+    Perforations are grouped by well: well w owns perforations
+    ptr[w]..ptr[w+1]-1, perforating cells[p] (natural numbering)."""
+
+    ptr: np.ndarray    # int32 [nwells+1]
+    cells: np.ndarray  # int32 [nperf]
+    B: np.ndarray      # float64 [nperf, 12], 4x3 row-major
+    C: np.ndarray      # float64 [nperf, 12], 4x3 row-major
+    D: np.ndarray      # float64 [nwells, 16], 4x4 row-major
+    Dinv: np.ndarray   # float64 [nwells, 16]
+
+    @property
+    def nwells(self) -> int:
+        return int(self.ptr.shape[0] - 1)
+
+
+def wells(system: BsrSystem, nwells: int, layers: int, seed=SEED_BASE + 101, scale=0.1) -> Wells:
+    """Vertical wells on a grid system: nwells distinct (i, j) columns drawn
+    uniformly; each perforates the active cells of up to `layers` consecutive
+    layers starting at a drawn depth.  Well index WI of a perforation:
+    scale x the mean face transmissibility of its cell; B and C entries
+    -WI x U(0.5, 1.5); D = (sum of the well's WI) x (U(1, 2) I + 0.05 U(-1, 1))
+    so that C^T D^-1 B stays small against the cell couplings."""
+    g = system.geom
+    if g is None:
+        raise ValueError("wells need a grid system")
+    nz, ny, nx = g["shape"]
+    kji = g["kji"]
+    cell_of = -np.ones(nz * ny * nx, dtype=np.int64)
+    cell_of[(kji[:, 0].astype(np.int64) * ny + kji[:, 1]) * nx + kji[:, 2]] = np.arange(system.nb)
+    key = stream_key(seed, _S_WELL)
+    # mean face transmissibility per cell (faces of the cell present in the grid)
+    tsum = np.zeros((nz, ny, nx))
+    tcnt = np.zeros((nz, ny, nx))
+    for axis, tf in g["tface"].items():
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[axis] = slice(0, g["shape"][axis] - 1)
+        hi[axis] = slice(1, g["shape"][axis])
+        for sl in (lo, hi):
+            tsum[tuple(sl)] += tf
+            tcnt[tuple(sl)] += tf > 0
+    tmean = np.where(tcnt > 0, tsum / np.maximum(tcnt, 1), 1.0)
+    # columns drawn until nwells distinct ones perforate at least one active cell
+    ptr, cells, wi, used = [0], [], [], set()
+    u = uniform(key, np.arange(3 * 64 * (nwells + 1), dtype=np.uint64))
+    q = 0
+    while len(ptr) - 1 < nwells and q + 2 < u.shape[0]:
+        i, j = min(int(u[q] * nx), nx - 1), min(int(u[q + 1] * ny), ny - 1)
+        top = min(int(u[q + 2] * max(nz - layers, 1)), max(nz - layers, 0))
+        q += 3
+        if (i, j) in used:
+            continue
+        perf = [(k, int(cell_of[(k * ny + j) * nx + i])) for k in range(top, min(top + layers, nz))]
+        perf = [(k, c) for (k, c) in perf if c >= 0]
+        if not perf:
+            continue
+        used.add((i, j))
+        for k, cid in perf:
+            cells.append(cid)
+            wi.append(scale * tmean[k, j, i])
+        ptr.append(len(cells))
+    ptr = np.asarray(ptr, dtype=np.int32)
+    cells = np.asarray(cells, dtype=np.int32)
+    wi = np.asarray(wi)
+    nperf = cells.shape[0]
+    ctr = np.arange(24 * nperf, dtype=np.uint64) + np.uint64(1 << 20)
+    m = uniform(key, ctr, 0.5, 1.5).reshape(nperf, 24)
+    B = -wi[:, None] * m[:, :12]
+    C = -wi[:, None] * m[:, 12:]
+    nw = ptr.shape[0] - 1
+    dd = uniform(key, np.arange(4 * nw, dtype=np.uint64) + np.uint64(1 << 24), 1.0, 2.0).reshape(nw, 4)
+    dn = 0.05 * uniform(key, np.arange(16 * nw, dtype=np.uint64) + np.uint64(1 << 26), -1.0, 1.0).reshape(nw, 4, 4)
+    wsum = np.array([wi[ptr[w]:ptr[w + 1]].sum() for w in range(nw)])
+    D = wsum[:, None, None] * (dn + dd[:, :, None] * np.eye(4)[None])
+    Dinv = np.linalg.inv(D)
+    return Wells(ptr, cells, np.ascontiguousarray(B), np.ascontiguousarray(C),
+                 np.ascontiguousarray(D.reshape(nw, 16)), np.ascontiguousarray(Dinv.reshape(nw, 16)))
