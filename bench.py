@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--grid", type=int, default=100, help="grid edge (100 = the 1M-cell workload)")
     p.add_argument("--no-autotune", action="store_true", help="batched leg: AUTO options instead of the autotuner")
     p.add_argument("--no-jacobi", action="store_true", help="skip the block-Jacobi ILU0 leg")
+    p.add_argument("--no-wells", action="store_true", help="skip the standard-wells leg")
+    p.add_argument("--wells", type=int, default=5, help="standard wells of the wells leg")
     p.add_argument("--partitions", type=int, default=150, help="block-Jacobi partitions")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -375,6 +377,8 @@ def run_ours(args, rank, world, dist):
     del vals_h, b_h, x_h
     if not args.no_jacobi:
         out["block_jacobi"] = measure_jacobi(args, s, barrier, max_over_ranks, world)
+    if not args.no_wells:
+        out["wells"] = measure_wells(args, s, out["config"]["options"], barrier, max_over_ranks, world)
     if not args.no_batched:
         out["batched"] = measure_batched(args, barrier, max_over_ranks, world)
     if not args.no_serving:
@@ -418,6 +422,41 @@ def measure_jacobi(args, s, barrier, max_over_ranks, world):
                 info = sv.info()
             res[f"{sched}_{name}"] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st,
                                       "relres": rr, "nsets": info.nsets, "nphases": info.nphases}
+    return res
+
+
+def measure_wells(args, s, options, barrier, max_over_ranks, world):
+    """Standard wells applied separately (Section 4.6): args.wells vertical
+    wells of up to 20 perforated layers on the same system; the solver's
+    operator is A - sum C^T inv(D) B, preconditioned by ILU0 of A; refactor +
+    solve at the same rtol with the headline launch options, against no
+    wells."""
+    import torch
+    from paper_2309_11488_gb300 import opm, synth
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals, xt = dev(s.rowptr), dev(s.colidx), dev(s.vals), dev(s.x_true)
+    w = synth.wells(s, args.wells, 20)
+    res = {"wells": int(w.nwells), "perforations": int(w.ptr[-1])}
+    reps = max(3, args.steps // 20)
+    for name, ww in (("without", None), ("with", w)):
+        with opm.Solver(s.nb, rp, ci, vals, **options) as sv:
+            if ww is not None:
+                sv.set_wells(ww)
+            b = sv.spmv(xt)  # b = (A - sum C^T inv(D) B) x_true
+            x = torch.empty_like(b)
+            for _ in range(2):
+                sv.factor(vals)
+                _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                sv.factor(vals)
+                _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=200)
+            torch.cuda.synchronize()
+            dt = max_over_ranks(time.perf_counter() - t0)
+            err = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+        res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
+                     "x_err_vs_x_true": err}
     return res
 
 

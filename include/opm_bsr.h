@@ -167,6 +167,26 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
                                  opm_handle *out);
 
 /*
+ * Standard wells kept separate (Section 4.6): from now on every product
+ * with the system operator (the solver's SpMVs, the true residual and
+ * opm_spmv) is y = A x - sum over wells of C_w^T inv(D_w) B_w x, while the
+ * preconditioner stays the ILU0 of A.  For a standard well D_w is a single
+ * 4x4 block and B_w, C_w one row of 4x3 blocks, one per perforated cell.
+ *   nwells >= 0 (0 removes the wells); wptr[nwells+1] (wptr[0] = 0,
+ *   non-decreasing): well w perforates cells[wptr[w] .. wptr[w+1]-1]
+ *   (caller's row numbering, each in [0, nb)); B, C: 12 doubles per
+ *   perforation (4x3 row-major, in the order of cells); Dinv: 16 doubles
+ *   per well, the inverted D (4x4 row-major), as the paper's simulator
+ *   hands it over.  Host or device pointers, copied during the call; call
+ *   again after each Newton step with the new values.  Synchronises the
+ *   handle's stream first.
+ * Returns OPM_OK, OPM_ERR_ARG (bad sizes or cells), OPM_ERR_OOM or
+ * OPM_ERR_CUDA.
+ */
+opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, const int32_t *cells,
+                         const double *B, const double *C, const double *Dinv);
+
+/*
  * ILU0 refactorisation in place (Algorithm 2) with the analysis kept
  * (Section 4.4: the pattern, hence the schedule, does not change during a
  * simulation).  vals (host or device, 9*nnzb doubles, the caller's block

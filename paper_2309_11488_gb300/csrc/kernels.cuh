@@ -47,6 +47,20 @@ struct Sys {
   const int32_t *upd_ptr;
   const int64_t *upd_dst, *upd_src;
   const uint2 *sl_mask;  // per slice: (rows without U blocks, rows whose y is read later)
+  // standard wells applied separately (nwells = 0: none)
+  int32_t nwells, pad1;
+  const int32_t *w_ptr;     // [nwells+1] perforations of each well
+  const int32_t *w_cell;    // [nperf] perforated cell (schedule order)
+  const int32_t *w_of;      // [nperf] well of each perforation
+  const double *w_B, *w_C;  // [nperf][12] 4x3 row-major
+  const double *w_Dinv;     // [nwells][16] 4x4 row-major
+  const int32_t *w_rptr;    // [n+1] perforations of each row (into w_rperf)
+  const int32_t *w_rperf;   // perforation indices by row
+  const uint32_t *w_mask;   // per slice: rows with perforations
+  double *w_t2;             // [nwells][4] inv(D) B x of the current product
+  const int32_t *w_rows;    // [nwrows] perforated rows, ascending
+  int32_t nwrows, pad2;
+  double *w_corr;           // [3n] sum of C_p^T t2 over row i's perforations (perforated rows only)
   void *lu;  // factor values (double or float): [L | U | Dinv slices]
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
@@ -348,6 +362,74 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
   }
 }
 
+// Standard wells kept separate (Section 4.6): y -= C^T inv(D) B x.  k_wells
+// runs before each product, one CTA per system: first t2_w = inv(D_w)
+// (B_w x) for every well (one warp per well, lanes over the perforations,
+// fixed butterfly order), then, for every perforated row, corr_i = the sum
+// of C_p^T t2_w over its perforations (in perforation order).  The SpMV
+// kernels start a perforated row's sum at -corr_i.
+
+// The vector a product reads: 0 p^, 1 s^, 2 x, 3 w (caller's input).
+__device__ __forceinline__ const double *operator_input(const Sys &S, int which) {
+  return which == 0 ? S.ph : which == 1 ? S.sh : which == 2 ? S.x : S.w;
+}
+
+__global__ void __launch_bounds__(256) k_wells(Batch B, int which) {
+  pdl_enter();
+  const Sys &S = B.sys[blockIdx.x];
+  const int nw = S.nwells;
+  if (nw == 0) return;
+  const double *x = operator_input(S, which);
+  const int lane = threadIdx.x & 31;
+  for (int w = threadIdx.x >> 5; w < nw; w += blockDim.x >> 5) {
+    double t1[4] = {0.0, 0.0, 0.0, 0.0};
+    const int p1 = __ldg(S.w_ptr + w + 1);
+    for (int p = __ldg(S.w_ptr + w) + lane; p < p1; p += 32) {
+      const int c = __ldg(S.w_cell + p);
+      const double *Bp = S.w_B + 12ll * p;
+      const double x0 = __ldcg(x + 3ll * c), x1 = __ldcg(x + 3ll * c + 1), x2 = __ldcg(x + 3ll * c + 2);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        t1[r] = fma(__ldg(Bp + 3 * r), x0, fma(__ldg(Bp + 3 * r + 1), x1, fma(__ldg(Bp + 3 * r + 2), x2, t1[r])));
+    }
+    warp_sum<4>(t1);
+    if (lane < 4) {
+      const double *Dw = S.w_Dinv + 16ll * w + 4 * lane;
+      S.w_t2[4ll * w + lane] =
+          fma(__ldg(Dw), t1[0], fma(__ldg(Dw + 1), t1[1], fma(__ldg(Dw + 2), t1[2], __ldg(Dw + 3) * t1[3])));
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < S.nwrows; k += blockDim.x) {
+    const int i = __ldg(S.w_rows + k);
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int q = __ldg(S.w_rptr + i); q < __ldg(S.w_rptr + i + 1); ++q) {
+      const int p = __ldg(S.w_rperf + q);
+      const double *t2 = S.w_t2 + 4ll * __ldg(S.w_of + p);
+      const double *Cp = S.w_C + 12ll * p;
+      const double a = t2[0], b = t2[1], c = t2[2], d = t2[3];
+      c0 += fma(__ldg(Cp), a, fma(__ldg(Cp + 3), b, fma(__ldg(Cp + 6), c, __ldg(Cp + 9) * d)));
+      c1 += fma(__ldg(Cp + 1), a, fma(__ldg(Cp + 4), b, fma(__ldg(Cp + 7), c, __ldg(Cp + 10) * d)));
+      c2 += fma(__ldg(Cp + 2), a, fma(__ldg(Cp + 5), b, fma(__ldg(Cp + 8), c, __ldg(Cp + 11) * d)));
+    }
+    S.w_corr[3ll * i] = c0;
+    S.w_corr[3ll * i + 1] = c1;
+    S.w_corr[3ll * i + 2] = c2;
+  }
+}
+
+// The system operator's row: y = (A x)_i minus the wells' corr_i when row i
+// is perforated (the sum starts at -corr_i).
+__device__ __forceinline__ void row_operator(const Sys &S, const double *__restrict__ x, int i, double &y0,
+                                             double &y1, double &y2) {
+  if (S.nwells > 0 && i < S.n && ((__ldg(S.w_mask + (i >> 5)) >> (i & 31)) & 1u)) {
+    y0 = -__ldcg(S.w_corr + 3ll * i);
+    y1 = -__ldcg(S.w_corr + 3ll * i + 1);
+    y2 = -__ldcg(S.w_corr + 3ll * i + 2);
+  }
+  row_spmv(S.a_rp, S.a_col, S.a_val, x, i, S.n, y0, y1, y2);
+}
+
 // ------------------------------------------------------------ tile kernels
 //
 // One CTA per (system, tile).  Streaming kernels use tiles of kTileRows =
@@ -428,7 +510,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
   const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_spmv(S.a_rp, S.a_col, S.a_val, S.ph, i, S.n, y0, y1, y2);
+    row_operator(S, S.ph, i, y0, y1, y2);
     if (i < S.n) {
       double *v = S.v + 3ll * i;
       v[0] = y0; v[1] = y1; v[2] = y2;
@@ -459,7 +541,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
   const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_spmv(S.a_rp, S.a_col, S.a_val, S.sh, i, S.n, y0, y1, y2);
+    row_operator(S, S.sh, i, y0, y1, y2);
     if (i < S.n) {
       double *t = S.t + 3ll * i;
       t[0] = y0; t[1] = y1; t[2] = y2;
@@ -563,7 +645,7 @@ __global__ void __launch_bounds__(256, 8) k_finish(Batch B) {
   const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    if (ok) row_spmv(S.a_rp, S.a_col, S.a_val, S.x, i, S.n, y0, y1, y2);
+    if (ok) row_operator(S, S.x, i, y0, y1, y2);
     if (i < S.n) {
       const int o = S.perm[i];
       if (ok) {
@@ -586,7 +668,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_plain(Batch B) {
   OPM_TILE_S(B, S, lt);
   const int i = lt * kSpmvRows + threadIdx.x;
   double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_spmv(S.a_rp, S.a_col, S.a_val, S.w, i, S.n, y0, y1, y2);
+  row_operator(S, S.w, i, y0, y1, y2);
   if (i < S.n) {
     const int o = S.perm[i];
     S.x_out[3ll * o] = y0;

@@ -38,6 +38,7 @@ struct opm_solver {
   bool fp32 = false;
   Sys sys{};                     // this system's descriptor (host copy)
   std::vector<void *> allocs;
+  std::vector<void *> well_allocs;  // arrays of the current wells (replaced by opm_set_wells)
   int64_t dev_bytes = 0;
   double *vals_stage = nullptr;  // caller's values when given from host
   double *vec_in = nullptr, *vec_out = nullptr;  // caller-order staging
@@ -64,6 +65,7 @@ struct Runner {
   bool fp32 = false, cooperative = false, profile = false;
   int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
   int small_entries = 0;  // sweep phases with at most this many slices take the latency form
+  bool has_wells = false; // some member has wells: products launch k_wells first (graphs built so)
   std::vector<int32_t> fwd_ptr, bwd_ptr;
   Batch B{};
   Sys *h_sys = nullptr;      // pinned staging of the descriptors
@@ -260,10 +262,18 @@ int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
   mark(0);
   n += launch_apply<kModeP>(R, st);
   mark(1);
+  if (R.has_wells) {
+    launch_pdl(k_wells, R.nsys, 256, st, R.B, 0);
+    ++n;
+  }
   launch_pdl(k_spmv_v, R.ntiles_s, 256, st, R.B);
   mark(2);
   n += launch_apply<kModeS>(R, st);
   mark(3);
+  if (R.has_wells) {
+    launch_pdl(k_wells, R.nsys, 256, st, R.B, 1);
+    ++n;
+  }
   launch_pdl(k_spmv_t, R.ntiles_s, 256, st, R.B);
   mark(4);
   launch_pdl(k_update, R.ntiles, 256, st, R.B);
@@ -371,7 +381,13 @@ opm_status build_graphs(Runner &R) {
         s = OPM_ERR_CUDA;
         break;
       }
-      if ((s = add_kernel_node(g, &n_finish, &n_while, 1, (void *)k_finish, R.ntiles_s, 256, argsB)) != OPM_OK)
+      cudaGraphNode_t n_pre = n_while;
+      int which_x = 2;
+      void *argsW[] = {&R.B, &which_x};
+      if (R.has_wells &&
+          (s = add_kernel_node(g, &n_pre, &n_while, 1, (void *)k_wells, R.nsys, 256, argsW)) != OPM_OK)
+        break;
+      if ((s = add_kernel_node(g, &n_finish, &n_pre, 1, (void *)k_finish, R.ntiles_s, 256, argsB)) != OPM_OK)
         break;
       void *argsR[] = {&R.B, &R.d_res};
       if ((s = add_kernel_node(g, &n_res, &n_finish, 1, (void *)k_results, results_blocks(R), 128, argsR)) !=
@@ -450,6 +466,7 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     return fail(OPM_ERR_CUDA);
   }
   R->small_entries = o.small_phase_slices > 0 ? o.small_phase_slices : o.small_phase_slices < 0 ? 0 : 10 * sms;
+  for (auto *h : mem) R->has_wells = R->has_wells || h->sys.nwells > 0;
   int maxp = 0;
   for (auto *h : mem) maxp = std::max(maxp, (int)h->an.phase_ptr.size() - 1);
   R->nphases = maxp;
@@ -554,7 +571,24 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
 }
 
 // Copy the members' descriptors (with their per-call fields) to the device.
+// Graphs for the members' current wells: the products launch k_wells only
+// when some member has wells, so a change of that rebuilds the graphs.
+opm_status runner_sync_wells(Runner &R) {
+  bool any = false;
+  for (auto *h : R.mem) any = any || h->sys.nwells > 0;
+  if (any == R.has_wells) return OPM_OK;
+  CK(cudaStreamSynchronize(R.stream));
+  if (R.solve_exec) cudaGraphExecDestroy(R.solve_exec);
+  if (R.iter_exec) cudaGraphExecDestroy(R.iter_exec);
+  if (R.factor_exec) cudaGraphExecDestroy(R.factor_exec);
+  R.solve_exec = R.iter_exec = R.factor_exec = nullptr;
+  R.has_wells = any;
+  return build_graphs(R);
+}
+
 opm_status runner_push(Runner &R) {
+  opm_status ws = runner_sync_wells(R);
+  if (ws != OPM_OK) return ws;
   for (int s = 0; s < R.nsys; ++s) R.h_sys[s] = R.mem[s]->sys;
   CK(cudaMemcpyAsync((void *)R.B.sys, R.h_sys, sizeof(Sys) * R.nsys, cudaMemcpyHostToDevice, R.stream));
   return OPM_OK;
@@ -586,7 +620,7 @@ int64_t solve_graph_launches(const Runner &R) {
   int maxit = 1;
   for (int s = 0; s < R.nsys; ++s) maxit = std::max(maxit, R.h_res[s].iters);
   const int64_t bodies = (maxit + R.chunk - 1) / R.chunk;
-  return 3 + bodies * ((int64_t)R.iter_launches * R.chunk + 1);
+  return 3 + (R.has_wells ? 1 : 0) + bodies * ((int64_t)R.iter_launches * R.chunk + 1);
 }
 
 // Host-driven solve with per-kernel events (profiling).
@@ -623,6 +657,7 @@ opm_status runner_solve_profiled(Runner &R, opm_timing &t) {
     if (!any) break;
   }
   CK(cudaEventRecord(e0, R.stream));
+  if (R.has_wells) k_wells<<<R.nsys, 256, 0, R.stream>>>(R.B, 2);
   k_finish<<<R.ntiles_s, 256, 0, R.stream>>>(R.B);
   CK(cudaEventRecord(e1, R.stream));
   k_results<<<results_blocks(R), 128, 0, R.stream>>>(R.B, R.d_res);
@@ -838,9 +873,106 @@ void opm_destroy(opm_handle h) {
   if (h->run) runner_destroy(h->run);
   if (!h->allocs.empty()) cudaStreamSynchronize(h->stream);
   for (void *p : h->allocs) cudaFree(p);
+  if (!h->well_allocs.empty()) cudaStreamSynchronize(h->stream);
+  for (void *p : h->well_allocs) cudaFree(p);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   delete h;
+}
+
+opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, const int32_t *cells, const double *B,
+                         const double *C, const double *Dinv) {
+  if (!h || nwells < 0 || h->async_pending) return OPM_ERR_ARG;
+  if (nwells > 0 && (!wptr || !cells || !B || !C || !Dinv)) return OPM_ERR_ARG;
+  // ---- host copies of the structure (host or device pointers) and checks
+  std::vector<int32_t> hp, hc;
+  if (nwells > 0) {
+    hp.resize((size_t)nwells + 1);
+    CK(cudaMemcpy(hp.data(), wptr, sizeof(int32_t) * hp.size(), cudaMemcpyDefault));
+    if (hp[0] != 0) return OPM_ERR_ARG;
+    for (int32_t w = 0; w < nwells; ++w)
+      if (hp[w + 1] < hp[w]) return OPM_ERR_ARG;
+    hc.resize((size_t)hp[nwells]);
+    if (!hc.empty()) CK(cudaMemcpy(hc.data(), cells, sizeof(int32_t) * hc.size(), cudaMemcpyDefault));
+    for (int32_t c : hc)
+      if (c < 0 || c >= h->n) return OPM_ERR_ARG;
+  }
+  // ---- drop the previous wells (no kernel of this handle is in flight after the sync)
+  CK(cudaStreamSynchronize(h->stream));
+  for (void *p : h->well_allocs) cudaFree(p);
+  h->well_allocs.clear();
+  Sys &S = h->sys;
+  S.nwells = 0;
+  S.w_ptr = S.w_cell = S.w_of = S.w_rptr = S.w_rperf = nullptr;
+  S.w_B = S.w_C = S.w_Dinv = nullptr;
+  S.w_mask = nullptr;
+  S.w_t2 = S.w_corr = nullptr;
+  S.w_rows = nullptr;
+  S.nwrows = 0;
+  if (nwells == 0 || h->n == 0) return OPM_OK;
+  // ---- schedule-order cells, well of each perforation, perforations by row
+  const int32_t nperf = hp[nwells];
+  const Analysis &an = h->an;
+  std::vector<int32_t> pcell((size_t)nperf), wof((size_t)nperf), rptr((size_t)h->n + 1, 0), rperf((size_t)nperf);
+  std::vector<uint32_t> mask((size_t)h->nslices, 0u);
+  for (int32_t w = 0; w < nwells; ++w)
+    for (int32_t p = hp[w]; p < hp[w + 1]; ++p) {
+      pcell[p] = an.iperm[hc[p]];
+      wof[p] = w;
+      rptr[pcell[p] + 1]++;
+      mask[pcell[p] / kWarp] |= 1u << (pcell[p] % kWarp);
+    }
+  for (int32_t i = 0; i < h->n; ++i) rptr[i + 1] += rptr[i];
+  {
+    std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
+    for (int32_t p = 0; p < nperf; ++p) rperf[fill[pcell[p]]++] = p;
+  }
+  int64_t bytes = 0;
+  int32_t *d_ptr, *d_cell, *d_of, *d_rptr, *d_rperf;
+  uint32_t *d_mask;
+  double *d_B, *d_C, *d_D;
+  opm_status s;
+#define UPW(ptr, vec) \
+  if ((s = upload(h->well_allocs, bytes, h->stream, &ptr, vec)) != OPM_OK) return s
+  UPW(d_ptr, hp);
+  UPW(d_cell, pcell);
+  UPW(d_of, wof);
+  UPW(d_rptr, rptr);
+  UPW(d_rperf, rperf);
+  UPW(d_mask, mask);
+#undef UPW
+  if ((s = dalloc(h->well_allocs, bytes, &d_B, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, &d_C, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, &d_D, 16 * (size_t)nwells)) != OPM_OK) return s;
+  double *d_t2, *d_corr;
+  if ((s = dalloc(h->well_allocs, bytes, &d_t2, 4 * (size_t)nwells)) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, &d_corr, 3 * (size_t)h->n)) != OPM_OK) return s;
+  std::vector<int32_t> wrows;
+  for (int32_t i = 0; i < h->n; ++i)
+    if (rptr[i + 1] > rptr[i]) wrows.push_back(i);
+  int32_t *d_wrows;
+  if ((s = upload(h->well_allocs, bytes, h->stream, &d_wrows, wrows)) != OPM_OK) return s;
+  if (nperf > 0) {
+    CK(cudaMemcpyAsync(d_B, B, sizeof(double) * 12 * (size_t)nperf, cudaMemcpyDefault, h->stream));
+    CK(cudaMemcpyAsync(d_C, C, sizeof(double) * 12 * (size_t)nperf, cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaMemcpyAsync(d_D, Dinv, sizeof(double) * 16 * (size_t)nwells, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  S.w_ptr = d_ptr;
+  S.w_cell = d_cell;
+  S.w_of = d_of;
+  S.w_rptr = d_rptr;
+  S.w_rperf = d_rperf;
+  S.w_mask = d_mask;
+  S.w_B = d_B;
+  S.w_C = d_C;
+  S.w_Dinv = d_D;
+  S.w_t2 = d_t2;
+  S.w_corr = d_corr;
+  S.w_rows = d_wrows;
+  S.nwrows = (int32_t)wrows.size();
+  S.nwells = nwells;
+  return OPM_OK;
 }
 
 namespace {
@@ -1038,6 +1170,7 @@ opm_status opm_spmv(opm_handle h, const double *x, double *y) {
   Runner &R = *h->run;
   if ((s = runner_push(R)) != OPM_OK) return s;
   k_gather<<<R.ntiles, 256, 0, h->stream>>>(R.B);
+  if (R.has_wells) k_wells<<<R.nsys, 256, 0, h->stream>>>(R.B, 3);
   k_spmv_plain<<<R.ntiles_s, 256, 0, h->stream>>>(R.B);
   CK(cudaGetLastError());
   h->timing.launches += 2;

@@ -40,7 +40,7 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells"]
 
 
 class opm_options(ctypes.Structure):
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.opm_bsr_create.argtypes = [i32, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
         L.opm_bsr_create_jacobi.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
         L.opm_bsr_create_jacobi.restype = i32
+        L.opm_set_wells.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.opm_set_wells.restype = i32
         L.opm_bsr_create.restype = i32
         L.opm_ilu0_factor.argtypes = [vp, vp]
         L.opm_ilu0_factor.restype = i32
@@ -423,6 +425,16 @@ class Solver:
 
     def factor(self, vals=None) -> int:
         return opm_ilu0_factor(self.h, vals)
+
+    def set_wells(self, wells=None) -> int:
+        """opm_set_wells from an object with ptr, cells, B, C, Dinv (numpy or
+        torch); None removes the wells."""
+        if wells is None:
+            return lib().opm_set_wells(self.h.ptr, 0, None, None, None, None, None)
+        nw = int(wells.ptr.shape[0] - 1)
+        return lib().opm_set_wells(self.h.ptr, nw, _ptr(wells.ptr, np.int32), _ptr(wells.cells, np.int32),
+                                   _ptr(wells.B, np.float64), _ptr(wells.C, np.float64),
+                                   _ptr(wells.Dinv, np.float64))
 
     def solve(self, b, x=None, rtol=1e-2, maxit=200):
         if x is None:

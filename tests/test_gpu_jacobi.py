@@ -2,9 +2,10 @@
 preconditioner keeps only the partition-internal blocks; schedule,
 permutation and factors follow that pattern, the SpMV the whole matrix.
 Tolerances as in the plain parity tests (factors 1e-12, FP64 solves 1e-8 on
-x); FP32-factor solves 1e-5 on x: both sides factorise and sweep in FP32
-(unit roundoff 6e-8) but round in different orders (FMA, sums), which
-perturbs every preconditioner application at ~1e-6 relative."""
+x).  FP32-factor solves are compared at rtol 1e-10 at 1e-7 on x: both sides
+factorise and sweep in FP32 but round in different orders (FMA, sums), so
+at loose rtol their Krylov paths part; at a tight rtol both are pinned to
+the system's solution."""
 import numpy as np
 import pytest
 
@@ -97,13 +98,17 @@ def check_jacobi_solve(s, part, schedule, rtol, precision="fp64", maxit=200):
         xd, st, it, relres = sv.solve(dev(b), rtol=rtol, maxit=maxit)
         x = xd.cpu().numpy()
     assert st == res.status == 0
-    if it != res.iters:
+    if precision == "fp32":
+        # different FP32 rounding paths: converged to the same solution
+        assert abs(it - res.iters) <= 2
+        assert np.linalg.norm(x - x_ref) <= 1e-7 * np.linalg.norm(x_ref)
+    elif it != res.iters:
         assert abs(it - res.iters) == 1
         h = res.res_hist / res.res_hist[0]
         k = min(it, res.iters)
         assert any(abs(v / rtol - 1) < 1e-6 for v in (h[2 * k - 1], h[2 * k]) if np.isfinite(v))
     else:
-        assert np.linalg.norm(x - x_ref) <= (1e-8 if precision == "fp64" else 1e-5) * np.linalg.norm(x_ref)
+        assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
     assert relres <= rtol * (1 + 1e-6)
     return it, res.iters
 
@@ -115,10 +120,10 @@ def test_jacobi_solve_small(name, schedule):
     check_jacobi_solve(s, part, schedule, 1e-8)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_jacobi_solve_config2(precision):
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32", 1e-10)])
+def test_jacobi_solve_config2(precision, rtol):
     s = synth.config2()
-    check_jacobi_solve(s, synth.partition_grid(s, 16), "level", 1e-6, precision)
+    check_jacobi_solve(s, synth.partition_grid(s, 16), "level", rtol, precision)
 
 
 @pytest.mark.parametrize("schedule", ["level", "colour_sl"])
