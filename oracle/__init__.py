@@ -18,6 +18,9 @@ Section references are to arXiv 2309.11488:
   * block-Jacobi ILU0           -- Section 4.5 (partition-internal blocks
                                    only; copy by an index vector)
   * standard wells, separate    -- Section 4.6 (y -= C^T inv(D) B x)
+  * restarted GMRES             -- Section 2 names it as OPM's other solver
+                                   (method: Saad & Schultz 1986, right
+                                   preconditioning, CGS2 Arnoldi)
   * level scheduling / colouring-- Section 4.4 (greedy colouring in natural or
                                    smallest-last order)
 """
@@ -77,6 +80,9 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
+                                ctypes.c_int32, ctypes.c_int32, _i32p, _f64p, _f64p]
+        L.orc_gmres.restype = ctypes.c_int
         L.orc_apply_wells.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.orc_apply_wells.restype = None
         L.orc_bicgstab_w.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p, _f32p,
@@ -298,6 +304,35 @@ def to_dense(nb, rowptr, colidx, vals):
             j = colidx[m]
             a[3 * i:3 * i + 3, 3 * j:3 * j + 3] = vals[m]
     return a
+
+
+def gmres(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, restart=30) -> SolveResult:
+    """Restarted GMRES(m), right-preconditioned by the ILU0 factors (see
+    orc_gmres: CGS2 Arnoldi, Givens rotations, restart from the true
+    residual); res_hist holds ||r_0|| and the estimate after each step."""
+    rowptr, colidx, vals, b = _i32(rowptr), _i32(colidx), _f64(vals), _f64(b)
+    x = np.empty(3 * nb)
+    it = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1)
+    hist = np.full(maxit + 1, np.nan)
+    st = lib().orc_gmres(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p), _p(fac.lu, _f64p),
+                         _p(fac.dinv, _f64p), _p(b, _f64p), _p(x, _f64p), rtol, maxit, restart, _p(it, _i32p),
+                         _p(rr, _f64p), _p(hist, _f64p))
+    return SolveResult(x, int(st), int(it[0]), float(rr[0]), hist)
+
+
+def solve_system_gmres(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, restart=30, schedule="natural"):
+    """Same-ordering reference for GMRES: ILU0 of P A P^T, GMRES on P A P^T;
+    returns (x in natural order, SolveResult, perm)."""
+    perm, _ = schedule_perm(nb, rowptr, colidx, schedule)
+    prow, pcol, pval = permute(nb, rowptr, colidx, vals, perm)
+    fac = ilu0(nb, prow, pcol, pval)
+    if fac.status != 0:
+        raise ArithmeticError(f"oracle ILU0 failed with status {fac.status}")
+    res = gmres(nb, prow, pcol, pval, fac, np.asarray(b).reshape(nb, 3)[perm].ravel(), rtol, maxit, restart)
+    x = np.empty(3 * nb)
+    x.reshape(nb, 3)[perm] = res.x.reshape(nb, 3)
+    return x, res, perm
 
 
 def jacobi_pattern(nb, rowptr, colidx, vals, part):

@@ -470,6 +470,140 @@ done:
   return status;
 }
 
+/*
+ * Restarted GMRES(m) (Saad & Schultz 1986), OPM's other Krylov solver
+ * (Section 2), right-preconditioned by the ILU0 factors, x0 = 0.  Arnoldi
+ * with classical Gram-Schmidt applied twice (each pass: all projections
+ * h = V^T w first, then w -= V h); Givens rotations keep the least-squares
+ * problem triangular; the estimate |g_{j+1}| of ||r|| is tested after every
+ * step against rtol ||r_0|| (the rule of Section 4.2).  At the end of a
+ * cycle (m steps, convergence, maxit or an exact breakdown) x += inv(M) V y
+ * with H y = g; a new cycle starts from the true residual b - A x.  iters
+ * counts Arnoldi steps over all cycles.  Returns 0 (converged),
+ * 1 (maxit reached), -6 (non-finite b).  res_hist (optional, maxit + 1
+ * entries): ||r_0||, then the estimate after each step.
+ */
+int orc_gmres(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals, const double *lu,
+              const double *dinv, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
+              int32_t *iters, double *relres, double *res_hist) {
+  const size_t n = (size_t)BS * nb;
+  const int m = restart > 0 ? restart : 30;
+  double *V = calloc((size_t)(m + 1) * n, sizeof(double));
+  double *w = calloc(n, sizeof(double)), *z = calloc(n, sizeof(double)), *r = calloc(n, sizeof(double));
+  double *H = calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i * m + j] */
+  double *cs = calloc((size_t)m, sizeof(double)), *sn = calloc((size_t)m, sizeof(double));
+  double *g = calloc((size_t)m + 1, sizeof(double)), *y = calloc((size_t)m, sizeof(double));
+  double *h1 = calloc((size_t)m + 1, sizeof(double)), *h2 = calloc((size_t)m + 1, sizeof(double));
+  int status = 1;
+  *iters = 0;
+  for (size_t e = 0; e < n; ++e) {
+    x[e] = 0.0;
+    r[e] = b[e];
+  }
+  const double n0 = sqrt(dot(n, r, r));
+  double beta = n0;
+  if (res_hist) res_hist[0] = n0;
+  if (!isfinite(n0)) {
+    status = -6;
+    goto done;
+  }
+  if (n0 == 0.0) {
+    status = 0;
+    goto done;
+  }
+  const double tol = rtol * n0;
+  int32_t k = 0;
+  for (;;) {
+    for (size_t e = 0; e < n; ++e) V[e] = r[e] / beta;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int j = 0, conv = 0;
+    for (; j < m && k < maxit; ++j) {
+      ++k;
+      orc_ilu_apply(nb, rowptr, colidx, lu, dinv, V + (size_t)j * n, z);
+      orc_spmv(nb, rowptr, colidx, vals, z, w);
+      for (int i = 0; i <= j; ++i) h1[i] = dot(n, V + (size_t)i * n, w);
+      for (size_t e = 0; e < n; ++e) {
+        double acc = 0.0;
+        for (int i = 0; i <= j; ++i) acc += h1[i] * V[(size_t)i * n + e];
+        w[e] -= acc;
+      }
+      for (int i = 0; i <= j; ++i) h2[i] = dot(n, V + (size_t)i * n, w);
+      for (size_t e = 0; e < n; ++e) {
+        double acc = 0.0;
+        for (int i = 0; i <= j; ++i) acc += h2[i] * V[(size_t)i * n + e];
+        w[e] -= acc;
+      }
+      for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
+      const double hn = sqrt(dot(n, w, w));
+      H[(j + 1) * m + j] = hn;
+      if (hn != 0.0)
+        for (size_t e = 0; e < n; ++e) V[(size_t)(j + 1) * n + e] = w[e] / hn;
+      for (int i = 0; i < j; ++i) { /* earlier rotations on column j */
+        const double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[j * m + j], c = H[(j + 1) * m + j];
+      const double den = sqrt(a * a + c * c);
+      cs[j] = a / den;
+      sn[j] = c / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      if (res_hist) res_hist[k] = fabs(g[j + 1]);
+      if (fabs(g[j + 1]) <= tol || hn == 0.0) {
+        conv = 1;
+        ++j;
+        break;
+      }
+    }
+    /* x += inv(M) V y, H y = g (back substitution over the j steps done) */
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < j; ++l) acc -= H[i * m + l] * y[l];
+      y[i] = acc / H[i * m + i];
+    }
+    for (size_t e = 0; e < n; ++e) {
+      double acc = 0.0;
+      for (int i = 0; i < j; ++i) acc += y[i] * V[(size_t)i * n + e];
+      w[e] = acc;
+    }
+    orc_ilu_apply(nb, rowptr, colidx, lu, dinv, w, z);
+    for (size_t e = 0; e < n; ++e) x[e] += z[e];
+    if (conv) {
+      status = 0;
+      break;
+    }
+    if (k >= maxit) {
+      status = 1;
+      break;
+    }
+    orc_spmv(nb, rowptr, colidx, vals, x, w);
+    for (size_t e = 0; e < n; ++e) r[e] = b[e] - w[e];
+    beta = sqrt(dot(n, r, r));
+    if (beta <= tol) {
+      status = 0;
+      break;
+    }
+  }
+  *iters = k;
+done:
+  if (status == -6) {
+    *relres = NAN;
+  } else if (n0 == 0.0) {
+    *relres = 0.0;
+  } else {
+    orc_spmv(nb, rowptr, colidx, vals, x, w);
+    double nres = 0.0;
+    for (size_t e = 0; e < n; ++e) nres += (b[e] - w[e]) * (b[e] - w[e]);
+    *relres = sqrt(nres) / n0;
+  }
+  free(V); free(w); free(z); free(r); free(H); free(cs); free(sn); free(g); free(y); free(h1); free(h2);
+  return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense Gaussian elimination with partial pivoting, A x = b in place      */
 /* (brute-force reference for tiny systems).  a is n x n row-major.         */

@@ -676,3 +676,50 @@ def test_solve_with_wells_recovers_x_true():
     r = b - O.spmv_wells(s.nb, s.rowptr, s.colidx, s.vals, w, x)
     assert abs(np.linalg.norm(r) / np.linalg.norm(b) - res.relres) <= 1e-3 * res.relres
     assert np.linalg.norm(x - s.x_true) <= 1e-6 * np.linalg.norm(s.x_true)
+
+
+# ------------------------------------------------------------ restarted GMRES
+
+def test_gmres_minimises_the_residual_over_the_krylov_space():
+    """After j steps (no restart) GMRES's estimate equals
+    min over c of ||b - A inv(M) K_j c||, computed by brute force from the
+    explicit Krylov basis K_j = [b, (A inv(M)) b, ...] and a dense
+    least-squares solve."""
+    s = synth.random_pattern_system(20, 3, 31)
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = np.random.default_rng(4).standard_normal(3 * s.nb)
+    a = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    minv = np.column_stack([O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, e) for e in np.eye(3 * s.nb)])
+    op = a @ minv
+    for j in (1, 3, 6):
+        res = O.gmres(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-300, maxit=j, restart=50)
+        assert res.status == 1 and res.iters == j
+        K = np.column_stack([np.linalg.matrix_power(op, q) @ b for q in range(j)])
+        c, *_ = np.linalg.lstsq(op @ K, b, rcond=None)
+        best = np.linalg.norm(b - op @ K @ c)
+        np.testing.assert_allclose(res.res_hist[j], best, rtol=1e-8)
+        # and the returned x attains it: x = inv(M) K c (the true residual of x)
+        np.testing.assert_allclose(res.relres * np.linalg.norm(b), best, rtol=1e-8)
+
+
+def test_gmres_with_an_exact_preconditioner_takes_one_step():
+    """No-fill pattern: ILU0 is the exact LU, A inv(M) = I, one step."""
+    s = synth.chain_system(60)
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    res = O.gmres(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-10, maxit=50, restart=30)
+    assert res.status == 0 and res.iters == 1
+    np.testing.assert_allclose(res.x, s.x_true, rtol=0, atol=1e-12 * np.abs(s.x_true).max())
+
+
+def test_gmres_restart_longer_than_the_solve_changes_nothing():
+    s = synth.config1()
+    b = rhs(s)
+    x1, r1, _ = O.solve_system_gmres(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 200, 60, "colour")
+    x2, r2, _ = O.solve_system_gmres(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 200, 100, "colour")
+    assert r1.iters == r2.iters < 60
+    np.testing.assert_array_equal(x1, x2)
+    # a short restart still converges, the estimate tracking the true residual at the end
+    x3, r3, _ = O.solve_system_gmres(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 300, 5, "colour")
+    assert r3.status == 0 and r3.relres <= 1e-8 * (1 + 1e-6) and r3.iters > r1.iters
+    assert np.linalg.norm(x3 - s.x_true) <= 1e-6 * np.linalg.norm(s.x_true)
