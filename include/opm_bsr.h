@@ -167,6 +167,26 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
                                  opm_handle *out);
 
 /*
+ * Restarted GMRES(m) (Section 2 names restarted GMRES as OPM's other Krylov
+ * solver; method of Saad & Schultz 1986), with the handle's ILU0 (or
+ * block-Jacobi ILU0) as right preconditioner, x0 = 0.  Arnoldi with
+ * classical Gram-Schmidt applied twice; Givens rotations; the residual
+ * estimate is tested after every step against rtol ||b|| (the stopping rule
+ * of Section 4.2); each cycle of `restart` steps (0 = 30, at most 64) ends
+ * with x += inv(M) V y and the next starts from the true residual.
+ *   b, x as for opm_bicgstab_solve; maxit bounds the Arnoldi steps over all
+ *   cycles; *iters = steps taken; *relres = true ||b - A x|| / ||b|| (with
+ *   the wells' terms when wells are set).  Synchronous on the handle's
+ *   stream; uses (m + 1) extra vectors of device memory, kept for later
+ *   calls.  Not available on batches.
+ * Returns OPM_OK, OPM_NOT_CONVERGED, OPM_ERR_ARG, OPM_ERR_ZERO_PIVOT (no
+ * valid factors), OPM_ERR_BREAKDOWN (a zero rotation), OPM_ERR_NONFINITE,
+ * OPM_ERR_OOM or OPM_ERR_CUDA; on negative codes x is zero-filled.
+ */
+opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol, int32_t maxit,
+                           int32_t restart, int32_t *iters, double *relres);
+
+/*
  * Standard wells kept separate (Section 4.6): from now on every product
  * with the system operator (the solver's SpMVs, the true residual and
  * opm_spmv) is y = A x - sum over wells of C_w^T inv(D_w) B_w x, while the

@@ -369,9 +369,9 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
 // of C_p^T t2_w over its perforations (in perforation order).  The SpMV
 // kernels start a perforated row's sum at -corr_i.
 
-// The vector a product reads: 0 p^, 1 s^, 2 x, 3 w (caller's input).
+// The vector a product reads: 0 p^, 1 s^, 2 x, 3 w (caller's input), 4 t.
 __device__ __forceinline__ const double *operator_input(const Sys &S, int which) {
-  return which == 0 ? S.ph : which == 1 ? S.sh : which == 2 ? S.x : S.w;
+  return which == 0 ? S.ph : which == 1 ? S.sh : which == 2 ? S.x : which == 3 ? S.w : S.t;
 }
 
 __global__ void __launch_bounds__(256) k_wells(Batch B, int which) {

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "gmres.cuh"
 
 using namespace opm;
 
@@ -39,6 +40,11 @@ struct opm_solver {
   Sys sys{};                     // this system's descriptor (host copy)
   std::vector<void *> allocs;
   std::vector<void *> well_allocs;  // arrays of the current wells (replaced by opm_set_wells)
+  double *gm_V = nullptr;           // GMRES: Krylov basis, gm_m + 1 vectors
+  double *gm_part = nullptr;        // GMRES: per-tile partial sums
+  double *gm_sc = nullptr;          // GMRES: device scalars (projections, norm, y)
+  double *gm_host = nullptr;        // GMRES: pinned host mirror of gm_sc
+  int gm_m = 0;
   int64_t dev_bytes = 0;
   double *vals_stage = nullptr;  // caller's values when given from host
   double *vec_in = nullptr, *vec_out = nullptr;  // caller-order staging
@@ -875,9 +881,200 @@ void opm_destroy(opm_handle h) {
   for (void *p : h->allocs) cudaFree(p);
   if (!h->well_allocs.empty()) cudaStreamSynchronize(h->stream);
   for (void *p : h->well_allocs) cudaFree(p);
+  if (h->gm_V) cudaFree(h->gm_V);
+  if (h->gm_part) cudaFree(h->gm_part);
+  if (h->gm_sc) cudaFree(h->gm_sc);
+  if (h->gm_host) cudaFreeHost(h->gm_host);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   delete h;
+}
+
+// Restarted GMRES(m), the steps of the oracle's orc_gmres in the same order:
+// vector work in the kernels of gmres.cuh and the sweeps/SpMV of the
+// BiCGStab path, the Hessenberg column, Givens rotations and the small
+// triangular solve on the host (FP64), one host read per Arnoldi step.
+opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
+                           int32_t *iters, double *relres) {
+  if (!h || (h->n > 0 && (!b || !x)) || !(rtol >= 0.0) || maxit < 0 || restart < 0 || restart > kGmMaxVec - 1 ||
+      h->async_pending)
+    return OPM_ERR_ARG;
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (h->n == 0) return OPM_OK;
+  if (!h->factors_ok) return OPM_ERR_ZERO_PIVOT;
+  const int m = restart > 0 ? restart : 30;
+  bool x_dev = false;
+  opm_status s = prepare_solve(h, b, x, rtol, maxit, &x_dev);
+  if (s != OPM_OK) return s;
+  Runner &R = *h->run;
+  cudaStream_t st = h->stream;
+  const int64_t n3 = 3ll * h->n;
+  const size_t vbytes = sizeof(double) * (size_t)n3;
+  const int ntile = h->sys.ntiles_s;
+  // ---- buffers (kept for later calls; the basis grows with m)
+  if (h->gm_m < m) {
+    if (h->gm_V) cudaFree(h->gm_V);
+    h->gm_V = nullptr;
+    h->gm_m = 0;
+    if (cudaMalloc(&h->gm_V, vbytes * (size_t)(m + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      h->gm_V = nullptr;
+      return OPM_ERR_OOM;
+    }
+    h->gm_m = m;
+  }
+  if (!h->gm_part) {
+    if (cudaMalloc(&h->gm_part, sizeof(double) * (size_t)ntile * kGmMaxVec) != cudaSuccess ||
+        cudaMalloc(&h->gm_sc, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess ||
+        cudaMallocHost(&h->gm_host, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess) {
+      cudaGetLastError();
+      return OPM_ERR_OOM;
+    }
+  }
+  if ((s = runner_push(R)) != OPM_OK) return s;
+  const Sys &S = h->sys;
+  double *V = h->gm_V, *d_h1 = h->gm_sc, *d_h2 = h->gm_sc + kGmMaxVec, *d_nrm = h->gm_sc + 2 * kGmMaxVec,
+         *d_y = h->gm_sc + 3 * kGmMaxVec;
+  double *hh = h->gm_host;
+  const int egrid = (int)std::min<int64_t>((n3 + 255) / 256, 152 * 8);
+  auto dots = [&](const double *Vb, int nv, const double *w, double *out) {
+    k_gm_dots<<<ntile, 256, 0, st>>>(n3, Vb, n3, nv, w, h->gm_part);
+    k_gm_reduce<<<nv, 256, 0, st>>>(h->gm_part, ntile, out);
+  };
+  auto apply = [&](const double *in) {  // S.t = inv(M) in
+    CK(cudaMemcpyAsync(S.w, in, vbytes, cudaMemcpyDeviceToDevice, st));
+    launch_apply<kModePlain>(R, st);
+    return OPM_OK;
+  };
+  auto op = [&](int which, const double *in, double *out) {  // out = A in - wells
+    if (R.has_wells) k_wells<<<1, 256, 0, st>>>(R.B, which);
+    k_gm_operator<<<ntile, 256, 0, st>>>(R.B, in, out);
+  };
+  auto read = [&](int count) {
+    CK(cudaMemcpyAsync(hh, h->gm_sc, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return OPM_OK;
+  };
+  // ---- r = b (schedule order, kept in S.p), x = 0, n0 = ||r||
+  k_gather<<<R.ntiles, 256, 0, st>>>(R.B);
+  CK(cudaMemcpyAsync(S.p, S.w, vbytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(S.r, S.w, vbytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(S.x, 0, vbytes, st));
+  dots(S.r, 1, S.r, d_h1);
+  if ((s = read(1)) != OPM_OK) return s;
+  const double n0 = std::sqrt(hh[0]);
+  opm_status status = OPM_NOT_CONVERGED;
+  int32_t k = 0;
+  if (!std::isfinite(n0)) {
+    status = OPM_ERR_NONFINITE;
+  } else if (n0 == 0.0) {
+    status = OPM_OK;
+  } else {
+    const double tol = rtol * n0;
+    double beta = n0;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+    for (bool done = false; !done;) {
+      k_gm_scale<<<egrid, 256, 0, st>>>(n3, S.r, nullptr, beta, V);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int j = 0;
+      bool conv = false;
+      for (; j < m && k < maxit; ++j) {
+        ++k;
+        double *vj = V + (size_t)j * n3, *w = S.v;
+        apply(vj);
+        op(4, S.t, w);
+        dots(V, j + 1, w, d_h1);
+        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j + 1, d_h1, w, 0);
+        dots(V, j + 1, w, d_h2);
+        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j + 1, d_h2, w, 0);
+        dots(w, 1, w, d_nrm);
+        k_gm_scale<<<egrid, 256, 0, st>>>(n3, w, d_nrm, 0.0, V + (size_t)(j + 1) * n3);
+        if ((s = read(2 * kGmMaxVec + 1)) != OPM_OK) return s;
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[kGmMaxVec + i];
+        const double hn = std::sqrt(hh[2 * kGmMaxVec]);
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+        }
+        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        const double den = std::sqrt(a * a + c * c);
+        if (den == 0.0) {
+          status = OPM_ERR_BREAKDOWN;
+          done = true;
+          break;
+        }
+        cs[j] = a / den;
+        sn[j] = c / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        if (!std::isfinite(g[j + 1])) {
+          status = OPM_ERR_NONFINITE;
+          done = true;
+          break;
+        }
+        if (std::fabs(g[j + 1]) <= tol || hn == 0.0) {
+          conv = true;
+          ++j;
+          break;
+        }
+      }
+      if (done) break;
+      // ---- x += inv(M) V y with H y = g
+      for (int i = j - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
+        y[i] = acc / H[(size_t)i * m + i];
+      }
+      if (j > 0) {
+        CK(cudaMemcpyAsync(d_y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j, d_y, S.v, 1);
+        apply(S.v);
+        k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.t, nullptr, S.x, 1);
+      }
+      if (conv) {
+        status = OPM_OK;
+        break;
+      }
+      if (k >= maxit) {
+        status = OPM_NOT_CONVERGED;
+        break;
+      }
+      op(2, S.x, S.v);
+      k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.p, S.v, S.r, 0);
+      dots(S.r, 1, S.r, d_h1);
+      if ((s = read(1)) != OPM_OK) return s;
+      beta = std::sqrt(hh[0]);
+      if (beta <= tol) {
+        status = OPM_OK;
+        break;
+      }
+    }
+  }
+  // ---- true residual, x back to the caller's order (zeros on failure)
+  double rr = 0.0;
+  if (status == OPM_ERR_NONFINITE) {
+    rr = NAN;
+  } else if (n0 > 0.0) {
+    op(2, S.x, S.v);
+    k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.p, S.v, S.r, 0);
+    dots(S.r, 1, S.r, d_h1);
+    if ((s = read(1)) != OPM_OK) return s;
+    rr = std::sqrt(hh[0]) / n0;
+  }
+  if (status < 0) CK(cudaMemsetAsync(S.x, 0, vbytes, st));
+  CK(cudaMemcpyAsync(S.t, S.x, vbytes, cudaMemcpyDeviceToDevice, st));
+  k_scatter<<<R.ntiles, 256, 0, st>>>(R.B);
+  if (!x_dev) CK(cudaMemcpyAsync(x, h->vec_out, vbytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (iters) *iters = k;
+  if (relres) *relres = rr;
+  return status;
 }
 
 opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, const int32_t *cells, const double *B,

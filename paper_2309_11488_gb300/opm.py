@@ -40,7 +40,7 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve"]
 
 
 class opm_options(ctypes.Structure):
@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.opm_bsr_create_jacobi.restype = i32
         L.opm_set_wells.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.opm_set_wells.restype = i32
+        L.opm_gmres_solve.argtypes = [vp, vp, vp, f64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+        L.opm_gmres_solve.restype = i32
         L.opm_bsr_create.restype = i32
         L.opm_ilu0_factor.argtypes = [vp, vp]
         L.opm_ilu0_factor.restype = i32
@@ -425,6 +427,16 @@ class Solver:
 
     def factor(self, vals=None) -> int:
         return opm_ilu0_factor(self.h, vals)
+
+    def gmres(self, b, x=None, rtol=1e-2, maxit=200, restart=30):
+        """opm_gmres_solve; returns (x, status, iters, relres)."""
+        if x is None:
+            x = np.empty(3 * self.nb) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+        it = ctypes.c_int32()
+        rr = ctypes.c_double()
+        st = lib().opm_gmres_solve(self.h.ptr, _ptr(b, np.float64), _ptr(x, np.float64), float(rtol), int(maxit),
+                                   int(restart), ctypes.byref(it), ctypes.byref(rr))
+        return x, st, it.value, rr.value
 
     def set_wells(self, wells=None) -> int:
         """opm_set_wells from an object with ptr, cells, B, C, Dinv (numpy or
