@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="batched leg: AUTO options instead of the autotuner")
     p.add_argument("--no-jacobi", action="store_true", help="skip the block-Jacobi ILU0 leg")
     p.add_argument("--no-wells", action="store_true", help="skip the standard-wells leg")
+    p.add_argument("--no-gmres", action="store_true", help="skip the restarted-GMRES leg")
     p.add_argument("--wells", type=int, default=5, help="standard wells of the wells leg")
     p.add_argument("--partitions", type=int, default=150, help="block-Jacobi partitions")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -379,6 +380,8 @@ def run_ours(args, rank, world, dist):
         out["block_jacobi"] = measure_jacobi(args, s, barrier, max_over_ranks, world)
     if not args.no_wells:
         out["wells"] = measure_wells(args, s, out["config"]["options"], barrier, max_over_ranks, world)
+    if not args.no_gmres:
+        out["gmres"] = measure_gmres(args, s, out["config"]["options"], barrier, max_over_ranks, world)
     if not args.no_batched:
         out["batched"] = measure_batched(args, barrier, max_over_ranks, world)
     if not args.no_serving:
@@ -457,6 +460,35 @@ def measure_wells(args, s, options, barrier, max_over_ranks, world):
             err = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
         res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
                      "x_err_vs_x_true": err}
+    return res
+
+
+def measure_gmres(args, s, options, barrier, max_over_ranks, world):
+    """Restarted GMRES(30) with the same ILU0 on the same system (refactor +
+    solve to the same rtol, headline launch options), beside BiCGStab."""
+    import torch
+    from paper_2309_11488_gb300 import opm
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals, xt = dev(s.rowptr), dev(s.colidx), dev(s.vals), dev(s.x_true)
+    reps = max(3, args.steps // 20)
+    res = {"restart": 30}
+    with opm.Solver(s.nb, rp, ci, vals, **options) as sv:
+        b = sv.spmv(xt)
+        x = torch.empty_like(b)
+        for name, solve in (("gmres", lambda: sv.gmres(b, x, rtol=RTOL, maxit=300, restart=30)),
+                            ("bicgstab", lambda: sv.solve(b, x, rtol=RTOL, maxit=200))):
+            for _ in range(2):
+                sv.factor(vals)
+                _, st, it, rr = solve()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                sv.factor(vals)
+                _, st, it, rr = solve()
+            torch.cuda.synchronize()
+            dt = max_over_ranks(time.perf_counter() - t0)
+            res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
+                         "preconditioner_applications": it + (1 if name == "gmres" else it)}
     return res
 
 
