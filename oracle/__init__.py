@@ -18,6 +18,8 @@ Section references are to arXiv 2309.11488:
   * block-Jacobi ILU0           -- Section 4.5 (partition-internal blocks
                                    only; copy by an index vector)
   * standard wells, separate    -- Section 4.6 (y -= C^T inv(D) B x)
+  * iterative ILU0, Jacobi      -- Section 3's "Chow Patel ILU0" (Chow & Patel
+    triangular solves              2015; Anzt, Chow & Dongarra 2015)
   * restarted GMRES             -- Section 2 names it as OPM's other solver
                                    (method: Saad & Schultz 1986, right
                                    preconditioning, CGS2 Arnoldi)
@@ -80,6 +82,14 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_ilu0_cp.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p]
+        L.orc_ilu0_cp.restype = ctypes.c_int32
+        L.orc_ilu_apply_jacobi.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int32]
+        L.orc_ilu_apply_jacobi.restype = None
+        L.orc_bicgstab_x.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p, _f32p,
+                                     _f32p, ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.c_int32,
+                                     _f64p, _f64p, ctypes.c_double, ctypes.c_int32, _i32p, _f64p, _f64p]
+        L.orc_bicgstab_x.restype = ctypes.c_int
         L.orc_gmres.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
                                 ctypes.c_int32, ctypes.c_int32, _i32p, _f64p, _f64p]
         L.orc_gmres.restype = ctypes.c_int
@@ -138,9 +148,19 @@ class Factors:
     f32: bool = False
 
 
-def ilu0(nb, rowptr, colidx, vals, f32=False) -> Factors:
+def ilu0(nb, rowptr, colidx, vals, f32=False, cp_sweeps=0) -> Factors:
+    """ILU0 factors (Algorithm 2); with cp_sweeps > 0 the fine-grained
+    iterative ILU0 of Chow & Patel after that many synchronous sweeps."""
     rowptr, colidx, vals = _i32(rowptr), _i32(colidx), _f64(vals)
     nnzb = int(rowptr[nb])
+    if cp_sweeps > 0:
+        if f32:
+            raise ValueError("the iterative ILU0 is FP64 only")
+        lu = np.empty((nnzb, 9))
+        dinv = np.empty((nb, 9))
+        st = lib().orc_ilu0_cp(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p), int(cp_sweeps),
+                               _p(lu, _f64p), _p(dinv, _f64p))
+        return Factors(lu, dinv, int(st), False)
     if f32:
         lu = np.empty((nnzb, 9), dtype=np.float32)
         dinv = np.empty((nb, 9), dtype=np.float32)
@@ -154,9 +174,15 @@ def ilu0(nb, rowptr, colidx, vals, f32=False) -> Factors:
     return Factors(lu, dinv, int(st), f32)
 
 
-def ilu_apply(nb, rowptr, colidx, fac: Factors, r):
+def ilu_apply(nb, rowptr, colidx, fac: Factors, r, tri_sweeps=0):
+    """z = inv(U) inv(L) r (Algorithm 1); with tri_sweeps > 0 by that many
+    Jacobi sweeps per triangle (Anzt, Chow & Dongarra)."""
     rowptr, colidx, r = _i32(rowptr), _i32(colidx), _f64(r)
     z = np.empty(3 * nb)
+    if tri_sweeps > 0:
+        lib().orc_ilu_apply_jacobi(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(fac.lu, _f64p),
+                                   _p(fac.dinv, _f64p), _p(r, _f64p), _p(z, _f64p), int(tri_sweeps))
+        return z
     if fac.f32:
         lib().orc_ilu_apply_f32(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(fac.lu, _f32p),
                                 _p(fac.dinv, _f32p), _p(r, _f64p), _p(z, _f64p))
@@ -191,7 +217,7 @@ def spmv_wells(nb, rowptr, colidx, vals, wells, x):
 
 
 def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mpattern=None,
-             wells=None) -> SolveResult:
+             wells=None, tri_sweeps=0) -> SolveResult:
     """Right-preconditioned BiCGStab (Section 4.2); the factors live on
     mpattern = (rowptr, colidx) when given (block-Jacobi, Section 4.5), else
     on the matrix's own pattern; with wells (Section 4.6) every product with
@@ -212,12 +238,12 @@ def bicgstab(nb, rowptr, colidx, vals, fac: Factors, b, rtol=1e-2, maxit=200, mp
     d64 = fac.dinv if not fac.f32 else None
     lu32 = fac.lu if fac.f32 else None
     d32 = fac.dinv if fac.f32 else None
-    st = lib().orc_bicgstab_w(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
+    st = lib().orc_bicgstab_x(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(vals, _f64p),
                               _p(mrp, _i32p), _p(mci, _i32p),
                               _p(lu64, _f64p), _p(d64, _f64p), _p(lu32, _f32p), _p(d32, _f32p),
                               nw, _p(wp, _i32p), _p(wc, _i32p), _p(wb, _f64p), _p(wcc, _f64p), _p(wd, _f64p),
-                              _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p), _p(rr, _f64p),
-                              _p(hist, _f64p))
+                              int(tri_sweeps), _p(b, _f64p), _p(x, _f64p), rtol, maxit, _p(it, _i32p),
+                              _p(rr, _f64p), _p(hist, _f64p))
     return SolveResult(x, int(st), int(it[0]), float(rr[0]), hist)
 
 
@@ -352,7 +378,7 @@ def jacobi_pattern(nb, rowptr, colidx, vals, part):
 
 
 def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="natural", f32=False, part=None,
-                 wells=None):
+                 wells=None, cp_sweeps=0, tri_sweeps=0):
     """Same-ordering reference: ILU0 + BiCGStab on P A P^T with the oracle's
     own schedule permutation; with part, the preconditioner is the
     block-Jacobi ILU0 (Section 4.5): the schedule and the factors come from
@@ -367,7 +393,7 @@ def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="na
     prow, pcol, pval = permute(nb, rowptr, colidx, vals, perm)
     mprow, mpcol, mpval = permute(nb, mrp, mci, mvals, perm)
     pb = np.asarray(b).reshape(nb, 3)[perm].ravel()
-    fac = ilu0(nb, mprow, mpcol, mpval, f32=f32)
+    fac = ilu0(nb, mprow, mpcol, mpval, f32=f32, cp_sweeps=cp_sweeps)
     if fac.status != 0:
         raise ArithmeticError(f"oracle ILU0 failed with status {fac.status}")
     pw = None
@@ -375,7 +401,8 @@ def solve_system(nb, rowptr, colidx, vals, b, rtol=1e-2, maxit=200, schedule="na
         iperm = np.empty(nb, dtype=np.int64)
         iperm[perm] = np.arange(nb)
         pw = type(wells)(**{**wells.__dict__, "cells": iperm[np.asarray(wells.cells)].astype(np.int32)})
-    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit, mpattern=(mprow, mpcol), wells=pw)
+    res = bicgstab(nb, prow, pcol, pval, fac, pb, rtol, maxit, mpattern=(mprow, mpcol), wells=pw,
+                   tri_sweeps=tri_sweeps)
     x = np.empty(3 * nb)
     x.reshape(nb, 3)[perm] = res.x.reshape(nb, 3)
     return x, res, perm, nsets

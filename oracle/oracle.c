@@ -193,6 +193,118 @@ int orc_ilu0(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const dou
   return 0;
 }
 
+/*
+ * Fine-grained iterative ILU0 of Chow & Patel (2015), the "Chow Patel ILU0"
+ * of the paper's library table (Section 3): the factors are the fixed point
+ * of, for every block (i,j) of the pattern at once (synchronous sweeps, all
+ * right-hand sides from the previous sweep),
+ *   s = A_ij - sum_{k < min(i,j)} L_ik U_kj      (k ascending),
+ *   L_ij = s inv(U_jj) (i > j),  U_ii = s (its inverse kept),  U_ij = s (i < j).
+ * Initial guess L_ij = A_ij inv(A_jj), U_ij = A_ij.  After enough sweeps it
+ * reaches the ILU0 factors of orc_ilu0 with the same operations.  Output
+ * and returns as orc_ilu0 (a singular pivot during any sweep fails).
+ */
+int orc_ilu0_cp(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals, int32_t sweeps,
+                double *lu, double *dinv) {
+  const size_t nnzb = (size_t)rowptr[nb];
+  for (int32_t i = 0; i < nb; ++i) {
+    int64_t md = find_block(rowptr, colidx, i, i);
+    if (md < 0) return -(1 + nb + i);
+    if (orc_inv3(vals + BS2 * md, dinv + BS2 * (int64_t)i) != 0) return -(1 + i);
+  }
+  for (int32_t i = 0; i < nb; ++i)
+    for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+      if (colidx[m] < i) blk_mul(vals + BS2 * m, dinv + BS2 * (int64_t)colidx[m], lu + BS2 * m);
+      else memcpy(lu + BS2 * m, vals + BS2 * m, sizeof(double) * BS2);
+    }
+  double *lu2 = malloc(sizeof(double) * BS2 * (nnzb ? nnzb : 1));
+  double *d2 = malloc(sizeof(double) * BS2 * (size_t)(nb ? nb : 1));
+  int status = 0;
+  for (int32_t t = 0; t < sweeps && status == 0; ++t) {
+    for (int32_t i = 0; i < nb && status == 0; ++i)
+      for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+        const int32_t j = colidx[m];
+        const int32_t lim = j < i ? j : i;
+        double sum[BS2];
+        memcpy(sum, vals + BS2 * m, sizeof sum);
+        for (int64_t mk = rowptr[i]; mk < rowptr[i + 1] && colidx[mk] < lim; ++mk) {
+          int64_t mkj = find_block(rowptr, colidx, colidx[mk], j);
+          if (mkj >= 0) blk_mul_sub(lu + BS2 * mk, lu + BS2 * mkj, sum);
+        }
+        if (j < i) {
+          blk_mul(sum, dinv + BS2 * (int64_t)j, lu2 + BS2 * m);
+        } else {
+          memcpy(lu2 + BS2 * m, sum, sizeof sum);
+          if (j == i && orc_inv3(sum, d2 + BS2 * (int64_t)i) != 0) {
+            status = -(1 + i);
+            break;
+          }
+        }
+      }
+    if (status == 0) {
+      memcpy(lu, lu2, sizeof(double) * BS2 * nnzb);
+      memcpy(dinv, d2, sizeof(double) * BS2 * (size_t)nb);
+    }
+  }
+  free(lu2);
+  free(d2);
+  return status;
+}
+
+/*
+ * The triangular solves by Jacobi iteration (Anzt, Chow & Dongarra 2015):
+ * `sweeps` synchronous sweeps for L y = r from y = r,
+ *   y_i <- r_i - sum_{j<i} L_ij y_j,
+ * then `sweeps` for U z = y from z_i = inv(U_ii) y_i,
+ *   z_i <- inv(U_ii) (y_i - sum_{j>i} U_ij z_j),
+ * every sweep reading the previous iterate.  Exact after as many sweeps as
+ * the longest dependency chain of the factor.
+ */
+void orc_ilu_apply_jacobi(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *lu,
+                          const double *dinv, const double *r, double *z, int32_t sweeps) {
+  const size_t n = (size_t)BS * nb;
+  double *y = malloc(sizeof(double) * (n ? n : 1)), *y2 = malloc(sizeof(double) * (n ? n : 1));
+  double *z2 = malloc(sizeof(double) * (n ? n : 1));
+  memcpy(y, r, sizeof(double) * n);
+  for (int32_t t = 0; t < sweeps; ++t) {
+    for (int32_t i = 0; i < nb; ++i) {
+      double acc[BS];
+      for (int c = 0; c < BS; ++c) acc[c] = r[(int64_t)BS * i + c];
+      for (int64_t m = rowptr[i]; m < rowptr[i + 1] && colidx[m] < i; ++m) {
+        double tv[BS] = {0.0, 0.0, 0.0};
+        blk_matvec_add(lu + BS2 * m, y + (int64_t)BS * colidx[m], tv);
+        for (int c = 0; c < BS; ++c) acc[c] -= tv[c];
+      }
+      memcpy(y2 + (int64_t)BS * i, acc, sizeof acc);
+    }
+    memcpy(y, y2, sizeof(double) * n);
+  }
+  for (int32_t i = 0; i < nb; ++i) {
+    double zi[BS] = {0.0, 0.0, 0.0};
+    blk_matvec_add(dinv + BS2 * (int64_t)i, y + (int64_t)BS * i, zi);
+    memcpy(z + (int64_t)BS * i, zi, sizeof zi);
+  }
+  for (int32_t t = 0; t < sweeps; ++t) {
+    for (int32_t i = 0; i < nb; ++i) {
+      double acc[BS];
+      for (int c = 0; c < BS; ++c) acc[c] = y[(int64_t)BS * i + c];
+      for (int64_t m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+        if (colidx[m] <= i) continue;
+        double tv[BS] = {0.0, 0.0, 0.0};
+        blk_matvec_add(lu + BS2 * m, z + (int64_t)BS * colidx[m], tv);
+        for (int c = 0; c < BS; ++c) acc[c] -= tv[c];
+      }
+      double zi[BS] = {0.0, 0.0, 0.0};
+      blk_matvec_add(dinv + BS2 * (int64_t)i, acc, zi);
+      memcpy(z2 + (int64_t)BS * i, zi, sizeof zi);
+    }
+    memcpy(z, z2, sizeof(double) * n);
+  }
+  free(y);
+  free(y2);
+  free(z2);
+}
+
 /* ------------------------------------------------------------------------ */
 /* ILU0 application (Section 2.2, Algorithm 1, equations 3 and 4):          */
 /* solve L y = r by forward substitution with the unit lower factor, then   */
@@ -347,11 +459,21 @@ static double dot(size_t n, const double *a, const double *b) {
  * mcolidx): the block-Jacobi ILU0 of Section 4.5 factorises only the blocks
  * inside a partition while the SpMV keeps the whole matrix.
  */
+int orc_bicgstab_x(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                   const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
+                   const float *lu32, const float *dinv32, int32_t nwells, const int32_t *wptr,
+                   const int32_t *wcells, const double *B, const double *C, const double *Dinv, int32_t tri_sweeps,
+                   const double *b, double *x, double rtol, int32_t maxit, int32_t *iters, double *relres,
+                   double *res_hist);
+
 int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                    const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
                    const float *lu32, const float *dinv32, int32_t nwells, const int32_t *wptr,
                    const int32_t *wcells, const double *B, const double *C, const double *Dinv, const double *b,
-                   double *x, double rtol, int32_t maxit, int32_t *iters, double *relres, double *res_hist);
+                   double *x, double rtol, int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
+  return orc_bicgstab_x(nb, rowptr, colidx, vals, mrowptr, mcolidx, lu, dinv, lu32, dinv32, nwells, wptr, wcells,
+                        B, C, Dinv, 0, b, x, rtol, maxit, iters, relres, res_hist);
+}
 
 int orc_bicgstab_pc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                     const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
@@ -371,15 +493,17 @@ int orc_bicgstab(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const
 
 /*
  * The general form: preconditioner on its own pattern (block-Jacobi,
- * Section 4.5) and standard wells applied separately in every product with
- * the system operator (Section 4.6; nwells = 0: none).  The preconditioner
- * is the ILU0 of the cell matrix only.
+ * Section 4.5), standard wells applied separately in every product with
+ * the system operator (Section 4.6; nwells = 0: none), and the triangular
+ * solves by tri_sweeps Jacobi sweeps (0: exact substitution).  The
+ * preconditioner is the ILU0 of the cell matrix only.
  */
-int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+int orc_bicgstab_x(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
                    const int32_t *mrowptr, const int32_t *mcolidx, const double *lu, const double *dinv,
                    const float *lu32, const float *dinv32, int32_t nwells, const int32_t *wptr,
-                   const int32_t *wcells, const double *B, const double *C, const double *Dinv, const double *b,
-                   double *x, double rtol, int32_t maxit, int32_t *iters, double *relres, double *res_hist) {
+                   const int32_t *wcells, const double *B, const double *C, const double *Dinv, int32_t tri_sweeps,
+                   const double *b, double *x, double rtol, int32_t maxit, int32_t *iters, double *relres,
+                   double *res_hist) {
   size_t n = (size_t)BS * nb;
   double *r = calloc(n, sizeof(double)), *rh = calloc(n, sizeof(double));
   double *p = calloc(n, sizeof(double)), *v = calloc(n, sizeof(double));
@@ -414,6 +538,7 @@ int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, con
     double beta = (rho / rho_prev) * (alpha / omega);
     for (size_t e = 0; e < n; ++e) p[e] = r[e] + beta * (p[e] - omega * v[e]);
     if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, p, ph);
+    else if (tri_sweeps > 0) orc_ilu_apply_jacobi(nb, mrowptr, mcolidx, lu, dinv, p, ph, tri_sweeps);
     else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, p, ph);
     orc_spmv_wells(nb, rowptr, colidx, vals, nwells, wptr, wcells, B, C, Dinv, ph, v);
     double rhv = dot(n, rh, v);
@@ -431,6 +556,7 @@ int orc_bicgstab_w(int32_t nb, const int32_t *rowptr, const int32_t *colidx, con
       break;
     }
     if (lu32) orc_ilu_apply_f32(nb, mrowptr, mcolidx, lu32, dinv32, s, sh);
+    else if (tri_sweeps > 0) orc_ilu_apply_jacobi(nb, mrowptr, mcolidx, lu, dinv, s, sh, tri_sweeps);
     else orc_ilu_apply(nb, mrowptr, mcolidx, lu, dinv, s, sh);
     orc_spmv_wells(nb, rowptr, colidx, vals, nwells, wptr, wcells, B, C, Dinv, sh, t);
     double tt = dot(n, t, t);
@@ -480,7 +606,8 @@ done:
  * cycle (m steps, convergence, maxit or an exact breakdown) x += inv(M) V y
  * with H y = g; a new cycle starts from the true residual b - A x.  iters
  * counts Arnoldi steps over all cycles.  Returns 0 (converged),
- * 1 (maxit reached), -6 (non-finite b).  res_hist (optional, maxit + 1
+ * 1 (maxit reached), -5 (breakdown: a zero rotation denominator), -6
+ * (non-finite b or residual estimate; x then holds the last cycle's start).  res_hist (optional, maxit + 1
  * entries): ||r_0||, then the estimate after each step.
  */
 int orc_gmres(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals, const double *lu,
@@ -546,6 +673,10 @@ int orc_gmres(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const do
       }
       const double a = H[j * m + j], c = H[(j + 1) * m + j];
       const double den = sqrt(a * a + c * c);
+      if (den == 0.0) { /* w = 0 with H_jj = 0: no progress possible */
+        status = -5;
+        goto stop;
+      }
       cs[j] = a / den;
       sn[j] = c / den;
       H[j * m + j] = den;
@@ -553,6 +684,10 @@ int orc_gmres(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const do
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
       if (res_hist) res_hist[k] = fabs(g[j + 1]);
+      if (!isfinite(g[j + 1])) {
+        status = -6;
+        goto stop;
+      }
       if (fabs(g[j + 1]) <= tol || hn == 0.0) {
         conv = 1;
         ++j;
@@ -588,6 +723,7 @@ int orc_gmres(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const do
       break;
     }
   }
+stop:
   *iters = k;
 done:
   if (status == -6) {

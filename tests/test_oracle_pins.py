@@ -723,3 +723,164 @@ def test_gmres_restart_longer_than_the_solve_changes_nothing():
     x3, r3, _ = O.solve_system_gmres(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 300, 5, "colour")
     assert r3.status == 0 and r3.relres <= 1e-8 * (1 + 1e-6) and r3.iters > r1.iters
     assert np.linalg.norm(x3 - s.x_true) <= 1e-6 * np.linalg.norm(s.x_true)
+
+
+# ---------------------------------------------------------------- iterative ILU0, Jacobi triangular solves
+
+def _pattern_mask(s):
+    mask = np.zeros((s.nb, s.nb), dtype=bool)
+    for i in range(s.nb):
+        mask[i, s.colidx[s.rowptr[i]:s.rowptr[i + 1]]] = True
+    return mask
+
+
+def _cp_depth(s):
+    """Sweeps after which the synchronous fixed-point sweeps are exact, by
+    brute force over the dependency graph of the ILU0 equations: an entry
+    depends on L_ik and U_kj for every k < min(i,j) in the pattern, and
+    L_ij also on the pivot U_jj.  The initial guess is already exact for an
+    entry with an empty sum whose pivot (for L) is exact from the start;
+    every other entry is exact one sweep after its last dependency."""
+    mask = _pattern_mask(s)
+    depth = {}
+    for i in range(s.nb):          # rows in order: every dependency is in an earlier row
+        for j in np.nonzero(mask[i])[0]:
+            deps = [(i, k) for k in range(min(i, j)) if mask[i, k] and mask[k, j]]
+            deps += [(k, j) for k in range(min(i, j)) if mask[i, k] and mask[k, j]]
+            empty_sum = len(deps) == 0
+            if j < i:
+                deps.append((j, j))
+            worst = max((depth[d] for d in deps), default=0)
+            depth[(i, j)] = 0 if empty_sum and worst == 0 else 1 + worst
+    return max(depth.values())
+
+
+def test_chow_patel_zero_sweeps_is_the_initial_guess():
+    """No sweep leaves the initial guess L_ij = A_ij inv(A_jj), U_ij = A_ij."""
+    s = synth.random_pattern_system(30, 3, 41)
+    lu = np.empty((int(s.rowptr[-1]), 9))
+    dinv = np.empty((s.nb, 9))
+    st = O.lib().orc_ilu0_cp(s.nb, O._p(O._i32(s.rowptr), O._i32p), O._p(O._i32(s.colidx), O._i32p),
+                            O._p(O._f64(s.vals), O._f64p), 0, O._p(lu, O._f64p), O._p(dinv, O._f64p))
+    assert st == 0
+    a = s.vals.reshape(-1, 3, 3)
+    diag = [s.rowptr[i] + int(np.nonzero(s.colidx[s.rowptr[i]:s.rowptr[i + 1]] == i)[0][0]) for i in range(s.nb)]
+    for i in range(s.nb):
+        for m in range(s.rowptr[i], s.rowptr[i + 1]):
+            j = s.colidx[m]
+            want = a[m] @ np.linalg.inv(a[diag[j]]) if j < i else a[m]
+            np.testing.assert_allclose(lu[m].reshape(3, 3), want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+        np.testing.assert_allclose(dinv[i].reshape(3, 3), np.linalg.inv(a[diag[i]]), rtol=1e-12)
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.grid_system(4, 4, 3, synth.uniform(
+    synth.stream_key(5, 5), np.arange(48, dtype=np.uint64), -1, 1)),
+    lambda: synth.random_pattern_system(40, 3, 43)])
+def test_chow_patel_reaches_the_ilu0_identity_after_the_dependency_depth(maker):
+    """After exactly as many sweeps as the longest dependency chain (brute
+    force) the iterates satisfy (LU)_ij = A_ij on the pattern (checked with
+    dense products) and equal, bit for bit, the ILU0 of Algorithm 2, which
+    takes the same operations in the same order; one sweep earlier they
+    do not yet."""
+    s = maker()
+    d = _cp_depth(s)
+    assert 1 < d < s.nb
+    A = O.to_dense(s.nb, s.rowptr, s.colidx, s.vals)
+    big = np.kron(_pattern_mask(s), np.ones((3, 3), dtype=bool))
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, cp_sweeps=d)
+    assert fac.status == 0
+    L, U = dense_factors(s, fac)
+    assert np.abs(L @ U - A)[big].max() / np.abs(A).max() < 1e-14
+    for i in range(s.nb):          # the kept inverse pivots are the inverses of U's diagonal blocks
+        np.testing.assert_allclose(fac.dinv[i].reshape(3, 3) @ U[3 * i:3 * i + 3, 3 * i:3 * i + 3],
+                                   np.eye(3), atol=1e-12)
+    exact = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    np.testing.assert_array_equal(fac.lu, exact.lu)
+    np.testing.assert_array_equal(fac.dinv, exact.dinv)
+    early = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, cp_sweeps=d - 1)
+    assert not np.array_equal(early.lu, exact.lu)
+    late = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, cp_sweeps=d + 3)
+    np.testing.assert_array_equal(late.lu, exact.lu)
+
+
+def test_chow_patel_converges_geometrically_on_a_dominant_grid():
+    """On the diagonally dominant reservoir-like system a few sweeps already
+    bring the factors close (Chow & Patel report a handful of sweeps): the
+    distance to the exact ILU0 falls geometrically, by a factor of three or
+    more every two sweeps (an L entry takes its pivot from the previous
+    sweep, so a correction travels L -> U -> L in two)."""
+    s = synth.config1()
+    exact = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    dist = []
+    for t in (1, 3, 5, 7):
+        fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals, cp_sweeps=t)
+        assert fac.status == 0
+        dist.append(np.abs(fac.lu - exact.lu).max() / np.abs(exact.lu).max())
+    assert dist[0] < 0.1
+    assert all(b < a / 3 for a, b in zip(dist, dist[1:])), dist
+
+
+def test_chow_patel_flags_a_singular_pivot():
+    s = synth.block_diagonal_system(4, 9)
+    vals = s.vals.copy()
+    vals[2] = np.array([1.0, 2, 3, 2, 4, 6, 0, 0, 1])
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, vals, cp_sweeps=2)
+    assert fac.status == -(1 + 2)
+
+
+def test_jacobi_triangular_sweeps_follow_the_error_recurrence():
+    """Jacobi for L y = r (unit L) from y = r: y_t - y* = (-N)^t (r - y*) with
+    N the strictly lower part; for U z = y_T from z = inv(D) y_T:
+    z_t - z* = (-inv(D) S)^t (z_0 - z*) with S the strictly upper part."""
+    s = synth.random_pattern_system(25, 3, 45)
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    L, U = dense_factors(s, fac)
+    n = 3 * s.nb
+    N = L - np.eye(n)
+    D = np.zeros_like(U)
+    for i in range(s.nb):
+        D[3 * i:3 * i + 3, 3 * i:3 * i + 3] = U[3 * i:3 * i + 3, 3 * i:3 * i + 3]
+    Dinv = np.linalg.inv(D)
+    S = U - D
+    r = np.random.default_rng(9).standard_normal(n)
+    ystar = np.linalg.solve(L, r)
+    for t in (1, 2, 5):
+        yt = ystar + np.linalg.matrix_power(-N, t) @ (r - ystar)
+        zstar = np.linalg.solve(U, yt)
+        zt = zstar + np.linalg.matrix_power(-Dinv @ S, t) @ (Dinv @ yt - zstar)
+        z = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, r, tri_sweeps=t)
+        np.testing.assert_allclose(z, zt, rtol=0, atol=1e-11 * np.abs(zt).max())
+
+
+def test_jacobi_triangular_sweeps_are_exact_after_the_chain_length():
+    """Strictly triangular parts are nilpotent: after as many sweeps as the
+    longest chain of the factor's graph the Jacobi solve is the exact one."""
+    s = synth.grid_system(5, 4, 3, synth.uniform(synth.stream_key(5, 6), np.arange(60, dtype=np.uint64), -1, 1))
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    lev, nlev = O.levels(s.nb, s.rowptr, s.colidx)
+    r = np.random.default_rng(10).standard_normal(3 * s.nb)
+    exact = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, r)
+    z = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, r, tri_sweeps=nlev - 1)
+    np.testing.assert_allclose(z, exact, rtol=0, atol=1e-13 * np.abs(exact).max())
+    z = O.ilu_apply(s.nb, s.rowptr, s.colidx, fac, r, tri_sweeps=nlev - 2)
+    assert np.abs(z - exact).max() > 1e-10 * np.abs(exact).max()
+
+
+def test_iterative_ilu0_with_jacobi_solves_still_solves():
+    """BiCGStab with three Chow-Patel sweeps and three Jacobi sweeps per
+    triangle reaches x_true, at some cost in iterations over exact ILU0
+    (natural order).  Under a two-colour order every dependency chain has
+    length one, so a single sweep of each is already exact."""
+    s = synth.config1()
+    b = rhs(s)
+    x0, r0, *_ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-10, 400, "natural")
+    x1, r1, *_ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-10, 400, "natural", cp_sweeps=3,
+                               tri_sweeps=3)
+    assert r0.status == 0 and r1.status == 0
+    assert r0.iters < r1.iters <= 4 * r0.iters
+    assert np.linalg.norm(x1 - s.x_true) <= 1e-7 * np.linalg.norm(s.x_true)
+    x2, r2, _, nsets = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-10, 400, "colour")
+    x3, r3, _, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-10, 400, "colour", cp_sweeps=1,
+                                  tri_sweeps=1)
+    assert nsets == 2 and r2.iters == r3.iters
+    np.testing.assert_allclose(x3, x2, rtol=0, atol=1e-12 * np.abs(x2).max())
