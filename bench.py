@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-jacobi", action="store_true", help="skip the block-Jacobi ILU0 leg")
     p.add_argument("--no-wells", action="store_true", help="skip the standard-wells leg")
     p.add_argument("--no-gmres", action="store_true", help="skip the restarted-GMRES leg")
+    p.add_argument("--no-iterative", action="store_true",
+                   help="skip the iterative-ILU0 / Jacobi-triangular-solve leg")
     p.add_argument("--wells", type=int, default=5, help="standard wells of the wells leg")
     p.add_argument("--partitions", type=int, default=150, help="block-Jacobi partitions")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -382,6 +384,8 @@ def run_ours(args, rank, world, dist):
         out["wells"] = measure_wells(args, s, out["config"]["options"], barrier, max_over_ranks, world)
     if not args.no_gmres:
         out["gmres"] = measure_gmres(args, s, out["config"]["options"], barrier, max_over_ranks, world)
+    if not args.no_iterative:
+        out["iterative"] = measure_iterative(args, s, barrier, max_over_ranks, world)
     if not args.no_batched:
         out["batched"] = measure_batched(args, barrier, max_over_ranks, world)
     if not args.no_serving:
@@ -489,6 +493,47 @@ def measure_gmres(args, s, options, barrier, max_over_ranks, world):
             dt = max_over_ranks(time.perf_counter() - t0)
             res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
                          "preconditioner_applications": it + (1 if name == "gmres" else it)}
+    return res
+
+
+def measure_iterative(args, s, barrier, max_over_ranks, world):
+    """Chow-Patel iterative ILU0 (cp sweeps) and Jacobi triangular solves
+    (tri sweeps per triangle), the "Chow Patel ILU0" of Section 3's library
+    table, on the same system: factorisation time, solve time and iterations
+    to the same rtol, against the exact factorisation and substitution, for
+    level scheduling (the natural-order ILU0, many phases) and smallest-last
+    colouring (few phases)."""
+    import torch
+    from paper_2309_11488_gb300 import opm
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals, xt = dev(s.rowptr), dev(s.colidx), dev(s.vals), dev(s.x_true)
+    reps = max(3, args.steps // 20)
+    res = {}
+    for sched in ("level", "colour_sl"):
+        for cp, tri in ((0, 0), (0, 3), (3, 0), (2, 2), (3, 3)):
+            with opm.Solver(s.nb, rp, ci, vals, schedule=sched, cp_sweeps=cp, tri_sweeps=tri) as sv:
+                b = sv.spmv(xt)
+                x = torch.empty_like(b)
+                for _ in range(2):
+                    sv.factor(vals)
+                    _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=300)
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    sv.factor(vals)
+                torch.cuda.synchronize()
+                tf = max_over_ranks(time.perf_counter() - t0)
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    _, st, it, rr = sv.solve(b, x, rtol=RTOL, maxit=300)
+                torch.cuda.synchronize()
+                ts = max_over_ranks(time.perf_counter() - t0)
+                err = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+            res[f"{sched}_cp{cp}_tri{tri}"] = {
+                "solves_per_s": round(world * reps / (tf + ts), 2), "factor_ms": round(1e3 * tf / reps, 3),
+                "solve_ms": round(1e3 * ts / reps, 3), "iters": it, "status": st, "relres": rr,
+                "x_err_vs_x_true": err}
     return res
 
 

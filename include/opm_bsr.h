@@ -123,7 +123,29 @@ typedef struct opm_options {
                             wait for the preceding kernel), larger ones the
                             throughput form; 0 = default (10 per SM of the
                             device), -1 = throughput form for every phase   */
-  int32_t reserved[4];
+  int32_t cp_sweeps;     /* 0 = exact ILU0 by phases (Algorithm 2).  k > 0 =
+                            the fine-grained iterative ILU0 of Chow & Patel
+                            (the "Chow Patel ILU0" of Section 3's library
+                            table): from the guess L_ij = A_ij inv(A_jj),
+                            U_ij = A_ij, k synchronous sweeps of
+                              s = A_ij - sum_{k'<min(i,j)} L_ik' U_k'j,
+                              L_ij = s inv(U_jj), U_ij = s (i <= j),
+                            every block of the pattern at once, each sweep
+                            reading the previous one.  Reaches the ILU0
+                            factors after as many sweeps as the longest
+                            dependency chain; the schedule still orders the
+                            rows.  At most 4096; a second factor buffer is
+                            allocated                                         */
+  int32_t tri_sweeps;    /* 0 = exact triangular solves (Algorithm 1).  k > 0
+                            = k Jacobi sweeps per triangle (Anzt, Chow &
+                            Dongarra; the application half of the same
+                            table entry): y <- rhs - L y from y = rhs, then
+                            z <- inv(U_ii)(y - U_off z) from z = inv(U_ii) y,
+                            every row at once.  At most 64.  Used by every
+                            preconditioner application (BiCGStab, GMRES,
+                            opm_ilu_apply).  For a batch both counts are the
+                            batch's own options                               */
+  int32_t reserved[2];
 } opm_options;
 
 /* Fill *opt with the defaults (AUTO schedule, FP64, default stream). */
@@ -341,7 +363,8 @@ opm_status opm_solve_wait(opm_handle h, int32_t *iters, double *relres);
  * handles' device data and must be destroyed before them; members must not
  * be used on their own while a batch call on them runs.  Work goes on the
  * stream of opt (NULL = default stream); opt's schedule and precision are
- * ignored (the members fix them).
+ * ignored (the members fix them); its cp_sweeps and tri_sweeps apply to
+ * every member (the members' second buffers are allocated on demand).
  *   opm_batch_factor: vals[i] (host or device, NULL = refactor the values
  *     system i holds; vals itself may be NULL).
  *   opm_batch_solve: b[i], x[i] host or device; rtol[i] (rtol may be NULL =

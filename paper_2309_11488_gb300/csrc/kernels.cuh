@@ -62,9 +62,12 @@ struct Sys {
   int32_t nwrows, pad2;
   double *w_corr;           // [3n] sum of C_p^T t2 over row i's perforations (perforated rows only)
   void *lu;  // factor values (double or float): [L | U | Dinv slices]
+  void *lu2; // second factor buffer of the iterative ILU0 (cp_sweeps > 0), else NULL
   int64_t u_off, d_off;
   double *x, *r, *rh, *p, *v, *ph, *s, *sh, *t, *w;
   void *y;   // forward intermediate (factor precision)
+  void *y2;  // Jacobi triangular sweeps (tri_sweeps > 0): second forward iterate, else NULL
+  double *z2;  // Jacobi triangular sweeps: second backward iterate, else NULL
   double *partials;      // per tile: up to 4 partial sums
   double *grp_partials;  // per group of 32 tiles: up to 4 partial sums
   uint32_t *grp_count;   // per group of 32 tiles: tiles done (0 between kernels)
@@ -86,6 +89,8 @@ struct Batch {
   const int32_t *bwd_ptr; // [nphases + 1]: backward entries of phase c
   const int2 *tiles;      // (system, 1024-row tile) for the streaming kernels
   const int2 *tiles_s;    // (system, 256-row tile) for the SpMV kernels
+  const int4 *all_ent;    // every slice of every system: (system, slice, 0, n)
+  int32_t nall, pad;
   uint32_t *bar;          // grid barrier: arrivals at bar[0], generation at bar[32]
   int32_t nsys, nphases, ntiles, ntiles_s;
   int32_t skip_cta;       // test hook: this CTA never arrives at grid barriers (-1: off)
@@ -1083,6 +1088,53 @@ __global__ void __launch_bounds__(1024) k_apply(Batch B) {
   }
 }
 
+// Copies the lane's row of A into its L / D / U slots of the factor buffer
+// lu (the diagonal block into the Dinv slot, inverted later).  With
+// vals_user, block w of the permuted matrix comes from the caller's block
+// a_src[w] (Algorithm 3's index copy) and is also stored into A; without, A
+// is read.  Blocks outside the preconditioner's pattern have no slot.
+template <typename TF>
+__device__ __forceinline__ void copy_row_to_factors(const Sys &S, int sl, bool act, const double *vals_user,
+                                                    TF *lu) {
+  const int lane = threadIdx.x & 31;
+  const int s0 = sl * 32;
+  const int i = s0 + lane;
+  const int n = S.n;
+  const unsigned lt = lanemask_lt();
+  const int len = (i < n) ? __ldg(S.a_rp + i + 1) - __ldg(S.a_rp + i) : 0;
+  int base = (s0 < n) ? __ldg(S.a_rp + s0) : 0;
+  const int maxlen = __reduce_max_sync(0xffffffffu, act ? len : 0);
+  for (int k = 0; k < maxlen; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, len > k);
+    if (act && len > k) {
+      const int cnt = __popc(m);
+      const int q = __popc(m & lt);
+      const int w = base + q;
+      const int64_t dst = __ldg(S.a_dst + w);
+      const int64_t doff = dst >> 6;
+      const int dstr = (int)(dst & 63);
+      double *av = S.a_val + 9ll * base + q;
+      double e[9];
+      if (vals_user) {
+        const double *src = vals_user + 9ll * __ldg(S.a_src + w);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          e[c] = __ldg(src + c);
+          av[c * cnt] = e[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) e[c] = av[c * cnt];
+      }
+      if (dst >= 0) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
+      }
+    }
+    base += __popc(m);
+  }
+}
+
 // ILU0 decomposition (Algorithm 2) of the permuted matrix, phase by phase,
 // fused with the value permutation: with vals_in, block w of the permuted
 // matrix is copied from the caller's block a_src[w] (Algorithm 3's index
@@ -1099,41 +1151,7 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
   const double *__restrict__ vals_user = S.vals_in;
   const unsigned lt = lanemask_lt();
   DevState *st = S.st;
-  // ---- copy A's row into A (sliced) and into its L / D / U slots
-  {
-    const int len = (i < n) ? __ldg(S.a_rp + i + 1) - __ldg(S.a_rp + i) : 0;
-    int base = (s0 < n) ? __ldg(S.a_rp + s0) : 0;
-    const int maxlen = __reduce_max_sync(0xffffffffu, act ? len : 0);
-    for (int k = 0; k < maxlen; ++k) {
-      const unsigned m = __ballot_sync(0xffffffffu, len > k);
-      if (act && len > k) {
-        const int cnt = __popc(m);
-        const int q = __popc(m & lt);
-        const int w = base + q;
-        const int64_t dst = __ldg(S.a_dst + w);
-        const int64_t doff = dst >> 6;
-        const int dstr = (int)(dst & 63);
-        double *av = S.a_val + 9ll * base + q;
-        double e[9];
-        if (vals_user) {
-          const double *src = vals_user + 9ll * __ldg(S.a_src + w);
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            e[c] = __ldg(src + c);
-            av[c * cnt] = e[c];
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) e[c] = av[c * cnt];
-        }
-        if (dst >= 0) {  // blocks outside the preconditioner's pattern have no slot
-#pragma unroll
-          for (int c = 0; c < 9; ++c) lu[doff + (int64_t)c * dstr] = (TF)e[c];
-        }
-      }
-      base += __popc(m);
-    }
-  }
+  copy_row_to_factors<TF>(S, sl, act, vals_user, lu);
   // ---- eliminate with the pivots k < i (Algorithm 2's updates of row i)
   const int lrow = (i < n) ? __ldg(S.l_rp + i) : 0;
   const int len = (i < n) ? __ldg(S.l_rp + i + 1) - lrow : 0;

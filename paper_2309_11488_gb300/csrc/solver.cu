@@ -22,6 +22,7 @@
 
 #include "kernels.cuh"
 #include "gmres.cuh"
+#include "iterative.cuh"
 
 using namespace opm;
 
@@ -71,6 +72,9 @@ struct Runner {
   bool fp32 = false, cooperative = false, profile = false;
   int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
   int small_entries = 0;  // sweep phases with at most this many slices take the latency form
+  int cp_sweeps = 0;      // > 0: iterative ILU0 with this many sweeps instead of the phases
+  int tri_sweeps = 0;     // > 0: Jacobi triangular solves with this many sweeps per triangle
+  int nall = 0;           // slices of all systems (the iterative kernels' work list)
   bool has_wells = false; // some member has wells: products launch k_wells first (graphs built so)
   std::vector<int32_t> fwd_ptr, bwd_ptr;
   Batch B{};
@@ -186,10 +190,27 @@ void launch_pdl(void (*kern)(P...), int grid, int block, cudaStream_t st, A... a
 // phases run as one cooperative launch with grid barriers.
 constexpr int kMaxPhaseLaunches = 1024;
 
+// Bounds of the iterative sweeps (each sweep is a node of the captured graphs).
+constexpr int kMaxCpSweeps = 4096;
+constexpr int kMaxTriSweeps = 64;
+
 int blocks8(int entries) { return std::max(1, (entries + 7) / 8); }
+
+// Iterative ILU0: the initial guess, then cp_sweeps synchronous sweeps,
+// alternating between the two factor buffers so that the last sweep writes
+// the one the solver reads (sweep t of T writes buffer (T - t) & 1).
+template <typename TF>
+int launch_cp_factor_t(Runner &R, cudaStream_t st) {
+  const int T = R.cp_sweeps, g = blocks8(R.nall);
+  launch_pdl(k_cp_init<TF>, g, 256, st, R.B, 0, T & 1);
+  launch_pdl(k_cp_init<TF>, g, 256, st, R.B, 1, T & 1);
+  for (int t = 1; t <= T; ++t) launch_pdl(k_cp_sweep<TF>, g, 256, st, R.B, (T - t) & 1);
+  return T + 2;
+}
 
 template <typename TF>
 int launch_factor_t(Runner &R, cudaStream_t st) {
+  if (R.cp_sweeps > 0) return launch_cp_factor_t<TF>(R, st);
   if (R.cooperative) {
     launch_coop(k_factor<TF>, R.grid_factor, st, R.B);
     return 1;
@@ -222,8 +243,24 @@ void launch_sweep_phase(Runner &R, cudaStream_t st, int c, int cnt) {
   }
 }
 
+// Jacobi triangular solves: the right-hand side (MODE P / S), tri_sweeps
+// forward sweeps, tri_sweeps backward sweeps.
+template <typename TF, int MODE>
+int launch_jacobi_apply_t(Runner &R, cudaStream_t st) {
+  const int T = R.tri_sweeps, g = blocks8(R.nall);
+  int n = 2 * T;
+  if constexpr (MODE != kModePlain) {
+    launch_pdl(k_jac_rhs<MODE>, R.ntiles, 256, st, R.B);
+    ++n;
+  }
+  for (int t = 1; t <= T; ++t) launch_pdl(k_jac_fwd<TF, MODE>, g, 256, st, R.B, t, T);
+  for (int t = 1; t <= T; ++t) launch_pdl(k_jac_bwd<TF, MODE>, g, 256, st, R.B, t, T);
+  return n;
+}
+
 template <typename TF, int MODE>
 int launch_apply_t(Runner &R, cudaStream_t st) {
+  if (R.tri_sweeps > 0) return launch_jacobi_apply_t<TF, MODE>(R, st);
   if (R.cooperative) {
     launch_coop(k_apply<TF, MODE>, R.grid_apply, st, R.B);
     return 1;
@@ -472,6 +509,25 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     return fail(OPM_ERR_CUDA);
   }
   R->small_entries = o.small_phase_slices > 0 ? o.small_phase_slices : o.small_phase_slices < 0 ? 0 : 10 * sms;
+  R->cp_sweeps = o.cp_sweeps;
+  R->tri_sweeps = o.tri_sweeps;
+  // second buffers of the iterative sweeps, kept by the members
+  for (auto *h : mem) {
+    opm_status sa = OPM_OK;
+    const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+    if (R->cp_sweeps > 0 && !h->sys.lu2) {
+      uint8_t *p = nullptr;
+      sa = dalloc(h->allocs, h->dev_bytes, &p, esz * (size_t)h->an.lu_vals);
+      h->sys.lu2 = p;
+    }
+    if (sa == OPM_OK && R->tri_sweeps > 0 && !h->sys.y2) {
+      uint8_t *p = nullptr;
+      sa = dalloc(h->allocs, h->dev_bytes, &p, esz * 3 * (size_t)h->n);
+      h->sys.y2 = p;
+      if (sa == OPM_OK) sa = dalloc(h->allocs, h->dev_bytes, &h->sys.z2, 3 * (size_t)h->n);
+    }
+    if (sa != OPM_OK) return fail(sa);
+  }
   for (auto *h : mem) R->has_wells = R->has_wells || h->sys.nwells > 0;
   int maxp = 0;
   for (auto *h : mem) maxp = std::max(maxp, (int)h->an.phase_ptr.size() - 1);
@@ -513,6 +569,10 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     }
     R->bwd_ptr.push_back((int)ent.size());
   }
+  std::vector<int4> all_ent;
+  for (int s = 0; s < R->nsys; ++s)
+    for (int sl = 0; sl < mem[s]->nslices; ++sl) all_ent.push_back(make_int4(s, sl, 0, mem[s]->n));
+  R->nall = (int)all_ent.size();
   std::vector<int2> tiles, tiles_s;
   for (int s = 0; s < R->nsys; ++s) {
     for (int t = 0; t < mem[s]->sys.ntiles; ++t) tiles.push_back(make_int2(s, t));
@@ -524,12 +584,13 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
       sweep_launch == OPM_SWEEP_COOPERATIVE || (sweep_launch == OPM_SWEEP_AUTO && maxp > kMaxPhaseLaunches);
   // ---- device copies
   opm_status s;
-  int4 *d_ent;
+  int4 *d_ent, *d_all;
   int32_t *d_fwd, *d_bwd;
   int2 *d_tiles, *d_tiles_s;
   uint32_t *d_bar;
   Sys *d_sys;
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_ent, ent)) != OPM_OK) return fail(s);
+  if ((s = upload(R->allocs, R->dev_bytes, stream, &d_all, all_ent)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_fwd, R->fwd_ptr)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_bwd, R->bwd_ptr)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles, tiles)) != OPM_OK) return fail(s);
@@ -550,6 +611,8 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
   R->B.bwd_ptr = d_bwd;
   R->B.tiles = d_tiles;
   R->B.tiles_s = d_tiles_s;
+  R->B.all_ent = d_all;
+  R->B.nall = R->nall;
   R->B.ntiles_s = R->ntiles_s;
   R->B.bar = d_bar;
   R->B.nsys = R->nsys;
@@ -827,6 +890,8 @@ opm_status check_options(const opm_options &o) {
   if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
   if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;
   if (o.small_phase_slices < -1) return OPM_ERR_ARG;
+  if (o.cp_sweeps < 0 || o.cp_sweeps > kMaxCpSweeps || o.tri_sweeps < 0 || o.tri_sweeps > kMaxTriSweeps)
+    return OPM_ERR_ARG;
   return OPM_OK;
 }
 

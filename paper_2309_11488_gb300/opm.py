@@ -48,7 +48,7 @@ class opm_options(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
                 ("debug_skip_item", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
                 ("sweep_launch", ctypes.c_int32), ("small_phase_slices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("cp_sweeps", ctypes.c_int32), ("tri_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 OPM_TUNE_MAX = 24
@@ -336,13 +336,14 @@ def _ptr_array(arrays, dtype):
 class Batch:
     """A set of handles factorised and solved together (see include/opm_bsr.h)."""
 
-    def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto", small_phase_slices=0):
+    def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto", small_phase_slices=0, cp_sweeps=0,
+                 tri_sweeps=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.handles = list(handles)
         hs = (ctypes.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
         o = opm_options_default(stream=stream, chunk=chunk, sweep_launch=sweep_launch,
-                                small_phase_slices=small_phase_slices)
+                                small_phase_slices=small_phase_slices, cp_sweeps=cp_sweeps, tri_sweeps=tri_sweeps)
         out = ctypes.c_void_p()
         st = lib().opm_batch_create(len(self.handles), hs, ctypes.byref(o), ctypes.byref(out))
         if st != OPM_OK:
@@ -415,13 +416,14 @@ class Solver:
 
     def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
                  spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto",
-                 small_phase_slices=0, part=None):
+                 small_phase_slices=0, part=None, cp_sweeps=0, tri_sweeps=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
                                            spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item,
                                            profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch,
-                                           small_phase_slices=small_phase_slices)
+                                           small_phase_slices=small_phase_slices, cp_sweeps=cp_sweeps,
+                                           tri_sweeps=tri_sweeps)
         self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options, part=part)
         self.nb = nb
 

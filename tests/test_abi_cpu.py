@@ -43,6 +43,13 @@ def test_options_default():
     assert o.schedule == 0 and o.precision == 0 and o.debug_skip_item == -1 and o.chunk == 0
 
 
+def test_iterative_sweep_options_are_bounded_on_the_host():
+    s = synth.config1()
+    for kw in ({"cp_sweeps": -1}, {"tri_sweeps": -1}, {"cp_sweeps": 4097}, {"tri_sweeps": 65}):
+        st, h = opm.opm_bsr_create(s.nb, s.rowptr, s.colidx, s.vals, opm.opm_options_default(**kw), check=False)
+        assert st == opm.OPM_ERR_ARG and h is None
+
+
 def _create(nb, rp, ci, vals, **kw):
     return opm.opm_bsr_create(nb, np.asarray(rp, np.int32), np.asarray(ci, np.int32),
                               np.asarray(vals, np.float64), opm.opm_options_default(**kw), check=False)
