@@ -138,6 +138,24 @@ def algorithmic_apply_bytes(info, fp32: bool) -> int:
     return factors + vectors
 
 
+def jacobi_apply_work(info, sweeps: int, fp32: bool):
+    """Algorithmic work of one preconditioner application by Jacobi sweeps
+    (T = sweeps per triangle): the right-hand side (r, v and p read, p
+    written; 3.5 vector passes on average over the two BiCGStab
+    applications), T forward sweeps (L's blocks and columns, the row
+    pointers, the right-hand side, the gathered previous iterate and the new
+    one), z_0 = inv(U_ii) y_T (Dinv read, z_0 written), T backward sweeps
+    (U's blocks and columns, the row pointers, y_T, the gathered previous z,
+    Dinv and the new z).  Returns (bytes, FP64 FMAs)."""
+    n, nl, nu = info.nb, info.nnzb_lower, info.nnzb_upper
+    val = 4 if fp32 else 8
+    blk, vec, d = 9 * val + 4, 3 * val, 9 * val
+    nbytes = 3.5 * 24 * n + sweeps * (blk * nl + 4 * n + 24 * n + 2 * vec * n) + (d + 24) * n \
+        + sweeps * (blk * nu + 4 * n + vec * n + 2 * 24 * n + d * n)
+    fma = 4.5 * n + (0 if fp32 else 9 * sweeps * (nl + nu) + 9 * n * (sweeps + 1))
+    return int(nbytes), int(fma)
+
+
 # FP64 FMA peak of the GB300: 2 FP64 lanes per SM per clock (the FP64 pipe's
 # issue rate) x 152 SMs x 2.07 GHz maximum SM clock = 629 G FMA/s, i.e.
 # 1.259 TFLOP/s (the nominal 1.25 TFLOP/s FP64 of the part).
@@ -534,6 +552,32 @@ def measure_iterative(args, s, barrier, max_over_ranks, world):
                 "solves_per_s": round(world * reps / (tf + ts), 2), "factor_ms": round(1e3 * tf / reps, 3),
                 "solve_ms": round(1e3 * ts / reps, 3), "iters": it, "status": st, "relres": rr,
                 "x_err_vs_x_true": err}
+    # one Jacobi application (3 sweeps per triangle) against the HBM and FP64
+    # rooflines, timed by the profiled handle's events (level order)
+    with opm.Solver(s.nb, rp, ci, vals, schedule="level", cp_sweeps=3, tri_sweeps=3, profile_kernels=True) as sv:
+        b = sv.spmv(xt)
+        x = torch.empty_like(b)
+        sv.factor(vals)
+        sv.solve(b, x, rtol=RTOL, maxit=300)
+        sv.reset_timing()
+        for _ in range(reps):
+            sv.factor(vals)
+            sv.solve(b, x, rtol=RTOL, maxit=300)
+        t = sv.timing()
+        info = sv.info()
+    avg_ms = t.kernel_ms[1] / max(t.kernel_count[1], 1)
+    nbytes, fma = jacobi_apply_work(info, 3, False)
+    peak, src = peaks()
+    gbs = nbytes / (avg_ms * 1e-3) / 1e9
+    fmas = fma / (avg_ms * 1e-3)
+    res["jacobi_apply_level_tri3"] = {
+        "avg_launch_group_us": round(avg_ms * 1e3, 2), "applications": int(t.kernel_count[1]),
+        "kernels_per_application": 7,
+        "hbm": {"bytes": nbytes, "achieved_gbs": round(gbs, 1), "peak_gbs": peak, "frac": round(gbs / peak, 4),
+                "peak_source": src},
+        "fp64_fma": {"fmas": fma, "frac": round(fmas / FP64_FMA_PEAK, 4),
+                     "peak_source": "derived: 2 FP64 FMA lanes/SM/clock x 152 SMs x 2.07 GHz"},
+        "factor_ms_cp3": round(t.kernel_ms[0] / max(t.kernel_count[0], 1), 3)}
     return res
 
 
