@@ -338,11 +338,16 @@ opm_status opm_reset_timing(opm_handle h);
 /*
  * Asynchronous refactor + solve (the paper's per-Newton-step pair, Section
  * 4.4 and 4.2) for serving loops: enqueues, on the handle's stream and
- * without waiting, an optional refactorisation with vals (device, 9*nnzb
- * doubles; NULL = keep the factors) and a solve of A x = b (b, x device,
- * 3*nb doubles, caller's order).  The pointers must stay valid and
- * untouched until opm_solve_wait returns.  While a launch is pending the
- * handle accepts only opm_solve_ready and opm_solve_wait.
+ * without waiting, an optional refactorisation with vals (9*nnzb doubles;
+ * NULL = keep the factors) and a solve of A x = b (b, x 3*nb doubles,
+ * caller's order).  Each pointer may be device or host memory: host inputs
+ * are copied to the device and a host x is copied back on the same stream,
+ * so with page-locked host memory (cudaHostAlloc / cudaHostRegister) the
+ * whole step, transfers included, is enqueued without a host wait (the
+ * paper's Section 4.11 copies of the matrix and vectors).  The pointers
+ * must stay valid and untouched until opm_solve_wait returns.  While a
+ * launch is pending the handle accepts only opm_solve_ready and
+ * opm_solve_wait.
  * opm_solve_ready returns 1 when the work has completed (or none is
  * pending), else 0.  opm_solve_wait blocks until completion and returns
  * what opm_bicgstab_solve would (a singular pivot of the refactorisation is

@@ -1378,16 +1378,21 @@ opm_status opm_bicgstab_solve(opm_handle h, const double *b, double *x, double r
 opm_status opm_solve_launch(opm_handle h, const double *vals, const double *b, double *x, double rtol,
                             int32_t maxit) {
   if (!h || h->n == 0 || !b || !x || !(rtol >= 0.0) || h->async_pending || h->run->profile) return OPM_ERR_ARG;
-  if (!is_device_ptr(b) || !is_device_ptr(x) || (vals && !is_device_ptr(vals))) return OPM_ERR_ARG;
   if (!vals && !h->factors_ok) return OPM_ERR_ZERO_PIVOT;
-  h->sys.b_in = b;
-  h->sys.x_out = x;
-  h->sys.rtol = rtol;
-  h->sys.maxit = maxit;
-  h->sys.vals_in = vals;
-  opm_status s = runner_enqueue(*h->run, vals != nullptr, true);
+  const double *dv = nullptr;
+  opm_status s = staged_vals(h, vals, &dv);
+  if (s != OPM_OK) return s;
+  bool x_dev = false;
+  if ((s = prepare_solve(h, b, x, rtol, maxit, &x_dev)) != OPM_OK) return s;
+  h->sys.vals_in = dv;
+  Runner &R = *h->run;
+  s = runner_enqueue(R, vals != nullptr, true);
   h->sys.vals_in = nullptr;
   if (s != OPM_OK) return s;
+  if (!x_dev) {
+    CK(cudaMemcpyAsync(x, h->vec_out, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(R.ev_done, h->stream));  // completion now includes the copy back
+  }
   h->async_pending = true;
   h->timing.launches += vals ? h->run->factor_launches : 0;
   return OPM_OK;

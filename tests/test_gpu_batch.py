@@ -119,6 +119,27 @@ def test_async_launch_matches_synchronous(precision):
         assert sv.ready()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_async_launch_with_host_buffers(pinned):
+    """Host values, b and x (page-locked or pageable) are copied on the
+    handle's stream; results equal the device-buffer launch bit for bit."""
+    s = synth.config2()
+    b = rhs(s)
+    vals2 = synth.newton_update(s, 7)[0]
+    with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, schedule="colour") as sv:
+        xd = torch.empty(3 * s.nb, dtype=torch.float64, device="cuda")
+        sv.launch(dev(vals2), dev(b), xd, rtol=1e-2)
+        ref = sv.wait()
+        vh, bh = torch.from_numpy(vals2.copy()), torch.from_numpy(b.copy())
+        xh = torch.zeros(3 * s.nb, dtype=torch.float64)
+        if pinned:
+            vh, bh, xh = vh.pin_memory(), bh.pin_memory(), xh.pin_memory()
+        sv.launch(vh, bh, xh, rtol=1e-2)
+        got = sv.wait()
+    assert got == ref
+    np.testing.assert_array_equal(xh.numpy(), xd.cpu().numpy())
+
+
 def test_batch_async_launch():
     syss = synth.config4(nsys=5)
     bs = [dev(rhs(s)) for s in syss]
