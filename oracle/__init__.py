@@ -82,6 +82,8 @@ def lib():
         L.orc_colours.restype = ctypes.c_int32
         L.orc_order_by_key.argtypes = [ctypes.c_int32, _i32p, ctypes.c_int32, _i32p]
         L.orc_order_by_key.restype = None
+        L.orc_colours_kempe.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        L.orc_colours_kempe.restype = ctypes.c_int32
         L.orc_ilu0_cp.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _f64p, _f64p]
         L.orc_ilu0_cp.restype = ctypes.c_int32
         L.orc_ilu_apply_jacobi.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int32]
@@ -275,6 +277,15 @@ def colours_sl(nb, rowptr, colidx):
     return col, int(n)
 
 
+def colours_kempe(nb, rowptr, colidx):
+    """Smallest-last colouring, then the highest colour classes emptied by
+    Kempe-chain exchanges while possible (orc_colours_kempe)."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    col = np.empty(nb, dtype=np.int32)
+    n = lib().orc_colours_kempe(nb, _p(rowptr, _i32p), _p(colidx, _i32p), _p(col, _i32p))
+    return col, int(n)
+
+
 def order_by_key(key, nkeys):
     key = _i32(key)
     perm = np.empty(key.shape[0], dtype=np.int32)
@@ -283,7 +294,8 @@ def order_by_key(key, nkeys):
 
 
 def schedule_perm(nb, rowptr, colidx, schedule):
-    """perm[new] = old for 'natural', 'level', 'colour' or 'colour_sl' (Section 4.4):
+    """perm[new] = old for 'natural', 'level', 'colour', 'colour_sl' or
+    'colour_kempe' (Section 4.4):
     set-major; inside a set the closed rows (no neighbour in a later set)
     first; inside each of these groups the rows longer than the most common
     row length last; natural order inside each part.  Returns (perm, number
@@ -296,6 +308,8 @@ def schedule_perm(nb, rowptr, colidx, schedule):
         key, n = colours(nb, rowptr, colidx)
     elif schedule == "colour_sl":
         key, n = colours_sl(nb, rowptr, colidx)
+    elif schedule == "colour_kempe":
+        key, n = colours_kempe(nb, rowptr, colidx)
     else:
         raise ValueError(schedule)
     # inside each set: rows without a neighbour in a later set first; inside

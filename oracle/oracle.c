@@ -928,11 +928,13 @@ static int cmp_i32(const void *a, const void *b) {
  * coloured first-fit in the reverse order of removal.  Returns the number
  * of colours.
  */
-int32_t orc_colours_sl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *colour) {
+/* The symmetrised pattern with each row's distinct neighbours sorted
+   (no self loops): row i's neighbours are gadj[dptr[i] .. dptr[i+1]). */
+static void distinct_graph(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int64_t **dptr_out,
+                           int32_t **gadj_out) {
   int64_t *gptr;
   int32_t *gadj;
   sym_graph(nb, rowptr, colidx, &gptr, &gadj);
-  /* distinct neighbours, sorted, packed in place */
   int64_t *dptr = malloc(sizeof(int64_t) * ((size_t)nb + 1));
   int64_t w = 0;
   dptr[0] = 0;
@@ -943,6 +945,24 @@ int32_t orc_colours_sl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
       if (m == a || gadj[m] != gadj[m - 1]) gadj[w++] = gadj[m];
     dptr[i + 1] = w;
   }
+  free(gptr);
+  *dptr_out = dptr;
+  *gadj_out = gadj;
+}
+
+static int32_t colours_sl_graph(int32_t nb, const int64_t *dptr, const int32_t *gadj, int32_t *colour);
+
+int32_t orc_colours_sl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *colour) {
+  int64_t *dptr;
+  int32_t *gadj;
+  distinct_graph(nb, rowptr, colidx, &dptr, &gadj);
+  int32_t ncol = colours_sl_graph(nb, dptr, gadj, colour);
+  free(dptr);
+  free(gadj);
+  return ncol;
+}
+
+static int32_t colours_sl_graph(int32_t nb, const int64_t *dptr, const int32_t *gadj, int32_t *colour) {
   int32_t *deg = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1));
   char *gone = calloc((size_t)(nb ? nb : 1), 1);
   int32_t *order = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1));
@@ -984,8 +1004,98 @@ int32_t orc_colours_sl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
   free(order);
   free(gone);
   free(deg);
+  return ncol;
+}
+
+/*
+ * Colour-class reduction by Kempe chains (Kempe 1879) after the
+ * smallest-last colouring: the highest class is emptied row by row if it
+ * can be, then the next, until a class cannot be emptied or two colours
+ * remain.  A row v of the highest colour t first takes the smallest colour
+ * below t that none of its neighbours has.  Otherwise, for each pair of
+ * colours (a, b) below t (a ascending, then b ascending, b != a), the rows
+ * reachable from v's a-coloured neighbours through rows coloured a or b
+ * (breadth first: the starts in neighbour order, then each row's
+ * neighbours in order) are collected; if the search meets no neighbour of
+ * v and stays within kempe_cap rows, a and b are exchanged on the
+ * collected rows (a proper colouring stays proper, and no neighbour of v
+ * keeps colour a) and v takes a.  A row that finds no such pair keeps t.
+ * Returns the number of colours.
+ */
+enum { kempe_cap = 16384 };
+
+int32_t orc_colours_kempe(int32_t nb, const int32_t *rowptr, const int32_t *colidx, int32_t *colour) {
+  int64_t *dptr;
+  int32_t *gadj;
+  distinct_graph(nb, rowptr, colidx, &dptr, &gadj);
+  int32_t ncol = colours_sl_graph(nb, dptr, gadj, colour);
+  int32_t *nbr_of = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1)); /* row whose neighbour this is */
+  int32_t *mark = malloc(sizeof(int32_t) * (size_t)(nb ? nb : 1));   /* search that collected it */
+  int32_t *queue = malloc(sizeof(int32_t) * (size_t)(kempe_cap + 1));
+  int32_t *used = calloc((size_t)ncol + 1, sizeof(int32_t));
+  for (int32_t i = 0; i < nb; ++i) nbr_of[i] = mark[i] = -1;
+  int32_t search = 0;
+  while (ncol > 2) {
+    const int32_t t = ncol - 1;
+    int32_t left = 0;
+    for (int32_t v = 0; v < nb; ++v) {
+      if (colour[v] != t) continue;
+      for (int32_t c = 0; c < t; ++c) used[c] = 0;
+      for (int64_t m = dptr[v]; m < dptr[v + 1]; ++m) {
+        nbr_of[gadj[m]] = v;
+        if (colour[gadj[m]] < t) used[colour[gadj[m]]] = 1;
+      }
+      int32_t free_c = -1;
+      for (int32_t c = 0; c < t && free_c < 0; ++c)
+        if (!used[c]) free_c = c;
+      if (free_c >= 0) {
+        colour[v] = free_c;
+        continue;
+      }
+      int done = 0;
+      for (int32_t a = 0; a < t && !done; ++a)
+        for (int32_t b = 0; b < t && !done; ++b) {
+          if (b == a) continue;
+          ++search;
+          int32_t qn = 0, ok = 1;
+          for (int64_t m = dptr[v]; m < dptr[v + 1] && ok; ++m) {
+            const int32_t u = gadj[m];
+            if (colour[u] != a) continue;
+            if (qn == kempe_cap) ok = 0;
+            else {
+              mark[u] = search;
+              queue[qn++] = u;
+            }
+          }
+          for (int32_t head = 0; head < qn && ok; ++head) {
+            const int32_t x = queue[head];
+            for (int64_t m = dptr[x]; m < dptr[x + 1]; ++m) {
+              const int32_t y = gadj[m];
+              if (mark[y] == search || (colour[y] != a && colour[y] != b)) continue;
+              if (nbr_of[y] == v || qn == kempe_cap) {
+                ok = 0;
+                break;
+              }
+              mark[y] = search;
+              queue[qn++] = y;
+            }
+          }
+          if (ok) {
+            for (int32_t q = 0; q < qn; ++q) colour[queue[q]] = colour[queue[q]] == a ? b : a;
+            colour[v] = a;
+            done = 1;
+          }
+        }
+      if (!done) ++left;
+    }
+    if (left > 0) break;
+    --ncol;
+  }
+  free(used);
+  free(queue);
+  free(mark);
+  free(nbr_of);
   free(dptr);
-  free(gptr);
   free(gadj);
   return ncol;
 }

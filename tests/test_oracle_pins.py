@@ -375,20 +375,107 @@ def test_smallest_last_colours_a_grid_with_two_colours_and_faults_with_few():
     assert n_sl <= n_nat
 
 
+def _pattern_from_edges(n, edges):
+    """Symmetric BSR pattern (diagonal plus both directions of each edge)."""
+    rows = [{i} for i in range(n)]
+    for a, b in edges:
+        rows[a].add(b)
+        rows[b].add(a)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    colidx = np.array([c for r in rows for c in sorted(r)], dtype=np.int32)
+    return rowptr, colidx
+
+
+def _chromatic_number(n, edges):
+    """Smallest k admitting a proper colouring, by exhaustive search."""
+    for k in range(1, n + 1):
+        for cols in np.ndindex(*([k] * n)):
+            if all(cols[a] != cols[b] for a, b in edges):
+                return k
+    return n
+
+
+def _is_bipartite(s):
+    a, b = _edges(s)
+    adj = [[] for _ in range(s.nb)]
+    for x, y in zip(a, b):
+        adj[x].append(y)
+        adj[y].append(x)
+    side = -np.ones(s.nb, dtype=np.int64)
+    for r in range(s.nb):
+        if side[r] >= 0:
+            continue
+        side[r] = 0
+        stack = [r]
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if side[y] < 0:
+                    side[y] = 1 - side[x]
+                    stack.append(y)
+                elif side[y] == side[x]:
+                    return False
+    return True
+
+
+@pytest.mark.parametrize("maker", [synth.config1, synth.config2, lambda: synth.random_pattern_system(300, 3, 5),
+                                   lambda: synth.random_pattern_system(120, 4, 9), lambda: synth.tree_system(200, 3),
+                                   lambda: synth.chain_system(50)])
+def test_kempe_reduction_keeps_a_proper_colouring_with_no_more_colours(maker):
+    s = maker()
+    col, n = O.colours_kempe(s.nb, s.rowptr, s.colidx)
+    _, n_sl = O.colours_sl(s.nb, s.rowptr, s.colidx)
+    a, b = _edges(s)
+    assert np.all(col[a] != col[b])
+    assert n <= n_sl
+    assert set(np.unique(col)) == set(range(n))  # classes 0..n-1, none empty
+    if _is_bipartite(s) and len(a):
+        # forests and unfaulted grids are bipartite; the reduction reaches 2 there
+        assert n == 2
+
+
+def test_kempe_reduction_reaches_two_colours_on_the_bipartite_config2_pattern():
+    """C2's pattern happens to be bipartite (checked by BFS parity): greedy
+    smallest-last needs 4 colours there, the Kempe exchanges reach the
+    minimum, 2; C3's faults leave odd cycles and 3 colours."""
+    c2 = synth.config2()
+    assert _is_bipartite(c2)
+    assert O.colours_sl(c2.nb, c2.rowptr, c2.colidx)[1] == 4
+    assert O.colours_kempe(c2.nb, c2.rowptr, c2.colidx)[1] == 2
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_kempe_reduction_never_beats_the_chromatic_number(seed):
+    """Brute force on tiny random graphs: the count is at least the
+    chromatic number, and an odd cycle keeps 3 colours."""
+    rng = np.random.default_rng(seed)
+    n = 7
+    edges = sorted({tuple(sorted(e)) for e in rng.integers(0, n, size=(9, 2)) if e[0] != e[1]})
+    rowptr, colidx = _pattern_from_edges(n, edges)
+    col, k = O.colours_kempe(n, rowptr, colidx)
+    assert all(col[a] != col[b] for a, b in edges)
+    assert k >= _chromatic_number(n, edges)
+    cyc = [(i, (i + 1) % 5) for i in range(5)]
+    rowptr, colidx = _pattern_from_edges(5, cyc)
+    assert O.colours_kempe(5, rowptr, colidx)[1] == 3
+
+
 def test_order_by_key_is_stable_and_complete():
     key = np.array([2, 0, 1, 0, 2, 1, 0])
     perm = O.order_by_key(key, 3)
     np.testing.assert_array_equal(perm, [1, 3, 6, 2, 5, 0, 4])
 
 
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
     """Brute force on the sets the oracle returns: each set is contiguous in
     set order; inside it the rows without a neighbour in a later set come
     first; inside each of those groups the rows with more blocks than the
     most common count come last; natural order inside each part."""
     s = synth.random_pattern_system(60, 90, seed=11)
-    key, n = {"level": O.levels, "colour": O.colours, "colour_sl": O.colours_sl}[schedule](s.nb, s.rowptr, s.colidx)
+    key, n = {"level": O.levels, "colour": O.colours, "colour_sl": O.colours_sl,
+              "colour_kempe": O.colours_kempe}[schedule](s.nb, s.rowptr, s.colidx)
     perm, nsets = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
     assert nsets == n and sorted(perm.tolist()) == list(range(s.nb))
     nbrs = [set() for _ in range(s.nb)]
