@@ -72,12 +72,18 @@ enum {
   OPM_SCHED_LEVEL = 2,   /* level scheduling: same factors as natural order   */
   OPM_SCHED_COLOUR = 3,  /* greedy graph colouring, rows in natural order: a
                             different ILU0                                    */
-  OPM_SCHED_COLOUR_SL = 4 /* greedy graph colouring, rows in smallest-last
+  OPM_SCHED_COLOUR_SL = 4, /* greedy graph colouring, rows in smallest-last
                             order (Matula & Beck 1983: repeatedly remove a row
                             of least remaining degree, ties to the lowest row;
                             colour in reverse removal order): at most one more
                             colour than the pattern's degeneracy, usually
                             fewer colours than natural order                 */
+  OPM_SCHED_COLOUR_KEMPE = 5 /* smallest-last colouring, then the highest
+                            colour classes emptied by Kempe-chain exchanges
+                            (Kempe 1879) while possible: each row of the top
+                            class takes a free lower colour, or swaps a pair
+                            of lower colours on a bounded chain that frees
+                            one.  Fewer colours, hence fewer small phases   */
 };
 
 /* Storage precision of the ILU0 factors.  The Krylov recurrences, dots,

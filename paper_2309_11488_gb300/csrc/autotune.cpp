@@ -107,7 +107,7 @@ opm_status tune(Problem &P, bool allow_natural, int32_t repeats, const opm_optio
     return phases;
   };
   // 1. schedule x sweep launch (one launch per phase only for few phases)
-  std::vector<int32_t> scheds = {OPM_SCHED_LEVEL, OPM_SCHED_COLOUR, OPM_SCHED_COLOUR_SL};
+  std::vector<int32_t> scheds = {OPM_SCHED_LEVEL, OPM_SCHED_COLOUR, OPM_SCHED_COLOUR_SL, OPM_SCHED_COLOUR_KEMPE};
   if (allow_natural) scheds.push_back(OPM_SCHED_NATURAL);
   for (int32_t sc : scheds) {
     const int32_t phases = tryc({sc, OPM_SWEEP_COOPERATIVE, 2, 0});

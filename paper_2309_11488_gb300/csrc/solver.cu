@@ -885,7 +885,7 @@ opm_status alloc_system(opm_solver *h) {
 }
 
 opm_status check_options(const opm_options &o) {
-  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR_SL) return OPM_ERR_ARG;
+  if (o.schedule < OPM_SCHED_AUTO || o.schedule > OPM_SCHED_COLOUR_KEMPE) return OPM_ERR_ARG;
   if (o.precision != OPM_PREC_FP64 && o.precision != OPM_PREC_FP32_FACTORS) return OPM_ERR_ARG;
   if (o.chunk < 0 || o.spin_limit_us < 0) return OPM_ERR_ARG;
   if (o.sweep_launch < OPM_SWEEP_AUTO || o.sweep_launch > OPM_SWEEP_COOPERATIVE) return OPM_ERR_ARG;

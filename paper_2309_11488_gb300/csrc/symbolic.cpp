@@ -85,11 +85,11 @@ int32_t colour_sets(int32_t n, const std::vector<int64_t> &gp, const std::vector
 // are removed one at a time, each time one of least degree among those left
 // (distinct neighbours still present; ties to the lowest row), then coloured
 // in the reverse order of removal.
-int32_t colour_sets_sl(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
-                       std::vector<int32_t> &key) {
-  // distinct neighbour lists
-  std::vector<int64_t> dp((size_t)n + 1, 0);
-  std::vector<int32_t> da;
+// Each row's distinct neighbours, sorted.
+void distinct_lists(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                    std::vector<int64_t> &dp, std::vector<int32_t> &da) {
+  dp.assign((size_t)n + 1, 0);
+  da.clear();
   da.reserve(ga.size());
   std::vector<int32_t> tmp;
   for (int32_t i = 0; i < n; ++i) {
@@ -99,6 +99,21 @@ int32_t colour_sets_sl(int32_t n, const std::vector<int64_t> &gp, const std::vec
     da.insert(da.end(), tmp.begin(), tmp.end());
     dp[i + 1] = (int64_t)da.size();
   }
+}
+
+int32_t colour_sets_sl_lists(int32_t n, const std::vector<int64_t> &dp, const std::vector<int32_t> &da,
+                             std::vector<int32_t> &key);
+
+int32_t colour_sets_sl(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                       std::vector<int32_t> &key) {
+  std::vector<int64_t> dp;
+  std::vector<int32_t> da;
+  distinct_lists(n, gp, ga, dp, da);
+  return colour_sets_sl_lists(n, dp, da, key);
+}
+
+int32_t colour_sets_sl_lists(int32_t n, const std::vector<int64_t> &dp, const std::vector<int32_t> &da,
+                             std::vector<int32_t> &key) {
   std::vector<int32_t> deg(n), order;
   order.reserve(n);
   std::vector<char> gone(n, 0);
@@ -132,6 +147,82 @@ int32_t colour_sets_sl(int32_t n, const std::vector<int64_t> &gp, const std::vec
     nsets = std::max(nsets, c + 1);
   }
   return nsets;
+}
+
+// Smallest-last colouring, then fewer colour classes by Kempe-chain
+// exchanges (Kempe 1879): while more than two colours remain, each row v of
+// the highest colour t (in row order) takes the smallest lower colour free
+// among its neighbours, or else, trying colour pairs (a, b) below t with a
+// then b ascending, the first pair whose Kempe chain is usable: the rows
+// reached breadth first from v's a-coloured neighbours (in list order)
+// through rows coloured a or b.  The chain is usable when the search meets
+// no other neighbour of v within kKempeCap rows; a and b are then swapped
+// on it (the colouring stays proper and no neighbour of v keeps a) and v
+// takes a.  The pass stops at the first class that cannot be emptied.
+constexpr int32_t kKempeCap = 16384;
+
+int32_t colour_sets_kempe(int32_t n, const std::vector<int64_t> &gp, const std::vector<int32_t> &ga,
+                          std::vector<int32_t> &key) {
+  std::vector<int64_t> dp;
+  std::vector<int32_t> da;
+  distinct_lists(n, gp, ga, dp, da);
+  int32_t ncol = colour_sets_sl_lists(n, dp, da, key);
+  std::vector<int32_t> owner(n, -1), seen(n, -1), chain;
+  chain.reserve(kKempeCap);
+  std::vector<char> taken;
+  int32_t search = 0;
+  // the Kempe chain of (a, b) from v's a-neighbours; false when unusable
+  auto collect = [&](int32_t v, int32_t a, int32_t b) {
+    ++search;
+    chain.clear();
+    for (int64_t m = dp[v]; m < dp[v + 1]; ++m) {
+      const int32_t u = da[m];
+      if (key[u] != a) continue;
+      if ((int32_t)chain.size() == kKempeCap) return false;
+      seen[u] = search;
+      chain.push_back(u);
+    }
+    for (size_t h = 0; h < chain.size(); ++h) {
+      const int32_t x = chain[h];
+      for (int64_t m = dp[x]; m < dp[x + 1]; ++m) {
+        const int32_t y = da[m];
+        if (seen[y] == search || (key[y] != a && key[y] != b)) continue;
+        if (owner[y] == v || (int32_t)chain.size() == kKempeCap) return false;
+        seen[y] = search;
+        chain.push_back(y);
+      }
+    }
+    return true;
+  };
+  while (ncol > 2) {
+    const int32_t t = ncol - 1;
+    bool emptied = true;
+    for (int32_t v = 0; v < n; ++v) {
+      if (key[v] != t) continue;
+      taken.assign((size_t)t, 0);
+      for (int64_t m = dp[v]; m < dp[v + 1]; ++m) {
+        owner[da[m]] = v;
+        if (key[da[m]] < t) taken[key[da[m]]] = 1;
+      }
+      const int32_t lowest = (int32_t)(std::find(taken.begin(), taken.end(), 0) - taken.begin());
+      if (lowest < t) {
+        key[v] = lowest;
+        continue;
+      }
+      bool moved = false;
+      for (int32_t a = 0; a < t && !moved; ++a)
+        for (int32_t b = 0; b < t && !moved; ++b) {
+          if (b == a || !collect(v, a, b)) continue;
+          for (int32_t x : chain) key[x] = key[x] == a ? b : a;
+          key[v] = a;
+          moved = true;
+        }
+      if (!moved) emptied = false;
+    }
+    if (!emptied) break;
+    --ncol;
+  }
+  return ncol;
 }
 
 // Warp-sliced order of a CSR part: fills pos[csr block] = sliced block index
@@ -237,9 +328,10 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
     std::vector<int64_t> gp;
     std::vector<int32_t> ga;
     symmetrise(n, mrp, mci, gp, ga);
-    an.nsets = schedule == OPM_SCHED_LEVEL    ? level_sets(n, gp, ga, key)
-               : schedule == OPM_SCHED_COLOUR ? colour_sets(n, gp, ga, key)
-                                              : colour_sets_sl(n, gp, ga, key);
+    an.nsets = schedule == OPM_SCHED_LEVEL       ? level_sets(n, gp, ga, key)
+               : schedule == OPM_SCHED_COLOUR    ? colour_sets(n, gp, ga, key)
+               : schedule == OPM_SCHED_COLOUR_SL ? colour_sets_sl(n, gp, ga, key)
+                                                 : colour_sets_kempe(n, gp, ga, key);
     // Inside a set, rows with no neighbour in a later set (hence no U block)
     // come first: they finish within the forward sweep, and the backward
     // sweep of the set covers a contiguous tail.  Rows of a set share no

@@ -30,7 +30,7 @@ OPM_ERR_OOM = -7
 OPM_ERR_TIMEOUT = -8
 OPM_ERR_CUDA = -9
 
-SCHEDULES = {"auto": 0, "natural": 1, "level": 2, "colour": 3, "colour_sl": 4}
+SCHEDULES = {"auto": 0, "natural": 1, "level": 2, "colour": 3, "colour_sl": 4, "colour_kempe": 5}
 SWEEPS = {"auto": 0, "per_phase": 1, "cooperative": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 

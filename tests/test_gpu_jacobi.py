@@ -50,7 +50,7 @@ def case(name):
 
 @pytest.mark.parametrize("sweep", ["per_phase", "cooperative"])
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_jacobi_permutation_and_factors(name, schedule, sweep):
     s, part = case(name)
     perm, nsets, prow, pcol, mprow, mpcol, fac = ref_jacobi(s, part, schedule)
@@ -114,7 +114,7 @@ def check_jacobi_solve(s, part, schedule, rtol, precision="fp64", maxit=200):
 
 
 @pytest.mark.parametrize("name", ["c1_4parts", "ragged_mod3", "chain_cut"])
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_jacobi_solve_small(name, schedule):
     s, part = case(name)
     check_jacobi_solve(s, part, schedule, 1e-8)

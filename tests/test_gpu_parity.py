@@ -70,7 +70,7 @@ def check_spmv(s, schedule):
 
 
 @pytest.mark.parametrize("name", list(SMALL))
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_spmv_small(name, schedule):
     check_spmv(SMALL[name](), schedule)
 
@@ -88,7 +88,7 @@ SWEEPS = ["per_phase", "cooperative"]
 
 @pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", list(SMALL))
-@pytest.mark.parametrize("schedule", ["natural", "level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["natural", "level", "colour", "colour_sl", "colour_kempe"])
 def test_permutation_and_factors(name, schedule, sweep):
     s = SMALL[name]()
     if schedule == "natural" and s.nb > 2000:
@@ -116,7 +116,7 @@ def check_factors(nb, prow, pcol, fac, lu, dinv, tol):
     assert derr.max() <= tol
 
 
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_factors_config3_full_size(c3, schedule):
     perm, nsets, prow, pcol, pval, fac = ref_same_order(c3, schedule)
     with opm.Solver(c3.nb, dev(c3.rowptr), dev(c3.colidx), dev(c3.vals), schedule=schedule) as sv:
@@ -127,7 +127,7 @@ def test_factors_config3_full_size(c3, schedule):
 
 @pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", ["c1", "ragged33", "long_rows", "tree"])
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_ilu_apply(name, schedule, sweep):
     s = SMALL[name]()
     perm, nsets, prow, pcol, pval, fac = ref_same_order(s, schedule)
@@ -164,7 +164,7 @@ def check_solve(s, schedule, rtol, precision="fp64", maxit=200, xtol=1e-8, sweep
 
 @pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("name", list(SMALL))
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_solve_small(name, schedule, sweep):
     check_solve(SMALL[name](), schedule, 1e-8, sweep=sweep)
 
@@ -179,7 +179,7 @@ def test_solve_config2_level(c2):
 
 
 @pytest.mark.parametrize("sweep", SWEEPS)
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_solve_config3_full_size(c3, schedule, sweep):
     check_solve(c3, schedule, 1e-3, sweep=sweep)
 
@@ -190,7 +190,7 @@ def test_solve_natural_small():
 
 # ------------------------------------------------------------ FP32 factors
 
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_fp32_factors_match_single_precision_oracle(schedule):
     s = synth.config1()
     perm, nsets, prow, pcol, pval, fac = ref_same_order(s, schedule, f32=True)
@@ -199,7 +199,7 @@ def test_fp32_factors_match_single_precision_oracle(schedule):
     check_factors(s.nb, prow, pcol, fac, lu, dinv, 2e-5)
 
 
-@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl"])
+@pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_fp32_solve_tight_tolerance_matches_fp64_oracle(c2, schedule):
     b = rhs(c2)
     x_ref, res, _, _ = O.solve_system(c2.nb, c2.rowptr, c2.colidx, c2.vals, b, 1e-10, 200, schedule)
@@ -312,3 +312,15 @@ def test_user_stream():
     with opm.Solver(s.nb, s.rowptr, s.colidx, s.vals, stream=stream) as sv:
         x, st, it, rr = sv.solve(dev(b))
         assert st == 0 and rr <= 1e-2
+
+
+def test_kempe_schedule_has_fewer_phases_on_config3(c3):
+    """C3: smallest-last colouring leaves 4 colours; the Kempe exchanges
+    empty the fourth, so the sweeps walk 3 phases (the oracle's count)."""
+    _, n_sl = O.colours_sl(c3.nb, c3.rowptr, c3.colidx)
+    perm, nsets = O.schedule_perm(c3.nb, c3.rowptr, c3.colidx, "colour_kempe")
+    assert n_sl == 4 and nsets == 3
+    with opm.Solver(c3.nb, dev(c3.rowptr), dev(c3.colidx), dev(c3.vals), schedule="colour_kempe") as sv:
+        info = sv.info()
+        np.testing.assert_array_equal(sv.permutation(), perm)
+    assert info.nsets == 3 and info.nphases == 3

@@ -26,7 +26,7 @@ def abs_wells(w):
 
 
 @pytest.mark.parametrize("maker,nw,layers", [(synth.config1, 3, 4), (synth.config2, 6, 12)])
-@pytest.mark.parametrize("schedule", ["colour", "colour_sl", "level"])
+@pytest.mark.parametrize("schedule", ["colour", "colour_sl", "colour_kempe", "level"])
 def test_spmv_with_wells(maker, nw, layers, schedule):
     s = maker()
     w = synth.wells(s, nw, layers)
@@ -69,7 +69,7 @@ def check_solve_wells(s, w, schedule, rtol, precision="fp64", maxit=300):
     return x
 
 
-@pytest.mark.parametrize("schedule", ["colour", "colour_sl", "level"])
+@pytest.mark.parametrize("schedule", ["colour", "colour_sl", "colour_kempe", "level"])
 def test_solve_with_wells_small(schedule):
     s = synth.config1()
     check_solve_wells(s, synth.wells(s, 3, 4), schedule, 1e-8)
