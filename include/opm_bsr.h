@@ -67,7 +67,7 @@ typedef enum {
 
 /* Row order used for the parallel schedule (Section 4.4). */
 enum {
-  OPM_SCHED_AUTO = 0,    /* the library picks (currently: colouring)          */
+  OPM_SCHED_AUTO = 0,    /* the library picks (currently: OPM_SCHED_COLOUR_KEMPE) */
   OPM_SCHED_NATURAL = 1, /* caller's order; sequential dependency chains      */
   OPM_SCHED_LEVEL = 2,   /* level scheduling: same factors as natural order   */
   OPM_SCHED_COLOUR = 3,  /* greedy graph colouring, rows in natural order: a

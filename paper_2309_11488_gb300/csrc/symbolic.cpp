@@ -291,7 +291,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
   an = Analysis();
   an.n = n;
   an.nnzb = nnzb;
-  if (schedule == OPM_SCHED_AUTO) schedule = OPM_SCHED_COLOUR;
+  if (schedule == OPM_SCHED_AUTO) schedule = OPM_SCHED_COLOUR_KEMPE;
   an.schedule = schedule;
 
   // ---- the preconditioner's pattern.  With a partition (block-Jacobi ILU0,
