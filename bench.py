@@ -180,7 +180,7 @@ def kernel_source_hash() -> str:
     """Hash of what fixes the sweep kernels' DRAM traffic: their device code
     and the layout the symbolic analysis gives the factors."""
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "symbolic.cpp"):
+    for f in ("sweeps.cuh", "symbolic.cpp"):
         with open(os.path.join(ROOT, "paper_2309_11488_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libopm_bsr.so")
 SOURCES = ["solver.cu", "symbolic.cpp", "noalloc.cu", "autotune.cpp"]
-HEADERS = ["kernels.cuh", "gmres.cuh", "iterative.cuh", "opm_internal.h"]
+HEADERS = ["kernels.cuh", "sweeps.cuh", "factor.cuh", "gmres.cuh", "iterative.cuh", "opm_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -5,15 +5,17 @@
 // (Batch::all_ent, one warp per 32-row slice, one lane per row) instead of
 // one launch per level or colour.
 //
-// Both use the storage of kernels.cuh: factors warp-sliced [L | U | Dinv
-// slices], the diagonal block of U held only as its inverse.  Sweeps are
+// Both use the storage of the exact path (kernels.cuh, factor.cuh,
+// sweeps.cuh): factors warp-sliced [L | U | Dinv slices], the diagonal block
+// of U held only as its inverse.  Sweeps are
 // synchronous: sweep t reads the iterate of sweep t-1 from one buffer and
 // writes the other (lu/lu2 for the factors, y/y2 and the output/z2 for the
 // triangular solves); the buffers alternate so that the last sweep lands in
 // the buffer the rest of the solver reads.
 #pragma once
 
-#include "kernels.cuh"
+#include "factor.cuh"
+#include "sweeps.cuh"
 
 namespace opm {
 

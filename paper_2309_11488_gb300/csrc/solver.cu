@@ -21,6 +21,8 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "sweeps.cuh"
+#include "factor.cuh"
 #include "gmres.cuh"
 #include "iterative.cuh"
 
@@ -215,9 +217,18 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
     launch_coop(k_factor<TF>, R.grid_factor, st, R.B);
     return 1;
   }
-  for (int c = 0; c < R.nphases; ++c)
-    launch_pdl(k_factor_phase<TF>, blocks8(R.fwd_ptr[c + 1] - R.fwd_ptr[c]), 256, st, R.B, c);
-  return R.nphases;
+  // A small phase is bound by the FP64 rate of the SMs it occupies (a few
+  // warps per row, dozens of FMAs per block): two warps per CTA spread it
+  // over up to all SMs instead of one in eight.
+  int n = 0;
+  for (int c = 0; c < R.nphases; ++c) {
+    const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
+    if (cnt == 0) continue;
+    if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF>, (cnt + 1) / 2, 64, st, R.B, c);
+    else launch_pdl(k_factor_phase<TF>, blocks8(cnt), 256, st, R.B, c);
+    ++n;
+  }
+  return n;
 }
 
 // Slabs a small-phase sweep loads ahead of its wait: 8 covers nearly every
