@@ -463,18 +463,23 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
   OPM_TILE(B, S, lt);
   if (blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
   double acc[1] = {0.0};
+  const double *__restrict__ b_in = S.b_in;
+  const int32_t *__restrict__ perm = S.perm;
+  double *__restrict__ r = S.r, *__restrict__ rh = S.rh, *__restrict__ x = S.x, *__restrict__ p = S.p,
+                       *__restrict__ v = S.v;
+  const int n = S.n;
   OPM_TILE_ROWS(i, lt) {
-    if (i < S.n) {
-      const int o = S.perm[i];
-      const double b0 = S.b_in[3ll * o], b1 = S.b_in[3ll * o + 1], b2 = S.b_in[3ll * o + 2];
-      double *r = S.r + 3ll * i, *rh = S.rh + 3ll * i;
-      r[0] = b0; r[1] = b1; r[2] = b2;
-      rh[0] = b0; rh[1] = b1; rh[2] = b2;
+    if (i < n) {
+      const int o = __ldg(perm + i);
+      const double b0 = __ldg(b_in + 3ll * o), b1 = __ldg(b_in + 3ll * o + 1), b2 = __ldg(b_in + 3ll * o + 2);
+      const size_t e0 = 3ll * i;
+      r[e0] = b0; r[e0 + 1] = b1; r[e0 + 2] = b2;
+      rh[e0] = b0; rh[e0 + 1] = b1; rh[e0 + 2] = b2;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        S.x[3ll * i + c] = 0.0;
-        S.p[3ll * i + c] = 0.0;
-        S.v[3ll * i + c] = 0.0;
+        x[e0 + c] = 0.0;
+        p[e0 + c] = 0.0;
+        v[e0 + c] = 0.0;
       }
       acc[0] = fma(b0, b0, fma(b1, b1, fma(b2, b2, acc[0])));
     }
