@@ -343,7 +343,7 @@ def run_ours(args, rank, world, dist):
                 "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": f"{src} (MEMORY copy, MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_launch": int(nbytes), "avg_launch_us": round(avg * 1e3, 2), "launches": int(cnt),
-                "traffic": measured_traffic("apply", precision)}
+                "traffic": measured_traffic("apply", precision) if args.grid == 100 else None}
 
     def iteration(r, ms_total, precision):
         """Per-iteration time of the timed run (its refactorisation, setup

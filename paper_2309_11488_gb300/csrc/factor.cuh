@@ -35,11 +35,14 @@ __device__ __forceinline__ void copy_row_to_factors(const Sys &S, int sl, bool a
       double *av = S.a_val + 9ll * base + q;
       double e[9];
       if (vals_user) {
+        // the permuted copy is next read by the SpMV: its stores are marked
+        // evict-first, which keeps the pivot rows' inverses and U blocks in
+        // L2 for the gathers
         const double *src = vals_user + 9ll * __ldg(S.a_src + w);
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
           e[c] = __ldg(src + c);
-          av[c * cnt] = e[c];
+          __stcs(av + c * cnt, e[c]);
         }
       } else {
 #pragma unroll
