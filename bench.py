@@ -341,11 +341,20 @@ def run_ours(args, rank, world, dist):
         nbytes = algorithmic_apply_bytes(r["info"], precision == "fp32")
         peak, src = peaks()
         ach = nbytes / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        # FP64 FMAs of one application: 9 per factor block (L and U blocks
+        # in the sweeps, the inverse pivot once per row) and the right-hand
+        # side (6 per row for p^, 3 for s^); with FP64 factors the HBM and
+        # FP64 floors are within 1% of each other, so both are reported
+        info = r["info"]
+        fmas = 0 if precision == "fp32" else 9 * info.nnzb + 4.5 * info.nb
         return {"kernel": f"k_apply<{'float' if precision == 'fp32' else 'double'}> (ILU0 forward+backward)",
                 "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": f"{src} (MEMORY copy, MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_launch": int(nbytes), "avg_launch_us": round(avg * 1e3, 2), "launches": int(cnt),
-                "traffic": measured_traffic("apply", precision) if args.grid == 100 else None}
+                "traffic": measured_traffic("apply", precision) if args.grid == 100 else None,
+                "fp64_fma": {"fmas_per_launch": int(fmas),
+                             "frac": round(fmas / (avg * 1e-3) / FP64_FMA_PEAK, 4) if avg > 0 else 0.0,
+                             "peak_source": "derived: 2 FP64 FMA lanes/SM/clock x 152 SMs x 2.07 GHz"}}
 
     def iteration(r, ms_total, precision):
         """Per-iteration time of the timed run (its refactorisation, setup
