@@ -439,7 +439,7 @@ def measure_jacobi(args, s, barrier, max_over_ranks, world):
     keeps the blocks inside each of args.partitions transmissibility-weighted
     partitions (the paper's 150-partition configurations), the SpMV all of A;
     refactor + solve to the same rtol, against the plain preconditioner, for
-    level scheduling and smallest-last colouring."""
+    level scheduling and the Kempe-reduced colouring."""
     import torch
     from paper_2309_11488_gb300 import opm, synth
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -450,7 +450,7 @@ def measure_jacobi(args, s, barrier, max_over_ranks, world):
     res = {"partitions": int(args.partitions), "blocks_dropped": dropped,
            "blocks_dropped_frac": round(dropped / s.nnzb, 4)}
     reps = max(3, args.steps // 20)
-    for sched in ("level", "colour_sl"):
+    for sched in ("level", "colour_kempe"):
         for name, p in (("plain", None), ("jacobi", part)):
             with opm.Solver(s.nb, rp, ci, vals, schedule=sched, part=p) as sv:
                 b = sv.spmv(xt)

@@ -324,3 +324,32 @@ def test_kempe_schedule_has_fewer_phases_on_config3(c3):
         info = sv.info()
         np.testing.assert_array_equal(sv.permutation(), perm)
     assert info.nsets == 3 and info.nphases == 3
+
+
+def test_bench_launch_configuration_full_size(c3):
+    """The configuration the bench times on C3 (the autotuner's choice:
+    Kempe-reduced colouring, one launch per phase, one iteration per loop
+    body, default small-phase threshold), through the asynchronous
+    refactor + solve the bench calls: factors, solution and iteration count
+    against the oracle, and the ILU application sampled against the
+    oracle's."""
+    b = rhs(c3)
+    x_ref, res, perm, _ = O.solve_system(c3.nb, c3.rowptr, c3.colidx, c3.vals, b, 1e-3, 200, "colour_kempe")
+    with opm.Solver(c3.nb, dev(c3.rowptr), dev(c3.colidx), dev(c3.vals), schedule="colour_kempe",
+                    sweep_launch="per_phase", chunk=1, small_phase_slices=0) as sv:
+        np.testing.assert_array_equal(sv.permutation(), perm)
+        x = torch.empty(3 * c3.nb, dtype=torch.float64, device="cuda")
+        sv.launch(dev(c3.vals), dev(b), x, rtol=1e-3, maxit=200)
+        st, it, relres = sv.wait()
+        lu, dinv = sv.factors()
+        r = synth.uniform(synth.stream_key(9, 11), np.arange(3 * c3.nb, dtype=np.uint64), -1, 1)
+        z = sv.ilu_apply(dev(r)).cpu().numpy()
+    assert st == res.status == 0 and it == res.iters
+    assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    assert abs(relres - res.relres) <= 1e-6 * res.relres
+    _, _, prow, pcol, pval, fac = ref_same_order(c3, "colour_kempe")
+    check_factors(c3.nb, prow, pcol, fac, lu, dinv, 1e-12)
+    zp = O.ilu_apply(c3.nb, prow, pcol, fac, r.reshape(-1, 3)[perm].ravel())
+    z_ref = np.empty_like(zp)
+    z_ref.reshape(-1, 3)[perm] = zp.reshape(-1, 3)
+    np.testing.assert_allclose(z, z_ref, rtol=1e-11, atol=1e-12 * np.abs(z_ref).max())
