@@ -457,11 +457,38 @@ __device__ __forceinline__ void row_operator(const Sys &S, const double *__restr
 
 // Starts a solve: r = P b, r^ = r, x = p = v = 0, ||b||^2; the system's
 // last CTA sets the scalars.  A factorisation error makes the solve fail.
+// The solve state from ||b||^2 (bb) and the factorisation's outcome.
+__device__ __forceinline__ void setup_scalars(const Sys &S, DevState *st, double bb) {
+  const double n0 = sqrt(bb);
+  st->n0 = n0;
+  st->tol = S.rtol * n0;
+  st->maxit = S.maxit;
+  st->k = 1;
+  st->iters = 0;
+  st->half = 0;
+  st->error = 0;
+  st->relres = 0.0;
+  st->rho = bb;
+  st->rho_prev = 1.0;
+  st->alpha = 1.0;
+  st->omega = 1.0;
+  st->beta = bb;
+  if (st->ferror != 0) st->status = st->ferror;
+  else if (!isfinite(n0)) st->status = OPM_ERR_NONFINITE;
+  else if (n0 == 0.0) st->status = OPM_OK;
+  else if (S.maxit < 1) st->status = OPM_NOT_CONVERGED;
+  else st->status = kRunning;
+}
+
+// FINAL: the last CTA also sets the solve state.  Without FINAL (beside a
+// running factorisation) it only records ||b||^2 and leaves the state and
+// the grid barrier to k_start.
+template <bool FINAL>
 __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
   __shared__ RedShared<1> rs_;
   red_begin<1>(rs_);
   OPM_TILE(B, S, lt);
-  if (blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
+  if (FINAL && blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
   double acc[1] = {0.0};
   const double *__restrict__ b_in = S.b_in;
   const int32_t *__restrict__ perm = S.perm;
@@ -486,27 +513,17 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
   }
   double tot[1];
   if (red_end<1>(acc, rs_, S, lt, S.ntiles, tot) && (threadIdx.x & 31) == 0) {
-    DevState *st = S.st;
-    const double n0 = sqrt(tot[0]);
-    st->n0 = n0;
-    st->tol = S.rtol * n0;
-    st->maxit = S.maxit;
-    st->k = 1;
-    st->iters = 0;
-    st->half = 0;
-    st->error = 0;
-    st->relres = 0.0;
-    st->rho = tot[0];
-    st->rho_prev = 1.0;
-    st->alpha = 1.0;
-    st->omega = 1.0;
-    st->beta = tot[0];
-    if (st->ferror != 0) st->status = st->ferror;
-    else if (!isfinite(n0)) st->status = OPM_ERR_NONFINITE;
-    else if (n0 == 0.0) st->status = OPM_OK;
-    else if (S.maxit < 1) st->status = OPM_NOT_CONVERGED;
-    else st->status = kRunning;
+    if (FINAL) setup_scalars(S, S.st, tot[0]);
+    else S.st->bb = tot[0];
   }
+}
+
+// Joins the factorisation and k_setup<false>: the solve state of every
+// system, then the grid barrier's reset.
+__global__ void k_start(Batch B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) B.bar[0] = 0;
+  if (s < B.nsys) setup_scalars(B.sys[s], B.sys[s].st, B.sys[s].st->bb);
 }
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).

@@ -79,6 +79,7 @@ struct alignas(128) DevState {
   double n0, tol;
   double rhv, ss, ts, tt, rr, rhr;
   double relres;
+  double bb;       // ||b||^2 of the setup, when the state is set separately (k_start)
   int32_t status;  // kRunning or an opm_status
   int32_t k;       // current iteration, 1-based
   int32_t iters;

@@ -87,6 +87,7 @@ struct Runner {
   int64_t dev_bytes = 0;
   int grid_apply = 1, grid_factor = 1;
   cudaGraphExec_t solve_exec = nullptr, iter_exec = nullptr, factor_exec = nullptr;
+  cudaGraphExec_t fs_exec = nullptr;  // refactor + solve in one graph (setup beside the factorisation)
   int iter_launches = 0, factor_launches = 0;
   std::vector<cudaEvent_t> kev;  // profiling events, 6 per iteration of a chunk
   cudaEvent_t ev_done = nullptr;
@@ -383,11 +384,44 @@ opm_status add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraph
   return OPM_OK;
 }
 
+// Adds, after node dep of graph g: the device-side iteration loop (a
+// conditional while node whose body holds `chunk` iterations and the loop
+// condition), the wells' final term, the true residual and the results.
+opm_status add_solve_loop(Runner &R, cudaGraph_t g, cudaGraphNode_t dep, cudaStream_t cap) {
+  opm_status s = OPM_OK;
+  void *argsB[] = {&R.B};
+  cudaGraphNode_t n_while, n_finish, n_res;
+  cudaGraphConditionalHandle ch;
+  if (cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return OPM_ERR_CUDA;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = ch;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_while, g, &dep, nullptr, 1, &cp) != cudaSuccess) return OPM_ERR_CUDA;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return OPM_ERR_CUDA;
+  R.iter_launches = 0;
+  for (int it = 0; it < R.chunk; ++it) R.iter_launches = launch_iteration(R, cap, nullptr);
+  k_loop_cond<<<1, 256, 0, cap>>>(R.B, ch);
+  if (cudaStreamEndCapture(cap, &body) != cudaSuccess) return OPM_ERR_CUDA;
+  cudaGraphNode_t n_pre = n_while;
+  int which_x = 2;
+  void *argsW[] = {&R.B, &which_x};
+  if (R.has_wells && (s = add_kernel_node(g, &n_pre, &n_while, 1, (void *)k_wells, R.nsys, 256, argsW)) != OPM_OK)
+    return s;
+  if ((s = add_kernel_node(g, &n_finish, &n_pre, 1, (void *)k_finish, R.ntiles_s, 256, argsB)) != OPM_OK) return s;
+  void *argsR[] = {&R.B, &R.d_res};
+  return add_kernel_node(g, &n_res, &n_finish, 1, (void *)k_results, results_blocks(R), 128, argsR);
+}
+
 opm_status build_graphs(Runner &R) {
   cudaStream_t cap;
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   opm_status s = OPM_OK;
-  cudaGraph_t g = nullptr;
+  cudaGraph_t g = nullptr, fg = nullptr;
   // ---- factor graph
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     s = OPM_ERR_CUDA;
@@ -399,57 +433,39 @@ opm_status build_graphs(Runner &R) {
   }
   if (g) cudaGraphDestroy(g);
   g = nullptr;
-  // ---- solve graph with the device-side iteration loop
-  if (s == OPM_OK) do {
-      if (cudaGraphCreate(&g, 0) != cudaSuccess) {
-        s = OPM_ERR_CUDA;
-        break;
-      }
-      void *argsB[] = {&R.B};
-      cudaGraphNode_t n_setup, n_while, n_finish, n_res;
-      if ((s = add_kernel_node(g, &n_setup, nullptr, 0, (void *)k_setup, R.ntiles, 256, argsB)) != OPM_OK) break;
-      cudaGraphConditionalHandle ch;
-      if (cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-        s = OPM_ERR_CUDA;
-        break;
-      }
-      cudaGraphNodeParams cp = {};
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = ch;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      if (cudaGraphAddNode(&n_while, g, &n_setup, nullptr, 1, &cp) != cudaSuccess) {
-        s = OPM_ERR_CUDA;
-        break;
-      }
-      cudaGraph_t body = cp.conditional.phGraph_out[0];
-      if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
-          cudaSuccess) {
-        s = OPM_ERR_CUDA;
-        break;
-      }
-      R.iter_launches = 0;
-      for (int it = 0; it < R.chunk; ++it) R.iter_launches = launch_iteration(R, cap, nullptr);
-      k_loop_cond<<<1, 256, 0, cap>>>(R.B, ch);
-      if (cudaStreamEndCapture(cap, &body) != cudaSuccess) {
-        s = OPM_ERR_CUDA;
-        break;
-      }
-      cudaGraphNode_t n_pre = n_while;
-      int which_x = 2;
-      void *argsW[] = {&R.B, &which_x};
-      if (R.has_wells &&
-          (s = add_kernel_node(g, &n_pre, &n_while, 1, (void *)k_wells, R.nsys, 256, argsW)) != OPM_OK)
-        break;
-      if ((s = add_kernel_node(g, &n_finish, &n_pre, 1, (void *)k_finish, R.ntiles_s, 256, argsB)) != OPM_OK)
-        break;
-      void *argsR[] = {&R.B, &R.d_res};
-      if ((s = add_kernel_node(g, &n_res, &n_finish, 1, (void *)k_results, results_blocks(R), 128, argsR)) !=
-          OPM_OK)
-        break;
-      if (cudaGraphInstantiate(&R.solve_exec, g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
-    } while (0);
+  void *argsB[] = {&R.B};
+  // ---- solve graph: setup, then the device-side iteration loop
+  if (s == OPM_OK) {
+    cudaGraphNode_t n_setup;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+    if (s == OPM_OK) s = add_kernel_node(g, &n_setup, nullptr, 0, (void *)k_setup<true>, R.ntiles, 256, argsB);
+    if (s == OPM_OK) s = add_solve_loop(R, g, n_setup, cap);
+    if (s == OPM_OK && cudaGraphInstantiate(&R.solve_exec, g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+  }
   if (g) cudaGraphDestroy(g);
+  g = nullptr;
+  // ---- refactor + solve graph: the factorisation and the setup's vector
+  // work run as independent branches (the setup needs only b), joined by
+  // k_start, which applies the factorisation's outcome to the solve state.
+  // Not with cooperative launches, which must own the whole device.
+  if (s == OPM_OK && !R.cooperative) {
+    cudaGraphNode_t n_fac, n_setup, n_start;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      s = OPM_ERR_CUDA;
+    } else {
+      launch_factor_seq(R, cap);
+      if (cudaStreamEndCapture(cap, &fg) != cudaSuccess) s = OPM_ERR_CUDA;
+    }
+    if (s == OPM_OK && cudaGraphCreate(&g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+    if (s == OPM_OK && cudaGraphAddChildGraphNode(&n_fac, g, nullptr, 0, fg) != cudaSuccess) s = OPM_ERR_CUDA;
+    if (s == OPM_OK) s = add_kernel_node(g, &n_setup, nullptr, 0, (void *)k_setup<false>, R.ntiles, 256, argsB);
+    cudaGraphNode_t deps[2] = {n_fac, n_setup};
+    if (s == OPM_OK) s = add_kernel_node(g, &n_start, deps, 2, (void *)k_start, results_blocks(R), 128, argsB);
+    if (s == OPM_OK) s = add_solve_loop(R, g, n_start, cap);
+    if (s == OPM_OK && cudaGraphInstantiate(&R.fs_exec, g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (fg) cudaGraphDestroy(fg);
   g = nullptr;
   // ---- profiled iteration graph
   if (s == OPM_OK && R.profile) {
@@ -477,6 +493,7 @@ void runner_destroy(Runner *R) {
   if (R->solve_exec) cudaGraphExecDestroy(R->solve_exec);
   if (R->iter_exec) cudaGraphExecDestroy(R->iter_exec);
   if (R->factor_exec) cudaGraphExecDestroy(R->factor_exec);
+  if (R->fs_exec) cudaGraphExecDestroy(R->fs_exec);
   for (void *p : R->allocs) cudaFree(p);
   if (R->h_sys) cudaFreeHost(R->h_sys);
   if (R->h_res) cudaFreeHost(R->h_res);
@@ -661,7 +678,8 @@ opm_status runner_sync_wells(Runner &R) {
   if (R.solve_exec) cudaGraphExecDestroy(R.solve_exec);
   if (R.iter_exec) cudaGraphExecDestroy(R.iter_exec);
   if (R.factor_exec) cudaGraphExecDestroy(R.factor_exec);
-  R.solve_exec = R.iter_exec = R.factor_exec = nullptr;
+  if (R.fs_exec) cudaGraphExecDestroy(R.fs_exec);
+  R.solve_exec = R.iter_exec = R.factor_exec = R.fs_exec = nullptr;
   R.has_wells = any;
   return build_graphs(R);
 }
@@ -683,8 +701,12 @@ opm_status runner_pull_results(Runner &R) {
 opm_status runner_enqueue(Runner &R, bool factor, bool solve) {
   opm_status s = runner_push(R);
   if (s != OPM_OK) return s;
-  if (factor) CK(cudaGraphLaunch(R.factor_exec, R.stream));
-  if (solve) CK(cudaGraphLaunch(R.solve_exec, R.stream));
+  if (factor && solve && R.fs_exec) {
+    CK(cudaGraphLaunch(R.fs_exec, R.stream));
+  } else {
+    if (factor) CK(cudaGraphLaunch(R.factor_exec, R.stream));
+    if (solve) CK(cudaGraphLaunch(R.solve_exec, R.stream));
+  }
   if ((s = runner_pull_results(R)) != OPM_OK) return s;
   CK(cudaEventRecord(R.ev_done, R.stream));
   return OPM_OK;
@@ -709,7 +731,7 @@ opm_status runner_solve_profiled(Runner &R, opm_timing &t) {
   if (s != OPM_OK) return s;
   cudaEvent_t e0 = R.kev[0], e1 = R.kev[1];
   CK(cudaEventRecord(e0, R.stream));
-  k_setup<<<R.ntiles, 256, 0, R.stream>>>(R.B);
+  k_setup<true><<<R.ntiles, 256, 0, R.stream>>>(R.B);
   CK(cudaEventRecord(e1, R.stream));
   CK(cudaStreamSynchronize(R.stream));
   add_kernel_time(t, OPM_KERNEL_SETUP, e0, e1);
