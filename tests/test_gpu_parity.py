@@ -353,3 +353,43 @@ def test_bench_launch_configuration_full_size(c3):
     z_ref = np.empty_like(zp)
     z_ref.reshape(-1, 3)[perm] = zp.reshape(-1, 3)
     np.testing.assert_allclose(z, z_ref, rtol=1e-11, atol=1e-12 * np.abs(z_ref).max())
+
+
+@pytest.mark.parametrize("schedule", ["natural", "level", "colour_kempe"])
+def test_empty_system(schedule):
+    """nb = 0: every entry point succeeds and does nothing; the empty handle
+    reports empty info and an empty permutation."""
+    rowptr = np.zeros(1, dtype=np.int32)
+    colidx = np.zeros(0, dtype=np.int32)
+    vals = np.zeros((0, 9))
+    with opm.Solver(0, rowptr, colidx, vals, schedule=schedule) as sv:
+        assert sv.status == opm.OPM_OK
+        assert sv.factor(vals) == opm.OPM_OK
+        x, st, it, rr = sv.solve(np.zeros(0), rtol=1e-3)
+        assert (st, it, rr) == (opm.OPM_OK, 0, 0.0) and x.shape == (0,)
+        assert sv.spmv(np.zeros(0)).shape == (0,)
+        assert sv.ilu_apply(np.zeros(0)).shape == (0,)
+        x, st, it, rr = sv.gmres(np.zeros(0), rtol=1e-3)
+        assert st == opm.OPM_OK and it == 0
+        assert sv.info().nb == 0
+        assert len(sv.permutation()) == 0
+        # an empty system has nothing to launch or to batch
+        with pytest.raises(opm.OpmError):
+            sv.launch(vals, np.zeros(0), np.zeros(0))
+        with pytest.raises(opm.OpmError):
+            opm.Batch([sv.h])
+
+
+def test_degenerate_single_cell_and_identity_blocks():
+    """One cell, and a block-diagonal system of identity blocks: ILU0 is the
+    exact inverse, BiCGStab stops at the first half step with x = alpha b,
+    alpha = (r^,r)/(r^,v) = 1 up to the two sums' rounding orders."""
+    for nb in (1, 257):
+        rowptr = np.arange(nb + 1, dtype=np.int32)
+        colidx = np.arange(nb, dtype=np.int32)
+        vals = np.tile(np.eye(3).ravel(), (nb, 1))
+        b = synth.uniform(synth.stream_key(3, 7), np.arange(3 * nb, dtype=np.uint64), -1, 1)
+        with opm.Solver(nb, rowptr, colidx, vals) as sv:
+            x, st, it, rr = sv.solve(b, rtol=1e-10)
+        assert st == 0 and it == 1 and rr <= 1e-15
+        np.testing.assert_allclose(x, b, rtol=1e-15, atol=0)
