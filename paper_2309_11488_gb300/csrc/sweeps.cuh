@@ -258,7 +258,7 @@ __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
 // throughput form for large phases (256 threads); PRE > 0: latency form for
 // small phases (64 threads, so the few warps spread over all SMs).
 template <typename TF, int MODE, int PRE>
-__global__ void __launch_bounds__(PRE > 0 ? 64 : 256, PRE > 0 ? 1 : 5) k_fwd_phase(Batch B, int c) {
+__global__ void __launch_bounds__(PRE > 0 ? 64 : 256, PRE > 0 ? 1 : 4) k_fwd_phase(Batch B, int c) {
   pdl_trigger();
   if (PRE == 0) pdl_wait();
   const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(PRE > 0 ? 64 : 256, PRE > 0 ? 1 : 5) k_fwd_pha
 }
 
 template <typename TF, int MODE, int PRE>
-__global__ void __launch_bounds__(PRE > 0 ? 64 : 256) k_bwd_phase(Batch B, int c) {
+__global__ void __launch_bounds__(PRE > 0 ? 64 : 256, PRE > 0 ? 1 : 4) k_bwd_phase(Batch B, int c) {
   pdl_trigger();
   if (PRE == 0) pdl_wait();
   const int e = __ldg(B.bwd_ptr + c) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
