@@ -195,6 +195,29 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
                                  opm_handle *out);
 
 /*
+ * The symbolic analysis alone, on the host (no device, no handle): the same
+ * validation, schedule, permutation and phases opm_bsr_create /
+ * opm_bsr_create_jacobi compute (Section 4.4), for inspecting a schedule or
+ * choosing one without a GPU.
+ *   rowptr, colidx (and part, which may be NULL) must be host memory.
+ *   schedule: OPM_SCHED_*; perm (may be NULL): nb entries, perm[new] = old.
+ *   info (may be NULL) receives the counts.
+ *   Returns OPM_OK or the pattern error of opm_bsr_create (the offending row
+ *   via opm_last_error_row(NULL)); OPM_ERR_ARG on a bad argument.
+ */
+typedef struct opm_analysis_info {
+  int32_t schedule;    /* schedule used (never OPM_SCHED_AUTO)               */
+  int32_t nsets;       /* levels or colours (1 for natural order)            */
+  int32_t nphases;     /* runs of mutually independent rows the sweeps walk  */
+  int32_t reserved;
+  int64_t nnzb_kept;   /* blocks in the preconditioner's pattern             */
+  int64_t nnzb_lower;  /* strictly lower kept blocks of the permuted matrix  */
+  int64_t nnzb_upper;
+} opm_analysis_info;
+opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                           int32_t schedule, int32_t *perm, opm_analysis_info *info);
+
+/*
  * Restarted GMRES(m) (Section 2 names restarted GMRES as OPM's other Krylov
  * solver; method of Saad & Schultz 1986), with the handle's ILU0 (or
  * block-Jacobi ILU0) as right preconditioner, x0 = 0.  Arnoldi with

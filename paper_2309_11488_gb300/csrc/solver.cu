@@ -1371,6 +1371,29 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
   return create_impl(nb, rowptr, colidx, vals, part, opt, out);
 }
 
+opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                           int32_t schedule, int32_t *perm, opm_analysis_info *info) {
+  t_create_err_row = -1;
+  if (nb < 0 || !rowptr || (nb > 0 && !colidx) || schedule < OPM_SCHED_AUTO || schedule > OPM_SCHED_COLOUR_KEMPE)
+    return OPM_ERR_ARG;
+  Analysis an;
+  int32_t err_row = -1;
+  const opm_status s = analyse(nb, rowptr, colidx, part, schedule, an, &err_row);
+  t_create_err_row = err_row;
+  if (s != OPM_OK) return s;
+  if (perm && nb > 0) memcpy(perm, an.perm.data(), sizeof(int32_t) * (size_t)nb);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->schedule = an.schedule;
+    info->nsets = an.nsets;
+    info->nphases = nb > 0 ? (int32_t)an.phase_ptr.size() - 1 : 0;
+    info->nnzb_kept = an.nnzb_kept;
+    info->nnzb_lower = an.nnz_l;
+    info->nnzb_upper = an.nnz_u;
+  }
+  return OPM_OK;
+}
+
 opm_status opm_ilu0_factor(opm_handle h, const double *vals) {
   if (!h || h->async_pending) return OPM_ERR_ARG;
   return factor_impl(h, vals);

@@ -40,7 +40,8 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve",
+           "opm_bsr_analyse"]
 
 
 class opm_options(ctypes.Structure):
@@ -69,6 +70,12 @@ class opm_info(ctypes.Structure):
                 ("nsets", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
                 ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("nphases", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class opm_analysis_info(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("nsets", ctypes.c_int32), ("nphases", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("nnzb_kept", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
+                ("nnzb_upper", ctypes.c_int64)]
 
 
 KERNELS = ["factor", "apply", "spmv", "update", "setup", "finish"]
@@ -100,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.opm_bsr_create.argtypes = [i32, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
         L.opm_bsr_create_jacobi.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
         L.opm_bsr_create_jacobi.restype = i32
+        L.opm_bsr_analyse.argtypes = [i32, vp, vp, vp, i32, vp, ctypes.POINTER(opm_analysis_info)]
+        L.opm_bsr_analyse.restype = i32
         L.opm_set_wells.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.opm_set_wells.restype = i32
         L.opm_gmres_solve.argtypes = [vp, vp, vp, f64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(f64)]
@@ -228,6 +237,21 @@ def opm_bsr_create(nb, rowptr, colidx, vals, options: opm_options | None = None,
             opm_destroy(h)
         raise OpmError(st, "opm_bsr_create")
     return st, h
+
+
+def opm_bsr_analyse(nb, rowptr, colidx, schedule="auto", part=None):
+    """Host-only symbolic analysis: returns (status, perm, opm_analysis_info)."""
+    if isinstance(schedule, str):
+        schedule = SCHEDULES[schedule]
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    pt = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
+    perm = np.empty(max(int(nb), 0), dtype=np.int32)
+    info = opm_analysis_info()
+    st = lib().opm_bsr_analyse(int(nb), rowptr.ctypes.data, colidx.ctypes.data if colidx.size else None,
+                               pt.ctypes.data if pt is not None and pt.size else None, int(schedule),
+                               perm.ctypes.data if perm.size else None, ctypes.byref(info))
+    return st, perm, info
 
 
 def opm_ilu0_factor(h: Handle, vals=None) -> int:

@@ -110,7 +110,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no gcc")
     checks = {"opm_options": opm.opm_options, "opm_info": opm.opm_info, "opm_timing": opm.opm_timing,
-              "opm_tune_entry": opm.opm_tune_entry, "opm_tune_report": opm.opm_tune_report}
+              "opm_tune_entry": opm.opm_tune_entry, "opm_tune_report": opm.opm_tune_report,
+              "opm_analysis_info": opm.opm_analysis_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "opm_bsr.h"', 'int main(void) {']
     for cname, cls in checks.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -150,3 +151,60 @@ def test_jacobi_create_needs_a_partition():
     st = opm.lib().opm_bsr_create_jacobi(s.nb, s.rowptr.ctypes.data, s.colidx.ctypes.data, s.vals.ctypes.data,
                                          None, None, ctypes.byref(out))
     assert st == opm.OPM_ERR_ARG and not out.value
+
+
+# ------------------------------------------------- host analysis vs the oracle
+
+ANALYSE_CASES = {
+    "c1": synth.config1,
+    "c2": synth.config2,
+    "ragged33": lambda: synth.random_pattern_system(33, 3, 41),
+    "long_rows": lambda: synth.random_pattern_system(70, 20, 42),
+    "dense40": lambda: synth.random_pattern_system(40, 0, 43, dense=True),
+    "chain": lambda: synth.chain_system(100),
+    "tree": lambda: synth.tree_system(300, 44),
+}
+
+
+@pytest.mark.parametrize("schedule", ["natural", "level", "colour", "colour_sl", "colour_kempe"])
+@pytest.mark.parametrize("name", list(ANALYSE_CASES))
+def test_library_analysis_matches_the_oracle_schedule(name, schedule):
+    """The library's host analysis (no GPU) orders the rows exactly as the
+    oracle's independent implementation of the same rules, with the same
+    number of levels or colours."""
+    import oracle as O
+    s = ANALYSE_CASES[name]()
+    st, perm, info = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule)
+    assert st == opm.OPM_OK
+    ref, nsets = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
+    np.testing.assert_array_equal(perm, ref)
+    assert info.nsets == nsets and info.schedule == opm.SCHEDULES[schedule]
+    assert info.nnzb_kept == s.nnzb and info.nnzb_lower + info.nnzb_upper == s.nnzb - s.nb
+    if schedule != "natural":
+        assert info.nphases == nsets
+
+
+@pytest.mark.parametrize("schedule", ["level", "colour_kempe"])
+def test_library_analysis_of_a_block_jacobi_pattern_matches_the_oracle(schedule):
+    import oracle as O
+    s = synth.config2()
+    part = synth.partition_grid(s, 12)
+    st, perm, info = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule, part=part)
+    assert st == opm.OPM_OK
+    jrp, jci = O.jacobi_pattern(s.nb, s.rowptr, s.colidx, s.vals, part)[:2]
+    ref, nsets = O.schedule_perm(s.nb, jrp, jci, schedule)
+    np.testing.assert_array_equal(perm, ref)
+    assert info.nsets == nsets and info.nnzb_kept == int(jrp[-1])
+
+
+def test_library_analysis_reports_pattern_errors():
+    s = synth.config1()
+    ci = s.colidx.copy()
+    a = s.rowptr[3]
+    ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    st, perm, info = opm.opm_bsr_analyse(s.nb, s.rowptr, ci, "colour")
+    assert st == opm.OPM_ERR_PATTERN and opm.opm_last_error_row(None) == 3
+    st, _, _ = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, 99)
+    assert st == opm.OPM_ERR_ARG
+    st, perm, info = opm.opm_bsr_analyse(0, np.zeros(1, np.int32), np.zeros(0, np.int32), "colour")
+    assert st == opm.OPM_OK and perm.size == 0 and info.nsets == 0
