@@ -216,7 +216,7 @@ __device__ __forceinline__ double *jac_z(const Sys &S, int t, int T) {
 // Forward sweep t of T: y_t = h - L y_{t-1} with y_0 = h.  The last sweep
 // also starts the backward iteration, z_0 = inv(U_ii) y_T.
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_jac_fwd(Batch B, int t, int T) {
+__global__ void __launch_bounds__(256, 4) k_jac_fwd(Batch B, int t, int T) {
   pdl_enter();
   const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= B.nall) return;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_jac_fwd(Batch B, int t, int T) {
 
 // Backward sweep t of T: z_t = inv(U_ii)(y_T - U_off z_{t-1}).
 template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_jac_bwd(Batch B, int t, int T) {
+__global__ void __launch_bounds__(256, 4) k_jac_bwd(Batch B, int t, int T) {
   pdl_enter();
   const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= B.nall) return;
