@@ -281,7 +281,8 @@ int launch_apply_t(Runner &R, cudaStream_t st) {
   for (int c = 0; c < R.nphases; ++c) {
     const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
     if (cnt == 0) continue;
-    launch_sweep_phase<TF, MODE, true>(R, st, c, cnt);
+    if (c == 0) launch_pdl(k_fwd_first<TF, MODE>, blocks8(cnt), 256, st, R.B);  // no L blocks in phase 0
+    else launch_sweep_phase<TF, MODE, true>(R, st, c, cnt);
     ++n;
   }
   for (int c = R.nphases - 1; c >= 0; --c) {

@@ -254,6 +254,59 @@ __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
   }
 }
 
+// The forward step of the first phase, whose rows have no L blocks (no
+// earlier row precedes them): y_i = rhs_i, z_i = inv(U_ii) y_i for rows
+// without U blocks.  The same expressions as fwd_rows, without its walk of
+// the L blocks, and with the register budget of a streaming kernel (eight
+// CTAs per SM) so that the many short warps overlap their few loads.
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(256, 8) k_fwd_first(Batch B) {
+  pdl_trigger();
+  const int e = __ldg(B.fwd_ptr) + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (e >= __ldg(B.fwd_ptr + 1)) return;
+  const int4 E = B.ent[e];
+  const Sys &S = B.sys[E.x];
+  const int lane = threadIdx.x & 31;
+  const int i = E.y * 32 + lane;
+  if (i < E.z || i >= E.w) return;
+  const uint2 M = __ldg(S.sl_mask + E.y);
+  const bool eager = (M.x >> lane) & 1u, ystore = (M.y >> lane) & 1u;
+  pdl_wait();
+  const DevState *st = S.st;
+  if (MODE != kModePlain && !running(st)) return;
+  const double *rin = (MODE == kModePlain) ? S.w : S.r;
+  double *hout = (MODE == kModeP) ? S.p : S.s;
+  const Vec3<double> rr = load3cg(rin + 3ll * i);
+  double h0 = rr.c0, h1 = rr.c1, h2 = rr.c2;
+  if (MODE != kModePlain) {
+    const Vec3<double> vo = load3cg(S.v + 3ll * i);
+    if (MODE == kModeP) {
+      const double c1 = st->beta, c2 = st->omega;
+      const Vec3<double> po = load3cg(hout + 3ll * i);
+      h0 = fma(c1, fma(-c2, vo.c0, po.c0), rr.c0);
+      h1 = fma(c1, fma(-c2, vo.c1, po.c1), rr.c1);
+      h2 = fma(c1, fma(-c2, vo.c2, po.c2), rr.c2);
+    } else {
+      const double c1 = st->alpha;
+      h0 = fma(-c1, vo.c0, rr.c0);
+      h1 = fma(-c1, vo.c1, rr.c1);
+      h2 = fma(-c1, vo.c2, rr.c2);
+    }
+    double *ho = hout + 3ll * i;
+    ho[0] = h0; ho[1] = h1; ho[2] = h2;
+  }
+  const TF a0 = (TF)h0, a1 = (TF)h1, a2 = (TF)h2;
+  if (eager) {
+    TF d[9];
+    load_dinv<TF>(static_cast<const TF *>(S.lu) + S.d_off + (int64_t)kSliceVals * E.y + lane, d);
+    store_dinv_product<TF>(sweep_out<MODE>(S) + 3ll * i, d, a0, a1, a2);
+  }
+  if (ystore) {
+    TF *yi = static_cast<TF *>(S.y) + 3ll * i;
+    yi[0] = a0; yi[1] = a1; yi[2] = a2;
+  }
+}
+
 // One launch per phase, one sweep entry (a 32-row slice) per warp.  PRE = 0:
 // throughput form for large phases (256 threads); PRE > 0: latency form for
 // small phases (64 threads, so the few warps spread over all SMs).
