@@ -35,9 +35,15 @@ sys.path.insert(0, ROOT)
 METRIC = "ILU0-BiCGStab solves/s & HBM roofline frac; FP32-ILU vs FP64; p50/p99 latency"
 UNIT = "solves/s"
 RTOL = 1e-3
-WORKLOAD = ("C3: 100^3 grid, 5% inactive cells, 1% fault connections, lognormal perm sigma=2; "
-            "949,871 cells, 6,328,435 3x3 blocks; per step: value permutation + ILU0 factorisation + "
-            "BiCGStab to rtol 1e-3 + true residual")
+
+
+def workload(grid, nb, nnzb):
+    """The workload's name: the grid it was generated on and its actual sizes
+    (the default 100^3 grid gives the 949,871-cell, 6,328,435-block system)."""
+    name = "C3: " if grid == 100 else ""
+    return (f"{name}{grid}^3 grid, 5% inactive cells, 1% fault connections, lognormal perm sigma=2; "
+            f"{nb:,} cells, {nnzb:,} 3x3 blocks; per step: value permutation + ILU0 factorisation + "
+            f"BiCGStab to rtol 1e-3 + true residual")
 
 
 def parse():
@@ -394,9 +400,11 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded generator shaped like the paper's 1M-cell model)",
-        "config": {"workload": WORKLOAD, "options": r64["options"], "nsets": r64["info"].nsets,
+        "config": {"workload": workload(args.grid, s.nb, len(s.colidx)), "options": r64["options"], "nsets": r64["info"].nsets,
                    "precision": "fp64 factors and Krylov", "rtol": RTOL, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (A values 456 MB, factors 456 MB)"},
+                   "l2": (f"inputs larger than L2 (A values {len(s.colidx) * 72 / 1e6:.0f} MB, factors "
+                          f"{len(s.colidx) * 72 / 1e6:.0f} MB)" if len(s.colidx) * 72 > 129e6 else
+                          "inputs smaller than L2: not flushed")},
         "iters": r64["iters"], "relres": r64["relres"], "status": [r64["st"], r64["st2"]],
         "x_err_vs_x_true": r64["err"],
         "roofline": roofline(r64, "fp64"),
@@ -767,7 +775,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": n,
             "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / n, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "schedule": "colour_kempe", "rtol": RTOL},
+            "config": {"workload": workload(args.grid, s.nb, len(s.colidx)), "schedule": "colour_kempe", "rtol": RTOL},
             "iters": res.iters, "relres": res.relres,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

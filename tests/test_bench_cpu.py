@@ -1,0 +1,70 @@
+"""The benchmark's JSON contract, checked on the CPU: the reference arm (the
+oracle on the host cores) on a small grid prints one JSON line with every
+key the contract names, and the algorithmic-work helpers count what they
+say on a hand-countable system."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    argv, sys.argv = sys.argv, ["bench.py"]
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--grid", "12", "--steps", "4",
+                          "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 4 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["iters"] >= 1 and d["relres"] <= 1e-3 * (1 + 1e-6)
+    assert "workload" in d["config"]
+
+
+class _Info:
+    def __init__(self, nb, nnzb, nl, nu):
+        self.nb, self.nnzb, self.nnzb_lower, self.nnzb_upper = nb, nnzb, nl, nu
+
+
+def test_work_counts_on_a_hand_counted_system():
+    """Two cells joined both ways: 4 blocks, 1 lower, 1 upper."""
+    b = _bench_module()
+    info = _Info(2, 4, 1, 1)
+    # application: 9 values x 8 B per block, 4 B per off-diagonal column,
+    # two row-pointer arrays of n + 1, five 24-B vector passes, y written and
+    # read back (2 x 3 values x 8 B) per row
+    assert b.algorithmic_apply_bytes(info, False) == 4 * 72 + 4 * 2 + 2 * 4 * 3 + 5 * 24 * 2 + 2 * 3 * 8 * 2
+    assert b.algorithmic_apply_bytes(info, True) == 4 * 36 + 4 * 2 + 2 * 4 * 3 + 5 * 24 * 2 + 2 * 3 * 4 * 2
+    nbytes, fma = b.iteration_work(info, False)
+    assert nbytes == 2 * (76 * 4 + 4 * 2) + 2 * (76 * 4 + 4 * 2) + 27 * 24 * 2
+    assert fma == 18 * 4 + 18 * 4 + 36 * 2
+    nbytes32, fma32 = b.iteration_work(info, True)
+    assert nbytes32 < nbytes and fma32 == 18 * 4 + 36 * 2
+    jb, jf = b.jacobi_apply_work(info, 1, False)
+    assert jf == int(4.5 * 2 + 9 * 1 * 2 + 9 * 2 * 2) and jb > b.algorithmic_apply_bytes(info, False) // 2
+
+
+def test_fp64_fma_peak_is_the_documented_lane_rate():
+    b = _bench_module()
+    assert np.isclose(b.FP64_FMA_PEAK, 2 * 152 * 2.07e9)
