@@ -1023,13 +1023,12 @@ opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol
     }
     h->gm_m = m;
   }
-  if (!h->gm_part) {
-    if (cudaMalloc(&h->gm_part, sizeof(double) * (size_t)ntile * kGmMaxVec) != cudaSuccess ||
-        cudaMalloc(&h->gm_sc, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess ||
-        cudaMallocHost(&h->gm_host, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess) {
-      cudaGetLastError();
-      return OPM_ERR_OOM;
-    }
+  // each buffer on its own: one that failed before is retried, none is used unallocated
+  if ((!h->gm_part && cudaMalloc(&h->gm_part, sizeof(double) * (size_t)ntile * kGmMaxVec) != cudaSuccess) ||
+      (!h->gm_sc && cudaMalloc(&h->gm_sc, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess) ||
+      (!h->gm_host && cudaMallocHost(&h->gm_host, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess)) {
+    cudaGetLastError();
+    return OPM_ERR_OOM;
   }
   if ((s = runner_push(R)) != OPM_OK) return s;
   const Sys &S = h->sys;
