@@ -225,6 +225,27 @@ def make_system(grid):
     return synth.config3(grid)
 
 
+def rank_sync(dist, sync_device, device):
+    """The replicas' timing plumbing: barrier() waits for every rank and then
+    for this rank's device; max_over_ranks(v) is the largest v over the
+    ranks (the slowest replica's time), reduced on `device` ("cuda" with
+    NCCL, "cpu" with gloo).  Without a process group both act on this rank
+    alone."""
+    def barrier():
+        if dist:
+            dist.barrier()
+        sync_device()
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        import torch
+        tt = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+    return barrier, max_over_ranks
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2309_11488_gb300 import opm
@@ -236,10 +257,7 @@ def run_ours(args, rank, world, dist):
     rp, ci, vals = dev(s.rowptr), dev(s.colidx), dev(s.vals)
     xt = dev(s.x_true)
 
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier, max_over_ranks = rank_sync(dist, torch.cuda.synchronize, "cuda")
 
     def tuned(precision):
         """Launch options for this workload: the autotuner's choice, or the
@@ -304,13 +322,6 @@ def run_ours(args, rank, world, dist):
             t = sp.timing()
         return sv, dict(ms=ms, timing=t, launches=launches, info=info, clocks=clk.summary(), err=err, options=kw,
                         autotune=tune, **stat)
-
-    def max_over_ranks(v):
-        if not dist:
-            return v
-        tt = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
 
     sv64, r64 = measure("fp64")
     sv32, r32 = measure("fp32")
