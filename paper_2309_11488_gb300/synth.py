@@ -50,7 +50,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 SEED_BASE = 2309114880
 
 # stream identifiers (any distinct constants)
-_S_PERM, _S_LAYER, _S_MASK, _S_FAULT, _S_M, _S_ACC, _S_DNOISE, _S_X, _S_DIMS, _S_SCALE, _S_WELL = range(1, 12)
+_S_PERM, _S_LAYER, _S_MASK, _S_FAULT, _S_M, _S_ACC, _S_DNOISE, _S_X, _S_DIMS, _S_SCALE, _S_WELL, _S_DROP = range(1, 13)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -402,7 +402,7 @@ def chain_system(nb, seed=SEED_BASE + 17) -> BsrSystem:
                        meta={"config": f"chain {nb}"})
 
 
-def random_pattern_system(nb, extra_per_row, seed, symmetric=True, dense=False) -> BsrSystem:
+def random_pattern_system(nb, extra_per_row, seed, dense=False) -> BsrSystem:
     """Random pattern with diagonal dominance built like the grid recipe.
     ``dense=True`` gives every block present (all pairs connected)."""
     key = stream_key(seed, _S_FAULT)
@@ -422,6 +422,19 @@ def random_pattern_system(nb, extra_per_row, seed, symmetric=True, dense=False) 
         nb, a.astype(np.int64), b.astype(np.int64), t, stream_key(seed, _S_M),
         stream_key(seed, _S_ACC), stream_key(seed, _S_DNOISE), stream_key(seed, _S_X))
     return BsrSystem(nb, rowptr, colidx, vals, x_true, {"config": f"random nb={nb}", "seed": seed})
+
+
+def one_way_system(base: BsrSystem, frac, seed) -> BsrSystem:
+    """base with a seeded fraction of its off-diagonal blocks removed, each
+    removal one way only (block (a, b) goes while (b, a) may stay): a
+    non-symmetric pattern.  Only off-diagonal blocks go, so every row stays
+    diagonally dominant; x_true is kept."""
+    u = uniform(stream_key(seed, _S_DROP), np.arange(base.nnzb, dtype=np.uint64))
+    rows = np.repeat(np.arange(base.nb), np.diff(base.rowptr))
+    keep = (rows == base.colidx) | (u >= frac)
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=base.nb))]).astype(np.int32)
+    meta = dict(base.meta, one_way_drop=frac, drop_seed=seed)
+    return BsrSystem(base.nb, rowptr, base.colidx[keep].copy(), base.vals[keep].copy(), base.x_true.copy(), meta)
 
 
 def tree_system(nb, seed) -> BsrSystem:

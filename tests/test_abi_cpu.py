@@ -210,16 +210,6 @@ def test_library_analysis_reports_pattern_errors():
     assert st == opm.OPM_OK and perm.size == 0 and info.nsets == 0
 
 
-def _drop_off_diagonal(s, frac, seed):
-    """The pattern of s with a seeded fraction of its off-diagonal blocks
-    removed, each one way only: a non-symmetric pattern, diagonal kept."""
-    rng = np.random.default_rng(seed)
-    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
-    keep = (rows == s.colidx) | (rng.random(s.colidx.size) >= frac)
-    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=s.nb))]).astype(np.int32)
-    return rowptr, s.colidx[keep].astype(np.int32)
-
-
 SWEEP = [(nb, extra, frac) for nb in (1, 2, 5, 31, 32, 33, 64, 97, 200) for extra, frac in ((0, 0.0), (1, 0.5),
                                                                                        (3, 0.0), (8, 0.7))]
 
@@ -229,8 +219,8 @@ def test_library_analysis_matches_the_oracle_on_random_patterns(nb, extra, frac)
     """Seeded random patterns, symmetric and not, sized around the 32-row
     slices: every schedule's permutation and set count equal the oracle's."""
     import oracle as O
-    s = synth.random_pattern_system(nb, extra, 1000 + nb * 10 + extra)
-    rowptr, colidx = _drop_off_diagonal(s, frac, nb + extra)
+    s = synth.one_way_system(synth.random_pattern_system(nb, extra, 1000 + nb * 10 + extra), frac, nb + extra)
+    rowptr, colidx = s.rowptr, s.colidx
     for schedule in ("natural", "level", "colour", "colour_sl", "colour_kempe"):
         st, perm, info = opm.opm_bsr_analyse(nb, rowptr, colidx, schedule)
         assert st == opm.OPM_OK, schedule

@@ -45,6 +45,9 @@ SMALL = {
     "dense40": lambda: synth.random_pattern_system(40, 0, 43, dense=True),
     "chain": lambda: synth.chain_system(100),
     "tree": lambda: synth.tree_system(300, 44),
+    # non-symmetric patterns: L and U are not each other's transpose
+    "one_way200": lambda: synth.one_way_system(synth.random_pattern_system(200, 4, 45), 0.5, 46),
+    "one_way_c1": lambda: synth.one_way_system(synth.config1(), 0.3, 47),
 }
 
 
@@ -126,7 +129,7 @@ def test_factors_config3_full_size(c3, schedule):
 
 
 @pytest.mark.parametrize("sweep", SWEEPS)
-@pytest.mark.parametrize("name", ["c1", "ragged33", "long_rows", "tree"])
+@pytest.mark.parametrize("name", ["c1", "ragged33", "long_rows", "tree", "one_way200"])
 @pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
 def test_ilu_apply(name, schedule, sweep):
     s = SMALL[name]()

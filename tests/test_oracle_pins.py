@@ -155,7 +155,8 @@ def test_no_fill_patterns_exact_and_one_iteration(maker):
     np.testing.assert_allclose(res.x, s.x_true, rtol=1e-10, atol=1e-11)
 
 
-@pytest.mark.parametrize("maker", [synth.config1, lambda: synth.random_pattern_system(60, 4, 21, dense=False)])
+@pytest.mark.parametrize("maker", [synth.config1, lambda: synth.random_pattern_system(60, 4, 21, dense=False),
+                                   lambda: synth.one_way_system(synth.random_pattern_system(60, 6, 22), 0.5, 23)])
 def test_ilu0_defining_identity_on_pattern(maker):
     s = maker()
     fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
@@ -307,7 +308,8 @@ def _edges(s):
     return rows[off], s.colidx[off]
 
 
-@pytest.mark.parametrize("maker", [synth.config2, lambda: synth.random_pattern_system(300, 3, 5)])
+@pytest.mark.parametrize("maker", [synth.config2, lambda: synth.random_pattern_system(300, 3, 5),
+                                   lambda: synth.one_way_system(synth.random_pattern_system(300, 4, 6), 0.5, 7)])
 def test_schedule_sets_are_independent_and_minimal(maker):
     s = maker()
     a, b = _edges(s)
@@ -607,6 +609,26 @@ def test_generator_rows_are_diagonally_dominant_up_to_noise():
     d = v[diag]
     for r in range(3):
         assert np.all(d[:, r, r] >= off_sum[:, r] + 0.1 - 0.05)
+
+
+def test_one_way_generator_drops_blocks_one_way_and_keeps_the_rest():
+    """The non-symmetric stand-in: every kept block has A's value, the
+    diagonal stays, some blocks lose their mirror, and a fraction near the
+    requested one goes."""
+    base = synth.random_pattern_system(400, 5, 31)
+    s = synth.one_way_system(base, 0.4, 32)
+    key = lambda sy: np.repeat(np.arange(sy.nb), np.diff(sy.rowptr)).astype(np.int64) * sy.nb + sy.colidx
+    kb, ks = key(base), key(s)
+    pos = np.searchsorted(kb, ks)
+    np.testing.assert_array_equal(kb[pos], ks)                  # a subset of base's blocks, in row order
+    np.testing.assert_array_equal(s.vals, base.vals[pos])       # with base's values
+    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
+    assert np.count_nonzero(rows == s.colidx) == s.nb           # every diagonal kept
+    nb_off = base.nnzb - base.nb
+    assert abs((base.nnzb - s.nnzb) / nb_off - 0.4) < 0.03
+    mirrored = np.isin(s.colidx.astype(np.int64) * s.nb + rows, ks)
+    assert np.count_nonzero(~mirrored) > 0.2 * (s.nnzb - s.nb)  # one-way blocks present
+    np.testing.assert_array_equal(synth.one_way_system(base, 0.4, 32).colidx, s.colidx)
 
 
 # ------------------------------------------------------- block-Jacobi ILU0
