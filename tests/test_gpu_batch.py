@@ -22,7 +22,8 @@ def rhs(s):
 
 def systems():
     out = [synth.config1(), synth.random_pattern_system(777, 3, 5), synth.chain_system(45),
-           synth.block_diagonal_system(70, 2)]
+           synth.block_diagonal_system(70, 2),
+           synth.one_way_system(synth.random_pattern_system(300, 4, 48), 0.5, 49)]  # non-symmetric pattern
     out += synth.config4(nsys=6)  # uneven grid sizes of the batched workload
     return out
 

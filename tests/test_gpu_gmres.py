@@ -46,6 +46,7 @@ SMALL = {
     "ragged33": lambda: synth.random_pattern_system(33, 3, 41),
     "tree": lambda: synth.tree_system(300, 44),
     "long_rows": lambda: synth.random_pattern_system(70, 20, 42),
+    "one_way200": lambda: synth.one_way_system(synth.random_pattern_system(200, 4, 45), 0.5, 46),
 }
 
 

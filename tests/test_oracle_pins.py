@@ -884,7 +884,8 @@ def test_chow_patel_zero_sweeps_is_the_initial_guess():
 
 @pytest.mark.parametrize("maker", [lambda: synth.grid_system(4, 4, 3, synth.uniform(
     synth.stream_key(5, 5), np.arange(48, dtype=np.uint64), -1, 1)),
-    lambda: synth.random_pattern_system(40, 3, 43)])
+    lambda: synth.random_pattern_system(40, 3, 43),
+    lambda: synth.one_way_system(synth.random_pattern_system(40, 4, 44), 0.5, 45)])
 def test_chow_patel_reaches_the_ilu0_identity_after_the_dependency_depth(maker):
     """After exactly as many sweeps as the longest dependency chain (brute
     force) the iterates satisfy (LU)_ij = A_ij on the pattern (checked with
