@@ -9,6 +9,12 @@ the seeded 100^3 grid with a 5% inactive mask and 1% fault connections
 (949,871 cells, 6.33M 3x3 blocks), b = A x_true formed on the GPU with the
 library's own SpMV.  Inputs (456 MB of values) are larger than L2.
 
+`value` is device-timed with the inputs resident in HBM.  `e2e` makes the same
+calls from pinned host buffers: each step copies the values and b in and
+reads x back.  It is measured one step at a time, and again as
+`e2e.overlapped`, with two handles on two streams used alternately so that a
+step's copies overlap the other handle's kernels.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Multi-GPU (torchrun): every rank solves its own replica (the single-system
