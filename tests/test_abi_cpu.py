@@ -228,3 +228,31 @@ def test_library_analysis_matches_the_oracle_on_random_patterns(nb, extra, frac)
         np.testing.assert_array_equal(perm, ref, err_msg=schedule)
         assert info.nsets == nsets, schedule
         assert info.nnzb_kept == rowptr[-1] and info.nnzb_lower + info.nnzb_upper == rowptr[-1] - nb
+
+
+def test_constants_match_the_header(tmp_path):
+    """Status codes, schedules, precisions, sweep modes, kernel indices and
+    the tuner's table size: the binding's values are the header's (plain gcc
+    on this host)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    want = {f"OPM_{k}": getattr(opm, f"OPM_{k}") for k in
+            ("OK", "NOT_CONVERGED", "ERR_ARG", "ERR_PATTERN", "ERR_NO_DIAG", "ERR_ZERO_PIVOT", "ERR_BREAKDOWN",
+             "ERR_NONFINITE", "ERR_OOM", "ERR_TIMEOUT", "ERR_CUDA", "TUNE_MAX")}
+    want.update({f"OPM_SCHED_{k.upper()}": v for k, v in opm.SCHEDULES.items()})
+    want.update({"OPM_PREC_FP64": opm.PRECISIONS["fp64"], "OPM_PREC_FP32_FACTORS": opm.PRECISIONS["fp32"]})
+    want.update({f"OPM_SWEEP_{k.upper()}": v for k, v in opm.SWEEPS.items()})
+    want.update({f"OPM_KERNEL_{k.upper()}": q for q, k in enumerate(opm.KERNELS)})
+    want["OPM_KERNEL_COUNT"] = len(opm.KERNELS)
+    lines = ['#include <stdio.h>', '#include "opm_bsr.h"', 'int main(void) {']
+    lines += [f'  printf("{name} %d\\n", (int)({name}));' for name in want]
+    lines.append('  return 0; }')
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines() if ln)
+    for name, v in want.items():
+        assert int(got[name]) == v, name
