@@ -154,6 +154,10 @@ typedef struct opm_options {
   int32_t reserved[2];
 } opm_options;
 
+/* Largest nb a handle or an analysis accepts: row counts rounded up to
+ * whole tiles and slices stay within int32. */
+#define OPM_MAX_ROWS 2147479551
+
 /* Fill *opt with the defaults (AUTO schedule, FP64, default stream). */
 void opm_options_default(opm_options *opt);
 
@@ -163,7 +167,11 @@ void opm_options_default(opm_options *opt);
  * the paper's per-solve table moves here), computes the level or colour
  * schedule and the row permutation (Section 4.4), builds the library's
  * permuted device copy of the matrix and factorises it (Algorithm 2).
- *   nb >= 0; rowptr, colidx, vals as above (host or device); opt may be NULL.
+ *   0 <= nb <= OPM_MAX_ROWS, else OPM_ERR_ARG; rowptr, colidx, vals as above
+ *   (host or device); opt may be NULL.  The block count is bounded by the
+ *   int32 row pointers (below 2^31); device memory binds well before either
+ *   bound: per block the values, the factors and the index maps, per row
+ *   about fifteen 3-vectors (opm_get_info reports the bytes held).
  *   On success *out receives a new handle.  On OPM_ERR_ZERO_PIVOT *out still
  *   receives the handle (its factors invalid) so that opm_last_error_row can
  *   be read and opm_ilu0_factor retried with other values; the caller
@@ -203,7 +211,8 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
  *   schedule: OPM_SCHED_*; perm (may be NULL): nb entries, perm[new] = old.
  *   info (may be NULL) receives the counts.
  *   Returns OPM_OK or the pattern error of opm_bsr_create (the offending row
- *   via opm_last_error_row(NULL)); OPM_ERR_ARG on a bad argument.
+ *   via opm_last_error_row(NULL)); OPM_ERR_ARG on a bad argument (nb
+ *   outside 0 .. OPM_MAX_ROWS included).
  */
 typedef struct opm_analysis_info {
   int32_t schedule;    /* schedule used (never OPM_SCHED_AUTO)               */

@@ -1277,7 +1277,7 @@ opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
   if (!out) return OPM_ERR_ARG;
   *out = nullptr;
   t_create_err_row = -1;
-  if (nb < 0 || !rowptr || (nb > 0 && (!colidx || !vals))) return OPM_ERR_ARG;
+  if (nb < 0 || nb > OPM_MAX_ROWS || !rowptr || (nb > 0 && (!colidx || !vals))) return OPM_ERR_ARG;
   opm_options o;
   opm_options_default(&o);
   if (opt) o = *opt;
@@ -1374,7 +1374,8 @@ opm_status opm_bsr_create_jacobi(int32_t nb, const int32_t *rowptr, const int32_
 opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
                            int32_t schedule, int32_t *perm, opm_analysis_info *info) {
   t_create_err_row = -1;
-  if (nb < 0 || !rowptr || (nb > 0 && !colidx) || schedule < OPM_SCHED_AUTO || schedule > OPM_SCHED_COLOUR_KEMPE)
+  if (nb < 0 || nb > OPM_MAX_ROWS || !rowptr || (nb > 0 && !colidx) || schedule < OPM_SCHED_AUTO ||
+      schedule > OPM_SCHED_COLOUR_KEMPE)
     return OPM_ERR_ARG;
   Analysis an;
   int32_t err_row = -1;

@@ -29,6 +29,7 @@ OPM_ERR_NONFINITE = -6
 OPM_ERR_OOM = -7
 OPM_ERR_TIMEOUT = -8
 OPM_ERR_CUDA = -9
+OPM_MAX_ROWS = 2147479551  # largest nb a handle or an analysis accepts
 
 SCHEDULES = {"auto": 0, "natural": 1, "level": 2, "colour": 3, "colour_sl": 4, "colour_kempe": 5}
 SWEEPS = {"auto": 0, "per_phase": 1, "cooperative": 2}
@@ -246,7 +247,7 @@ def opm_bsr_analyse(nb, rowptr, colidx, schedule="auto", part=None):
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
     colidx = np.ascontiguousarray(colidx, dtype=np.int32)
     pt = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
-    perm = np.empty(max(int(nb), 0), dtype=np.int32)
+    perm = np.empty(int(nb) if 0 <= int(nb) <= OPM_MAX_ROWS else 0, dtype=np.int32)
     info = opm_analysis_info()
     st = lib().opm_bsr_analyse(int(nb), rowptr.ctypes.data, colidx.ctypes.data if colidx.size else None,
                                pt.ctypes.data if pt is not None and pt.size else None, int(schedule),

@@ -89,6 +89,13 @@ def test_bad_arguments():
     assert st == opm.OPM_ERR_ARG
     st, h = _create(s.nb, s.rowptr, s.colidx, s.vals, precision=5)
     assert st == opm.OPM_ERR_ARG
+    # nb beyond the row limit is refused before any array is read
+    # (non-null arrays, so that only the size can be the reason)
+    st, h = _create(opm.OPM_MAX_ROWS + 1, [0, 1], [0], np.zeros(9))
+    assert st == opm.OPM_ERR_ARG
+    st, perm, info = opm.opm_bsr_analyse(opm.OPM_MAX_ROWS + 1, np.array([0, 1], np.int32), np.zeros(1, np.int32),
+                                         "level")
+    assert st == opm.OPM_ERR_ARG and perm.size == 0
 
 
 def test_product_package_never_imports_the_oracle():
@@ -240,7 +247,7 @@ def test_constants_match_the_header(tmp_path):
         pytest.skip("no gcc")
     want = {f"OPM_{k}": getattr(opm, f"OPM_{k}") for k in
             ("OK", "NOT_CONVERGED", "ERR_ARG", "ERR_PATTERN", "ERR_NO_DIAG", "ERR_ZERO_PIVOT", "ERR_BREAKDOWN",
-             "ERR_NONFINITE", "ERR_OOM", "ERR_TIMEOUT", "ERR_CUDA", "TUNE_MAX")}
+             "ERR_NONFINITE", "ERR_OOM", "ERR_TIMEOUT", "ERR_CUDA", "TUNE_MAX", "MAX_ROWS")}
     want.update({f"OPM_SCHED_{k.upper()}": v for k, v in opm.SCHEDULES.items()})
     want.update({"OPM_PREC_FP64": opm.PRECISIONS["fp64"], "OPM_PREC_FP32_FACTORS": opm.PRECISIONS["fp32"]})
     want.update({f"OPM_SWEEP_{k.upper()}": v for k, v in opm.SWEEPS.items()})
