@@ -733,7 +733,14 @@ def measure_batched(args, barrier, max_over_ranks, world):
         for h in hs:
             h.close()
     cells = sum(q.nb for q in syss)
-    return {"workload": f"{len(syss)} independent systems, {cells} cells total, grids 5..40 per axis, "
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_batched(len(syss))
+        except Exception as e:  # the GPU figures stand without it
+            cpu = {"kind": "oracle", "unavailable": f"{type(e).__name__}: {e}"}
+    return {"cpu_baseline": cpu,
+            "workload": f"{len(syss)} independent systems, {cells} cells total, grids 5..40 per axis, "
                         f"per step: batched refactor + BiCGStab to rtol 1e-2 for every system",
             "value": res["fp32"]["solves_per_s"], "unit": "solves/s", "dtype": "f64 Krylov + f32 factors",
             "fp32_factors": res["fp32"], "fp64": res["fp64"],
@@ -804,6 +811,77 @@ def cpu_baseline(s, n_solves=2):
             "sample": f"{n_solves} full steps (value permutation, ILU0, BiCGStab to rtol 1e-3 in {res.iters} "
                       f"iterations, true residual) of the same system in the library's default order, "
                       f"single-threaded C, {os.cpu_count()} host cores present"}
+
+
+def _batched_oracle_worker(conn, indices, nsys, rtol, repeats):
+    """One host core of the batched workload's CPU baseline.  Regenerates its
+    systems and sets them up untimed (b = A x_true, the colour_kempe order),
+    reports ready, then on "go" times `repeats` passes of value permutation
+    + ILU0 + BiCGStab over them and sends (seconds, statuses, iterations)."""
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_2309_11488_gb300 import synth
+    dims = synth.config4_dims(nsys)
+    work = []
+    for k in indices:
+        q = synth.config4_system(k, dims)
+        b = O.spmv(q.nb, q.rowptr, q.colidx, q.vals, q.x_true)
+        perm, _ = O.schedule_perm(q.nb, q.rowptr, q.colidx, "colour_kempe")
+        work.append((q, perm, b.reshape(-1, 3)[perm].ravel()))
+    conn.send("ready")
+    conn.recv()
+    st, its = [], []
+    t0 = time.perf_counter()
+    for rep in range(repeats):
+        for q, perm, pb in work:
+            prow, pcol, pval = O.permute(q.nb, q.rowptr, q.colidx, q.vals, perm)
+            fac = O.ilu0(q.nb, prow, pcol, pval)
+            res = O.bicgstab(q.nb, prow, pcol, pval, fac, pb, rtol, 200)
+            if rep == 0:
+                st.append(int(res.status))
+                its.append(int(res.iters))
+    conn.send((time.perf_counter() - t0, st, its))
+    conn.close()
+
+
+def cpu_baseline_batched(nsys, rtol=1e-2, repeats=5, cores=None, timeout_s=600.0):
+    """The oracle on all host cores for the batched workload: one spawned
+    process per core, systems dealt round-robin, every process started on
+    the same signal; solves/s = repeats x nsys / the slowest process's time."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = max(1, min(cores or os.cpu_count() or 1, nsys))
+    procs = []
+    try:
+        for w in range(cores):
+            parent, child = ctx.Pipe()
+            p = ctx.Process(target=_batched_oracle_worker, args=(child, list(range(w, nsys, cores)), nsys, rtol,
+                                                                 repeats), daemon=True)
+            p.start()
+            procs.append((p, parent))
+        for p, c in procs:
+            if not c.poll(timeout_s) or c.recv() != "ready":
+                raise RuntimeError("an oracle process did not get ready")
+        for p, c in procs:
+            c.send("go")
+        out = []
+        for p, c in procs:
+            if not c.poll(timeout_s):
+                raise RuntimeError("an oracle process did not finish")
+            out.append(c.recv())
+    finally:
+        for p, c in procs:
+            p.join(5)
+            if p.is_alive():
+                p.terminate()
+    wall = max(o[0] for o in out)
+    st = [v for o in out for v in o[1]]
+    its = [v for o in out for v in o[2]]
+    return {"value": round(repeats * nsys / wall, 2), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{repeats} passes over all {nsys} systems (value permutation, ILU0, BiCGStab to rtol {rtol:g} "
+                      f"in the colour_kempe order, FP64), one single-threaded C oracle process per core, systems "
+                      f"dealt round-robin; time of the slowest process",
+            "status_ok": sum(1 for v in st if v == 0), "iters_mean": float(np.mean(its)) if its else 0.0}
 
 
 def run_reference(args, rank, world):

@@ -349,15 +349,20 @@ def config4_dims(nsys=256, seed=None):
     return dims
 
 
+def config4_system(s, dims, seed=None) -> BsrSystem:
+    """System s of the batched workload, given config4_dims(nsys, seed):
+    all active, sigma = 1, its own seed."""
+    seed = config_seed(4) if seed is None else seed
+    nx, ny, nz = dims[s]
+    ss = seed + 1 + s
+    return grid_system(nx, ny, nz, _lognormal_field(ss, (nz, ny, nx), 1.0), seed=ss,
+                       meta={"config": f"C4 system {s}"})
+
+
 def config4(nsys=256, seed=None):
     """256 independent all-active systems of uneven size, sigma = 1."""
-    seed = config_seed(4) if seed is None else seed
-    out = []
-    for s, (nx, ny, nz) in enumerate(config4_dims(nsys, seed)):
-        ss = seed + 1 + s
-        out.append(grid_system(nx, ny, nz, _lognormal_field(ss, (nz, ny, nx), 1.0), seed=ss,
-                               meta={"config": f"C4 system {s}"}))
-    return out
+    dims = config4_dims(nsys, seed)
+    return [config4_system(s, dims, seed) for s in range(nsys)]
 
 
 def config5_dims(npat=32, seed=None):

@@ -68,3 +68,16 @@ def test_work_counts_on_a_hand_counted_system():
 def test_fp64_fma_peak_is_the_documented_lane_rate():
     b = _bench_module()
     assert np.isclose(b.FP64_FMA_PEAK, 2 * 152 * 2.07e9)
+
+
+def test_batched_cpu_baseline_runs_one_oracle_process_per_core():
+    """The batched workload's oracle baseline on 8 systems and 2 spawned
+    processes: every system converges, the line names the cores and the
+    sample, and the rate is repeats x systems / the slowest process."""
+    code = ("import bench, json; print(json.dumps(bench.cpu_baseline_batched(8, repeats=2, cores=2)))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["kind"] == "oracle" and d["cores"] == 2 and d["unit"] == "solves/s"
+    assert d["status_ok"] == 8 and d["iters_mean"] >= 1 and d["value"] > 0
+    assert "8 systems" in d["sample"] and "per core" in d["sample"]
