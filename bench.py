@@ -762,9 +762,7 @@ def measure_serving(args, barrier, max_over_ranks, world):
 
     def requests(duration, seed):
         t = serve.poisson_arrivals(args.rate, duration, seed)
-        key = synth.stream_key(seed, 5)
-        pick = np.minimum((synth.uniform(key, np.arange(len(t), dtype=np.uint64)) * len(pats)).astype(int),
-                          len(pats) - 1)
+        pick = serving_picks(len(pats), len(t), seed)
         return [serve.Request(i, float(ti), int(pick[i]), *tmpl[int(pick[i])][i % 2]) for i, ti in enumerate(t)]
 
     eng.run(requests(args.serve_warm_s, 31))          # warm: instances, clocks
@@ -773,6 +771,11 @@ def measure_serving(args, barrier, max_over_ranks, world):
     barrier()
     summ = stats.summary()
     eng.close()
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            summ["cpu_baseline"] = cpu_baseline_serving(len(pats))
+        except Exception as e:  # the GPU figures stand without it
+            summ["cpu_baseline"] = {"kind": "oracle", "unavailable": f"{type(e).__name__}: {e}"}
     cells = [q.nb for q in pats]
     summ.update({"workload": f"{len(pats)} patterns of {min(cells)}..{max(cells)} cells, Poisson arrivals "
                              f"{args.rate:g} req/s for {args.serve_s:g} s (after {args.serve_warm_s:g} s warm), "
@@ -813,28 +816,46 @@ def cpu_baseline(s, n_solves=2):
                       f"single-threaded C, {os.cpu_count()} host cores present"}
 
 
-def _batched_oracle_worker(conn, indices, nsys, rtol, repeats):
-    """One host core of the batched workload's CPU baseline.  Regenerates its
-    systems and sets them up untimed (b = A x_true, the colour_kempe order),
+def _oracle_worker(conn, kind, jobs, nsys, rtol, repeats):
+    """One host core of a multi-core oracle baseline.  Builds its share of the
+    workload and sets it up untimed (b = A x_true, the colour_kempe order),
     reports ready, then on "go" times `repeats` passes of value permutation
-    + ILU0 + BiCGStab over them and sends (seconds, statuses, iterations)."""
+    + ILU0 + BiCGStab over its jobs and sends (seconds, statuses,
+    iterations).  kind "batched": jobs are indices of the batched workload's
+    systems; kind "serving": jobs are (pattern, template) requests, the
+    values of a template made once and shared by its requests."""
     sys.path.insert(0, ROOT)
     import oracle as O
     from paper_2309_11488_gb300 import synth
-    dims = synth.config4_dims(nsys)
+    systems, prepared, perms = {}, {}, {}
+    dims = synth.config4_dims(nsys) if kind == "batched" else None
     work = []
-    for k in indices:
-        q = synth.config4_system(k, dims)
-        b = O.spmv(q.nb, q.rowptr, q.colidx, q.vals, q.x_true)
-        perm, _ = O.schedule_perm(q.nb, q.rowptr, q.colidx, "colour_kempe")
-        work.append((q, perm, b.reshape(-1, 3)[perm].ravel()))
+    for job in jobs:
+        if job not in prepared:
+            if kind == "batched":
+                q = synth.config4_system(job, dims)
+                vals, xt = q.vals, q.x_true
+                pk = ("s", job)
+            else:
+                p, k = job
+                if p not in systems:
+                    systems[p] = synth.config5_pattern(p)
+                q = systems[p]
+                vals, xt = synth.newton_update(q, 1000 * p + k)
+                pk = ("p", p)
+            if pk not in perms:
+                perms[pk] = O.schedule_perm(q.nb, q.rowptr, q.colidx, "colour_kempe")[0]
+            perm = perms[pk]
+            b = O.spmv(q.nb, q.rowptr, q.colidx, vals, xt)
+            prepared[job] = (q, vals, perm, b.reshape(-1, 3)[perm].ravel())
+        work.append(prepared[job])
     conn.send("ready")
     conn.recv()
     st, its = [], []
     t0 = time.perf_counter()
     for rep in range(repeats):
-        for q, perm, pb in work:
-            prow, pcol, pval = O.permute(q.nb, q.rowptr, q.colidx, q.vals, perm)
+        for q, vals, perm, pb in work:
+            prow, pcol, pval = O.permute(q.nb, q.rowptr, q.colidx, vals, perm)
             fac = O.ilu0(q.nb, prow, pcol, pval)
             res = O.bicgstab(q.nb, prow, pcol, pval, fac, pb, rtol, 200)
             if rep == 0:
@@ -844,19 +865,16 @@ def _batched_oracle_worker(conn, indices, nsys, rtol, repeats):
     conn.close()
 
 
-def cpu_baseline_batched(nsys, rtol=1e-2, repeats=5, cores=None, timeout_s=600.0):
-    """The oracle on all host cores for the batched workload: one spawned
-    process per core, systems dealt round-robin, every process started on
-    the same signal; solves/s = repeats x nsys / the slowest process's time."""
+def _run_oracle_processes(kind, shards, nsys, rtol, repeats, timeout_s):
+    """One spawned process per shard, all started on the same signal; returns
+    (the slowest process's seconds, statuses, iterations)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    cores = max(1, min(cores or os.cpu_count() or 1, nsys))
     procs = []
     try:
-        for w in range(cores):
+        for jobs in shards:
             parent, child = ctx.Pipe()
-            p = ctx.Process(target=_batched_oracle_worker, args=(child, list(range(w, nsys, cores)), nsys, rtol,
-                                                                 repeats), daemon=True)
+            p = ctx.Process(target=_oracle_worker, args=(child, kind, jobs, nsys, rtol, repeats), daemon=True)
             p.start()
             procs.append((p, parent))
         for p, c in procs:
@@ -874,13 +892,55 @@ def cpu_baseline_batched(nsys, rtol=1e-2, repeats=5, cores=None, timeout_s=600.0
             p.join(5)
             if p.is_alive():
                 p.terminate()
-    wall = max(o[0] for o in out)
-    st = [v for o in out for v in o[1]]
-    its = [v for o in out for v in o[2]]
+    return (max(o[0] for o in out), [v for o in out for v in o[1]], [v for o in out for v in o[2]])
+
+
+def cpu_baseline_batched(nsys, rtol=1e-2, repeats=5, cores=None, timeout_s=600.0):
+    """The oracle on all host cores for the batched workload: one spawned
+    process per core, systems dealt round-robin, every process started on
+    the same signal; solves/s = repeats x nsys / the slowest process's time."""
+    cores = max(1, min(cores or os.cpu_count() or 1, nsys))
+    shards = [list(range(w, nsys, cores)) for w in range(cores)]
+    wall, st, its = _run_oracle_processes("batched", shards, nsys, rtol, repeats, timeout_s)
     return {"value": round(repeats * nsys / wall, 2), "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"{repeats} passes over all {nsys} systems (value permutation, ILU0, BiCGStab to rtol {rtol:g} "
                       f"in the colour_kempe order, FP64), one single-threaded C oracle process per core, systems "
                       f"dealt round-robin; time of the slowest process",
+            "status_ok": sum(1 for v in st if v == 0), "iters_mean": float(np.mean(its)) if its else 0.0}
+
+
+def serving_picks(npat, nreq, seed=32):
+    """Patterns of the first nreq requests of the serving run's request
+    stream (the same counter-based draw the serving leg makes)."""
+    from paper_2309_11488_gb300 import synth
+    u = synth.uniform(synth.stream_key(seed, 5), np.arange(nreq, dtype=np.uint64))
+    return np.minimum((u * npat).astype(int), npat - 1)
+
+
+def cpu_baseline_serving(npat, nreq=256, rtol=1e-2, repeats=1, cores=None, timeout_s=600.0):
+    """The oracle on all host cores for the serving workload, closed loop (no
+    arrival process): the first nreq requests of the serving stream, each a
+    refactorisation + solve of its pattern with the request's values.  A
+    pattern's requests stay on one process; patterns are dealt to the least
+    loaded process by cells x requests.  solves/s = repeats x nreq / the
+    slowest process's time."""
+    from paper_2309_11488_gb300 import synth
+    pick = serving_picks(npat, nreq)
+    cells = {p: int(np.prod(d)) for p, d in enumerate(synth.config5_dims(npat))}
+    jobs = {}
+    for i, p in enumerate(pick.tolist()):
+        jobs.setdefault(p, []).append((p, i % 2))
+    cores = max(1, min(cores or os.cpu_count() or 1, len(jobs)))
+    shards, load = [[] for _ in range(cores)], [0] * cores
+    for p in sorted(jobs, key=lambda p: -cells[p] * len(jobs[p])):
+        w = int(np.argmin(load))
+        shards[w] += jobs[p]
+        load[w] += cells[p] * len(jobs[p])
+    wall, st, its = _run_oracle_processes("serving", shards, npat, rtol, repeats, timeout_s)
+    return {"value": round(repeats * nreq / wall, 2), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {nreq} requests of the serving stream over {len(jobs)} of {npat} patterns, "
+                      f"closed loop (value permutation, ILU0, BiCGStab to rtol {rtol:g} in the colour_kempe "
+                      f"order, FP64), one single-threaded C oracle process per core; time of the slowest process",
             "status_ok": sum(1 for v in st if v == 0), "iters_mean": float(np.mean(its)) if its else 0.0}
 
 

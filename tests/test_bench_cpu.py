@@ -81,3 +81,19 @@ def test_batched_cpu_baseline_runs_one_oracle_process_per_core():
     assert d["kind"] == "oracle" and d["cores"] == 2 and d["unit"] == "solves/s"
     assert d["status_ok"] == 8 and d["iters_mean"] >= 1 and d["value"] > 0
     assert "8 systems" in d["sample"] and "per core" in d["sample"]
+
+
+def test_serving_cpu_baseline_solves_the_serving_streams_requests():
+    """The serving workload's oracle baseline on the first 12 requests over 4
+    patterns: every request converges, and the requests are the serving
+    stream's (the same pattern draw as the serving leg)."""
+    code = ("import bench, json; print(json.dumps(bench.cpu_baseline_serving(4, nreq=12, cores=2)))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["kind"] == "oracle" and d["cores"] == 2 and d["status_ok"] == 12 and d["value"] > 0
+    b = _bench_module()
+    pick = b.serving_picks(4, 12)
+    assert pick.min() >= 0 and pick.max() < 4
+    np.testing.assert_array_equal(pick, b.serving_picks(4, 40)[:12])  # a prefix of any longer stream
+    assert f"over {len(set(pick.tolist()))} of 4 patterns" in d["sample"]
