@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--partitions", type=int, default=150, help="block-Jacobi partitions")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the C1 / C2 (L2-resident) leg")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--patterns", type=int, default=32)
@@ -489,6 +490,11 @@ def run_ours(args, rank, world, dist):
         out["gmres"] = measure_gmres(args, s, out["config"]["options"], barrier, max_over_ranks, world)
     if not args.no_iterative:
         out["iterative"] = measure_iterative(args, s, barrier, max_over_ranks, world)
+    if not args.no_small:
+        try:
+            out["small_configs"] = measure_small(args, barrier, world, rank)
+        except Exception as e:  # the other figures stand without it
+            out["small_configs"] = {"unavailable": f"{type(e).__name__}: {e}"}
     if not args.no_batched:
         out["batched"] = measure_batched(args, barrier, max_over_ranks, world)
     if not args.no_serving:
@@ -597,6 +603,80 @@ def measure_gmres(args, s, options, barrier, max_over_ranks, world):
             res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
                          "preconditioner_applications": it + (1 if name == "gmres" else it)}
     return res
+
+
+def small_config_cases():
+    """(name, generator, rtol, schedule) of the configurations that fit in L2:
+    C1 (10x10x5, natural order) and C2 (the 44,431-cell NORNE stand-in, graph
+    colouring, rtol 1e-2 and 1e-6), each also in the library's default order."""
+    from paper_2309_11488_gb300 import synth
+    return [("C1", synth.config1, 1e-2, "natural"), ("C1", synth.config1, 1e-2, "auto"),
+            ("C2", synth.config2, 1e-2, "colour"), ("C2", synth.config2, 1e-6, "colour"),
+            ("C2", synth.config2, 1e-2, "auto"), ("C2", synth.config2, 1e-6, "auto")]
+
+
+def oracle_small(q, rtol, schedule, repeats=5):
+    """The oracle, single-threaded, on one small configuration in the order
+    the library used: median seconds of `repeats` steps (value permutation,
+    ILU0, BiCGStab), the order's setup untimed."""
+    import oracle as O
+    b = O.spmv(q.nb, q.rowptr, q.colidx, q.vals, q.x_true)
+    perm, _ = O.schedule_perm(q.nb, q.rowptr, q.colidx, schedule)
+    pb = b.reshape(-1, 3)[perm].ravel()
+    times, res = [], None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        prow, pcol, pval = O.permute(q.nb, q.rowptr, q.colidx, q.vals, perm)
+        fac = O.ilu0(q.nb, prow, pcol, pval)
+        res = O.bicgstab(q.nb, prow, pcol, pval, fac, pb, rtol, 200)
+        times.append(time.perf_counter() - t0)
+    return float(np.median(times)), res
+
+
+def measure_small(args, barrier, world, rank):
+    """C1 and C2, which fit in L2: per step one refactor + solve (launch and
+    wait), each step timed with CUDA events, median of at least 20 steps;
+    beside it the oracle, single-threaded, median of 5 steps in the same
+    order (rank 0 at one GPU only)."""
+    import torch
+    from paper_2309_11488_gb300 import opm
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    names = {v: k for k, v in opm.SCHEDULES.items()}
+    reps = max(20, args.steps // 10)
+    out, cache = [], {}
+    for name, gen, rtol, schedule in small_config_cases():
+        if name not in cache:
+            cache[name] = gen()
+        q = cache[name]
+        rp, ci, va, xt = dev(q.rowptr), dev(q.colidx), dev(q.vals), dev(q.x_true)
+        with opm.Solver(q.nb, rp, ci, va, schedule=schedule) as sv:
+            used = names[sv.info().schedule]
+            b = sv.spmv(xt)
+            x = torch.empty_like(b)
+
+            def step():
+                sv.launch(va, b, x, rtol=rtol, maxit=200)
+                return sv.wait()
+            for _ in range(5):
+                step()
+            barrier()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for e0, e1 in ev:
+                e0.record()
+                st, it, rr = step()
+                e1.record()
+            torch.cuda.synchronize()
+            ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+        p50 = float(np.median(ms))
+        row = {"config": name, "cells": q.nb, "blocks": q.nnzb, "schedule": used, "rtol": rtol, "iters": it,
+               "status": st, "relres": rr, "p50_ms": round(p50, 4), "p90_ms": round(float(np.percentile(ms, 90)), 4),
+               "solves_per_s": round(world * 1e3 / p50, 2), "repeats": reps}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            t, res = oracle_small(q, rtol, used)
+            row["oracle"] = {"p50_ms": round(1e3 * t, 3), "solves_per_s": round(1.0 / t, 3), "iters": res.iters,
+                             "cores": 1, "repeats": 5, "kind": "oracle"}
+        out.append(row)
+    return {"cases": out, "l2": "inputs smaller than L2, not flushed: L2-resident latency per refactor + solve"}
 
 
 def measure_iterative(args, s, barrier, max_over_ranks, world):

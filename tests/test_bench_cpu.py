@@ -97,3 +97,16 @@ def test_serving_cpu_baseline_solves_the_serving_streams_requests():
     assert pick.min() >= 0 and pick.max() < 4
     np.testing.assert_array_equal(pick, b.serving_picks(4, 40)[:12])  # a prefix of any longer stream
     assert f"over {len(set(pick.tolist()))} of 4 patterns" in d["sample"]
+
+
+def test_small_configuration_leg_cases_and_oracle_half():
+    """The C1 / C2 leg covers both configurations, both C2 tolerances and the
+    library's default order beside the paper's; its oracle half solves C1 in
+    natural order to the stopping rule."""
+    b = _bench_module()
+    cases = b.small_config_cases()
+    assert {(c[0], c[2]) for c in cases} == {("C1", 1e-2), ("C2", 1e-2), ("C2", 1e-6)}
+    assert {c[3] for c in cases if c[0] == "C2"} == {"colour", "auto"}
+    q = cases[0][1]()
+    t, res = b.oracle_small(q, 1e-2, "natural", repeats=3)
+    assert t > 0 and res.status == 0 and res.iters >= 1 and res.relres <= 1e-2 * (1 + 1e-6)
