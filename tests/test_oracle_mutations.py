@@ -1,0 +1,102 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each case copies the oracle, the seeded input generator, the pin tests and
+their golden files into a temporary directory, plants one mistake in the
+copy of oracle.c (the repository's own oracle is never touched) and runs the
+pins there: at least one must fail.  The control case plants nothing and
+must pass, so that a failure is the mistake's and not the harness's.  A
+mutant that passes every pin would name a gap in the pins.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# name -> [(text in oracle.c, replacement)], each text present exactly once
+MUTANTS = {
+    "control": [],
+    # blocks and the 3x3 inverse
+    "matvec_transposed_block": [("acc += a[r * BS + c] * x[c];", "acc += a[c * BS + r] * x[c];")],
+    "inverse_without_pivoting": [("if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;", "if (0) piv = r;")],
+    # ILU0 (Algorithm 2)
+    "ilu0_left_product_with_pivot": [("blk_mul(lu + BS2 * mk, dinv + BS2 * (int64_t)k, lik);",
+                                      "blk_mul(dinv + BS2 * (int64_t)k, lu + BS2 * mk, lik);")],
+    "ilu0_update_added": [("for (int e = 0; e < BS2; ++e) c[e] -= p[e];",
+                           "for (int e = 0; e < BS2; ++e) c[e] += p[e];")],
+    "ilu0_diagonal_not_updated": [("if (mkj >= 0) blk_mul_sub(lik, lu + BS2 * mkj, lu + BS2 * mj);",
+                                   "if (mkj >= 0 && j != i) blk_mul_sub(lik, lu + BS2 * mkj, lu + BS2 * mj);")],
+    # ILU0 application (Algorithm 1)
+    "apply_without_inverse_pivot": [("    double zi[BS] = {0.0, 0.0, 0.0};\n    blk_matvec_add(dinv + BS2 * (int64_t)i, acc, zi);\n"
+                                     "    for (int c = 0; c < BS; ++c) z[(int64_t)BS * i + c] = zi[c];",
+                                     "    for (int c = 0; c < BS; ++c) z[(int64_t)BS * i + c] = acc[c];")],
+    "apply_backward_skips_last_upper": [("      if (j <= i) continue;\n      double t[BS] = {0.0, 0.0, 0.0};\n"
+                                         "      blk_matvec_add(lu + BS2 * m, z + (int64_t)BS * j, t);",
+                                         "      if (j <= i || m == rowptr[i + 1] - 1) continue;\n"
+                                         "      double t[BS] = {0.0, 0.0, 0.0};\n"
+                                         "      blk_matvec_add(lu + BS2 * m, z + (int64_t)BS * j, t);")],
+    # BiCGStab (van der Vorst) and the stopping rule of Section 4.2
+    "bicgstab_beta_inverted": [("double beta = (rho / rho_prev) * (alpha / omega);",
+                                "double beta = (rho / rho_prev) * (omega / alpha);")],
+    "bicgstab_half_step_without_update": [("      for (size_t e = 0; e < n; ++e) x[e] += alpha * ph[e];\n      status = 0;",
+                                           "      status = 0;")],
+    "bicgstab_residual_sign": [("r[e] = s[e] - omega * t[e];", "r[e] = s[e] + omega * t[e];")],
+    "bicgstab_stops_late": [("    if (nr <= tol) {", "    if (nr <= 0.5 * tol) {")],
+    "bicgstab_half_step_stops_late": [("    if (ns <= tol) { /* half-step exit */", "    if (ns <= 0.5 * tol) {")],
+    "bicgstab_stops_early": [("    if (nr <= tol) {", "    if (nr <= 2.0 * tol) {")],
+    # schedules (Section 4.4)
+    "levels_not_incremented": [("if (j < i && level[j] + 1 > l) l = level[j] + 1;",
+                                "if (j < i && level[j] > l) l = level[j];")],
+    "graph_not_symmetrised": [("      deg[i]++;\n      deg[j]++;", "      deg[i]++;"),
+                              ("      adj[ptr[i] + fill[i]++] = j;\n      adj[ptr[j] + fill[j]++] = i;",
+                               "      adj[ptr[i] + fill[i]++] = j;")],
+    "permute_leaves_columns_unsorted": [("while (at > base && pcolidx[at - 1] > nc) {", "while (0) {")],
+    # wells (Section 4.6)
+    "wells_added": [("y[(int64_t)BS * wcells[p] + c] -= acc;", "y[(int64_t)BS * wcells[p] + c] += acc;")],
+    "wells_B_for_C": [("acc += C[12 * (int64_t)p + 3 * r + c] * t2[r];", "acc += B[12 * (int64_t)p + 3 * r + c] * t2[r];")],
+    # restarted GMRES
+    "gmres_rotation_sign": [("H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;", "H[(i + 1) * m + j] = sn[i] * a + cs[i] * c;")],
+    # Chow-Patel sweeps and Jacobi triangular sweeps: Gauss-Seidel instead of synchronous
+    "chow_patel_in_place": [("          blk_mul(sum, dinv + BS2 * (int64_t)j, lu2 + BS2 * m);",
+                             "          blk_mul(sum, dinv + BS2 * (int64_t)j, lu2 + BS2 * m);\n"
+                             "          memcpy(lu + BS2 * m, lu2 + BS2 * m, sizeof sum);")],
+    "jacobi_forward_in_place": [("        blk_matvec_add(lu + BS2 * m, y + (int64_t)BS * colidx[m], tv);",
+                                 "        blk_matvec_add(lu + BS2 * m, y2 + (int64_t)BS * colidx[m], tv);")],
+}
+
+
+def _tree(dst):
+    """The pins with what they import, copied into dst."""
+    ign = shutil.ignore_patterns("_build", "__pycache__", "*.so", "*.tmp")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"), ignore=ign)
+    os.makedirs(os.path.join(dst, "paper_2309_11488_gb300"))
+    open(os.path.join(dst, "paper_2309_11488_gb300", "__init__.py"), "w").close()
+    shutil.copy(os.path.join(ROOT, "paper_2309_11488_gb300", "synth.py"), os.path.join(dst, "paper_2309_11488_gb300"))
+    os.makedirs(os.path.join(dst, "tests"))
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests"))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_a_planted_mistake(name, tmp_path):
+    _tree(str(tmp_path))
+    src_path = tmp_path / "oracle" / "oracle.c"
+    src = src_path.read_text()
+    for old, new in MUTANTS[name]:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    src_path.write_text(src)
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        "test_oracle_pins.py"], cwd=tmp_path / "tests", env=env, capture_output=True, text=True,
+                       timeout=900)
+    if name == "control":
+        assert r.returncode == 0, r.stdout[-3000:]
+    else:
+        # 1: a pin failed; negative: the mutant crashed the process.  Anything
+        # else (collection or usage errors) would be the harness's fault.
+        assert r.returncode == 1 or r.returncode < 0, (name, r.returncode, r.stdout[-3000:])

@@ -232,6 +232,34 @@ def test_bicgstab_stopping_rule(rtol):
     assert res.relres <= rtol * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("maker", [synth.config1, lambda: synth.random_pattern_system(300, 6, 12)])
+def test_bicgstab_stops_at_the_first_step_that_meets_the_rule(maker):
+    """BiCGStab's path does not depend on rtol, only where it stops does.
+    One run to 1e-13 gives the residual after every half and full step; for
+    each step whose residual is below all earlier ones, an rtol just above it
+    must stop exactly there (a half-step or a full-step exit), and both kinds
+    of exit must occur among the cases."""
+    s = maker()
+    fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
+    b = rhs(s)
+    full = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=1e-13, maxit=400)
+    assert full.status == 0
+    h = full.res_hist / full.res_hist[0]
+    kinds, running = set(), np.inf
+    for q in range(1, len(h)):
+        if np.isnan(h[q]):
+            break
+        tau = h[q] * (1 + 1e-9)
+        if tau < running:  # every earlier step is above tau: q is the first to meet it
+            r = O.bicgstab(s.nb, s.rowptr, s.colidx, s.vals, fac, b, rtol=tau, maxit=400)
+            k = r.iters
+            stop = 2 * k - 1 if np.isnan(r.res_hist[2 * k]) else 2 * k
+            assert r.status == 0 and stop == q, (q, stop)
+            kinds.add(q % 2)
+        running = min(running, h[q])
+    assert kinds == {0, 1}
+
+
 def test_bicgstab_scaling_and_zero_rhs():
     s = synth.config1()
     fac = O.ilu0(s.nb, s.rowptr, s.colidx, s.vals)
