@@ -57,6 +57,26 @@ MUTANTS = {
     # wells (Section 4.6)
     "wells_added": [("y[(int64_t)BS * wcells[p] + c] -= acc;", "y[(int64_t)BS * wcells[p] + c] += acc;")],
     "wells_B_for_C": [("acc += C[12 * (int64_t)p + 3 * r + c] * t2[r];", "acc += B[12 * (int64_t)p + 3 * r + c] * t2[r];")],
+    # the FP32-factor variant
+    "f32_ilu0_update_added": [("for (int e = 0; e < BS2; ++e) lu[BS2 * mj + e] -= p[e];",
+                               "for (int e = 0; e < BS2; ++e) lu[BS2 * mj + e] += p[e];")],
+    "f32_apply_without_inverse_pivot": [("t += dinv[BS2 * (int64_t)i + a * BS + c] * acc[c];",
+                                         "t += (a == c) ? acc[c] : 0.0f;")],
+    # dense Gaussian elimination (brute force)
+    "dense_solve_rhs_not_swapped": [("      double t = b[col];\n      b[col] = b[piv];\n      b[piv] = t;\n", "")],
+    # smallest-last colouring and the Kempe reduction
+    "smallest_last_not_reversed": [("for (int32_t t = cnt - 1; t >= 0; --t) {\n    int32_t v = order[t];",
+                                    "for (int32_t t = 0; t < cnt; ++t) {\n    int32_t v = order[t];")],
+    "smallest_last_degrees_not_updated": [("        deg[u]--;\n", "")],
+    "kempe_chain_may_reach_a_neighbour": [("if (nbr_of[y] == v || qn == kempe_cap) {", "if (qn == kempe_cap) {")],
+    "kempe_chain_not_exchanged": [("colour[queue[q]] = colour[queue[q]] == a ? b : a;", "colour[queue[q]] = b;")],
+    # order inside a set, and the stable order by key
+    "open_rows_first": [("for (int32_t i = 0; i < nb; ++i) out[i] = 2 * key[i];",
+                         "for (int32_t i = 0; i < nb; ++i) out[i] = 2 * key[i] + 1;"),
+                        ("      if (key[j] > key[i]) out[i] = 2 * key[i] + 1;\n      if (key[i] > key[j]) out[j] = 2 * key[j] + 1;",
+                         "      if (key[j] > key[i]) out[i] = 2 * key[i];\n      if (key[i] > key[j]) out[j] = 2 * key[j];")],
+    "order_by_key_unstable": [("for (int32_t i = 0; i < nb; ++i) perm[start[key[i]]++] = i;",
+                               "for (int32_t i = nb - 1; i >= 0; --i) perm[start[key[i]]++] = i;")],
     # restarted GMRES
     "gmres_rotation_sign": [("H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;", "H[(i + 1) * m + j] = sn[i] * a + cs[i] * c;")],
     # Chow-Patel sweeps and Jacobi triangular sweeps: Gauss-Seidel instead of synchronous

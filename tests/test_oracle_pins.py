@@ -497,13 +497,17 @@ def test_order_by_key_is_stable_and_complete():
     np.testing.assert_array_equal(perm, [1, 3, 6, 2, 5, 0, 4])
 
 
+@pytest.mark.parametrize("maker", [lambda: synth.random_pattern_system(60, 90, seed=11),
+                                   lambda: synth.random_pattern_system(300, 2, 13)])
 @pytest.mark.parametrize("schedule", ["level", "colour", "colour_sl", "colour_kempe"])
-def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
+def test_schedule_order_is_set_major_with_closed_rows_first(schedule, maker):
     """Brute force on the sets the oracle returns: each set is contiguous in
     set order; inside it the rows without a neighbour in a later set come
     first; inside each of those groups the rows with more blocks than the
-    most common count come last; natural order inside each part."""
-    s = synth.random_pattern_system(60, 90, seed=11)
+    most common count come last; natural order inside each part.  The dense
+    pattern mixes long and short rows in a set; the sparse one also mixes
+    closed and open rows, which the check asserts, so that both rules act."""
+    s = maker()
     key, n = {"level": O.levels, "colour": O.colours, "colour_sl": O.colours_sl,
               "colour_kempe": O.colours_kempe}[schedule](s.nb, s.rowptr, s.colidx)
     perm, nsets = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
@@ -521,13 +525,16 @@ def test_schedule_order_is_set_major_with_closed_rows_first(schedule):
     for v in lens:
         counts[v] = counts.get(v, 0) + 1
     common = min(v for v in counts if counts[v] == max(counts.values()))
+    mixed = 0
     for c in range(n):
         rows = [i for i in range(s.nb) if key[i] == c]
         closed = [i for i in rows if all(key[j] <= c for j in nbrs[i])]
         opened = [i for i in rows if any(key[j] > c for j in nbrs[i])]
+        mixed += bool(closed) and bool(opened)
         for grp in (closed, opened):
             expect += [i for i in grp if lens[i] <= common] + [i for i in grp if lens[i] > common]
     assert perm.tolist() == expect
+    assert mixed > 0 or s.nb == 60
     # a closed row has no U block in the permuted matrix
     prow, pcol, _ = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
     for ip in range(s.nb):
