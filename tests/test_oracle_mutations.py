@@ -16,7 +16,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# name -> [(text in oracle.c, replacement)], each text present exactly once
+# name -> [(text in oracle.c, replacement)] or [(file of the oracle, text, replacement)],
+# each text present exactly once in its file
 MUTANTS = {
     "control": [],
     # blocks and the 3x3 inverse
@@ -77,8 +78,29 @@ MUTANTS = {
                          "      if (key[j] > key[i]) out[i] = 2 * key[i];\n      if (key[i] > key[j]) out[j] = 2 * key[j];")],
     "order_by_key_unstable": [("for (int32_t i = 0; i < nb; ++i) perm[start[key[i]]++] = i;",
                                "for (int32_t i = nb - 1; i >= 0; --i) perm[start[key[i]]++] = i;")],
-    # restarted GMRES
+    # SpMV's gather and the value permutation
+    "spmv_reads_the_row_not_the_column": [("blk_matvec_add(vals + BS2 * m, x + (int64_t)BS * colidx[m], yi);",
+                                           "blk_matvec_add(vals + BS2 * m, x + (int64_t)BS * i, yi);")],
+    "permute_drops_the_blocks_values": [("      memcpy(pvals + BS2 * at, vals + BS2 * m, sizeof(double) * BS2);\n",
+                                         "      memcpy(pvals + BS2 * at, vals + BS2 * (rowptr[oi]), sizeof(double) * BS2);\n")],
+    # the Chow-Patel initial guess, the Jacobi backward sweep
+    "chow_patel_guess_without_pivot_inverse": [
+        ("      if (colidx[m] < i) blk_mul(vals + BS2 * m, dinv + BS2 * (int64_t)colidx[m], lu + BS2 * m);\n"
+         "      else memcpy(lu + BS2 * m, vals + BS2 * m, sizeof(double) * BS2);",
+         "      memcpy(lu + BS2 * m, vals + BS2 * m, sizeof(double) * BS2);")],
+    "jacobi_backward_without_inverse_pivot": [
+        ("      double zi[BS] = {0.0, 0.0, 0.0};\n      blk_matvec_add(dinv + BS2 * (int64_t)i, acc, zi);\n"
+         "      memcpy(z2 + (int64_t)BS * i, zi, sizeof zi);",
+         "      memcpy(z2 + (int64_t)BS * i, acc, sizeof acc);")],
+    # block-Jacobi pattern (Section 4.5), in the oracle's Python half
+    "jacobi_pattern_keeps_cross_blocks": [("__init__.py", "keep = part[rows] == part[colidx]",
+                                           "keep = (part[rows] == part[colidx]) | (rows + 1 == colidx)")],
+    "schedule_long_rows_first": [("__init__.py", "key3 = 2 * key2 + (lens > common).astype(np.int32)",
+                                  "key3 = 2 * key2 + (lens <= common).astype(np.int32)")],
+    # restarted GMRES: the end-of-cycle update
     "gmres_rotation_sign": [("H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;", "H[(i + 1) * m + j] = sn[i] * a + cs[i] * c;")],
+    "gmres_cycle_update_unpreconditioned": [("    orc_ilu_apply(nb, rowptr, colidx, lu, dinv, w, z);\n    for (size_t e = 0; e < n; ++e) x[e] += z[e];",
+                                             "    for (size_t e = 0; e < n; ++e) x[e] += w[e];")],
     # Chow-Patel sweeps and Jacobi triangular sweeps: Gauss-Seidel instead of synchronous
     "chow_patel_in_place": [("          blk_mul(sum, dinv + BS2 * (int64_t)j, lu2 + BS2 * m);",
                              "          blk_mul(sum, dinv + BS2 * (int64_t)j, lu2 + BS2 * m);\n"
@@ -101,22 +123,46 @@ def _tree(dst):
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
 
 
-@pytest.mark.parametrize("name", list(MUTANTS))
-def test_pins_catch_a_planted_mistake(name, tmp_path):
-    _tree(str(tmp_path))
-    src_path = tmp_path / "oracle" / "oracle.c"
-    src = src_path.read_text()
-    for old, new in MUTANTS[name]:
-        assert src.count(old) == 1, (name, old)
-        src = src.replace(old, new)
-    src_path.write_text(src)
-    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+def _run(name, root):
+    """Plant mutant `name` in a fresh copy under root and run the pins there;
+    returns (exit code, output tail)."""
+    dst = os.path.join(root, name)
+    _tree(dst)
+    for edit in MUTANTS[name]:
+        fname, old, new = edit if len(edit) == 3 else ("oracle.c", *edit)
+        path = os.path.join(dst, "oracle", fname)
+        with open(path) as f:
+            src = f.read()
+        if src.count(old) != 1:
+            return -1000, f"mutation text not found exactly once: {old!r}"
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+    # one thread each: the runs go side by side, so numpy's BLAS must not fan out
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                        "test_oracle_pins.py"], cwd=tmp_path / "tests", env=env, capture_output=True, text=True,
-                       timeout=900)
+                        "test_oracle_pins.py"], cwd=os.path.join(dst, "tests"), env=env, capture_output=True,
+                       text=True, timeout=900)
+    return r.returncode, r.stdout[-3000:]
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    """Every mutant's pin run, the runs side by side (independent processes)."""
+    from concurrent.futures import ThreadPoolExecutor
+    root = str(tmp_path_factory.mktemp("mutants"))
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futs = {name: ex.submit(_run, name, root) for name in MUTANTS}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_a_planted_mistake(name, results):
+    rc, out = results[name]
+    assert rc != -1000, out
     if name == "control":
-        assert r.returncode == 0, r.stdout[-3000:]
+        assert rc == 0, out
     else:
         # 1: a pin failed; negative: the mutant crashed the process.  Anything
         # else (collection or usage errors) would be the harness's fault.
-        assert r.returncode == 1 or r.returncode < 0, (name, r.returncode, r.stdout[-3000:])
+        assert rc == 1 or rc < 0, (name, rc, out)
