@@ -263,3 +263,26 @@ def test_constants_match_the_header(tmp_path):
     got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines() if ln)
     for name, v in want.items():
         assert int(got[name]) == v, name
+
+
+def test_missing_library_fails_loudly():
+    """Without the compiled library the binding raises ImportError on first
+    use (no CPU fallback): checked in a fresh process pointed at a path that
+    does not exist."""
+    import subprocess
+    import sys
+    code = ("import numpy as np\n"
+            "from paper_2309_11488_gb300 import opm, synth\n"
+            "opm.LIB_PATH = '/nonexistent/libopm_bsr.so'\n"
+            "opm._lib = None\n"
+            "s = synth.config1()\n"
+            "for call in (lambda: opm.lib(), lambda: opm.Solver(s.nb, s.rowptr, s.colidx, s.vals)):\n"
+            "    try:\n"
+            "        call()\n"
+            "    except ImportError as e:\n"
+            "        assert 'no CPU fallback' in str(e)\n"
+            "    else:\n"
+            "        raise SystemExit('no error')\n"
+            "print('ok')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stderr[-2000:]
