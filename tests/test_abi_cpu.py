@@ -286,3 +286,25 @@ def test_missing_library_fails_loudly():
             "print('ok')\n")
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stderr[-2000:]
+
+
+@pytest.mark.parametrize("schedule", ["level", "colour_kempe"])
+def test_block_jacobi_analysis_takes_any_int32_labels(schedule):
+    """Partition labels are arbitrary int32 values (negative, extreme,
+    non-contiguous): only equality matters.  The analysis of a one-way
+    pattern with such labels equals the oracle's, and relabelling the
+    partitions changes nothing."""
+    import oracle as O
+    s = synth.one_way_system(synth.random_pattern_system(240, 4, 51), 0.4, 52)
+    base = (np.arange(s.nb) // 17).astype(np.int64)
+    table = np.array([-2**31, 2**31 - 1, -7, 0, 123456789, -1, 5, 2**30, -2**30, 77, 3, -3, 9, 11, 13],
+                     dtype=np.int64)
+    part = table[base % len(table)].astype(np.int32)
+    st, perm, info = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule, part=part)
+    assert st == opm.OPM_OK
+    jrp, jci = O.jacobi_pattern(s.nb, s.rowptr, s.colidx, s.vals, part)[:2]
+    ref, nsets = O.schedule_perm(s.nb, jrp, jci, schedule)
+    np.testing.assert_array_equal(perm, ref)
+    assert info.nsets == nsets and info.nnzb_kept == int(jrp[-1])
+    st2, perm2, info2 = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule, part=(base % len(table)).astype(np.int32))
+    assert st2 == opm.OPM_OK and np.array_equal(perm2, perm) and info2.nnzb_kept == info.nnzb_kept
