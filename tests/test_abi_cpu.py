@@ -308,3 +308,33 @@ def test_block_jacobi_analysis_takes_any_int32_labels(schedule):
     assert info.nsets == nsets and info.nnzb_kept == int(jrp[-1])
     st2, perm2, info2 = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule, part=(base % len(table)).astype(np.int32))
     assert st2 == opm.OPM_OK and np.array_equal(perm2, perm) and info2.nnzb_kept == info.nnzb_kept
+
+
+def test_the_c_abi_from_plain_c(tmp_path):
+    """A C program compiled against include/opm_bsr.h and linked with the
+    library runs the host-only analysis of a 2x2 grid: levels 0, 1, 1, 2
+    and colours 0, 1, 1, 0 give the permutations below (set-major, closed
+    rows first inside a set), the binding agrees line by line, and a
+    missing diagonal is reported with its row."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    libdir = os.path.dirname(opm.LIB_PATH)
+    exe = tmp_path / "analyse_grid"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "analyse_grid.c"),
+                           "-L", libdir, "-lopm_bsr", f"-Wl,-rpath,{libdir}", "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    lines = out.stdout.splitlines()
+    # the binding gives the same analysis
+    rp = np.array([0, 3, 6, 9, 12], np.int32)
+    ci = np.array([0, 1, 2, 0, 1, 3, 0, 2, 3, 1, 2, 3], np.int32)
+    for line, schedule in zip(lines[:2], ("level", "colour")):
+        st, perm, info = opm.opm_bsr_analyse(4, rp, ci, schedule)
+        assert line == (f"ok schedule={info.schedule} nsets={info.nsets} lower={info.nnzb_lower} "
+                        f"upper={info.nnzb_upper} perm={','.join(str(v) for v in perm)}")
+    assert lines[0].endswith("nsets=3 lower=4 upper=4 perm=0,1,2,3")
+    # colour 0 = {0, 3}, both with a neighbour in colour 1 (open): natural order; then {1, 2}
+    assert lines[1].startswith("ok schedule=3 nsets=2") and lines[1].endswith("perm=0,3,1,2")
+    assert lines[2] == "missing diagonal block row=1"
