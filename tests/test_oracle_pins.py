@@ -666,6 +666,43 @@ def test_one_way_generator_drops_blocks_one_way_and_keeps_the_rest():
     np.testing.assert_array_equal(synth.one_way_system(base, 0.4, 32).colidx, s.colidx)
 
 
+def test_batched_and_serving_workload_recipes():
+    """The batched workload: 256 grids, every axis 5..40, 500..20,000 cells.
+    The serving patterns: cells log-uniform in 5,000..250,000 (up to the
+    rounding of the axes), nz no larger than nx or ny."""
+    d4 = synth.config4_dims(256)
+    cells = [x * y * z for x, y, z in d4]
+    assert len(d4) == 256 and all(5 <= v <= 40 for d in d4 for v in d)
+    assert all(500 <= c <= 20000 for c in cells) and len(set(d4)) > 200
+    d5 = synth.config5_dims(32)
+    c5 = np.array([x * y * z for x, y, z in d5], dtype=float)
+    assert len(d5) == 32 and all(z <= x and z <= y for x, y, z in d5)
+    assert 0.8 * 5000 <= c5.min() and c5.max() <= 1.25 * 250000
+    # the mean of 32 uniform logs on [ln 5e3, ln 2.5e5] has a standard deviation near 0.2
+    assert abs(np.log(c5).mean() - (np.log(5000) + np.log(250000)) / 2) < 0.6
+
+
+def test_one_million_cell_recipe():
+    """The 100^3 workload from first principles: about 5% of the cells
+    inactive, every face between two active cells a connection, and
+    round(1% of the active cells) extra fault connections, each joining two
+    active cells that are not face neighbours, at most 3 cells apart on
+    every axis.  Every connection gives two blocks, every cell one."""
+    s = synth.config3()
+    kji = s.geom["kji"]
+    act = np.zeros(s.geom["shape"], dtype=bool)
+    act[kji[:, 0], kji[:, 1], kji[:, 2]] = True
+    assert abs(s.nb - 950000) < 2000  # binomial standard deviation ~218
+    faces = int((act[1:] & act[:-1]).sum() + (act[:, 1:] & act[:, :-1]).sum() + (act[:, :, 1:] & act[:, :, :-1]).sum())
+    nfault = int(round(0.01 * s.nb))
+    assert s.nnzb == s.nb + 2 * faces + 2 * nfault
+    rows = np.repeat(np.arange(s.nb), np.diff(s.rowptr))
+    off = rows != s.colidx
+    d = np.abs(kji[rows[off]] - kji[s.colidx[off]])
+    far = d.sum(axis=1) > 1
+    assert int(far.sum()) == 2 * nfault and d[far].max() <= 3
+
+
 # ------------------------------------------------------- block-Jacobi ILU0
 
 def test_jacobi_pattern_keeps_exactly_the_partition_internal_blocks():
