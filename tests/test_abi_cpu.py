@@ -338,3 +338,43 @@ def test_the_c_abi_from_plain_c(tmp_path):
     # colour 0 = {0, 3}, both with a neighbour in colour 1 (open): natural order; then {1, 2}
     assert lines[1].startswith("ok schedule=3 nsets=2") and lines[1].endswith("perm=0,3,1,2")
     assert lines[2] == "missing diagonal block row=1"
+
+
+def _one_error(s, kind, row):
+    """s's pattern with exactly one error of `kind` planted in `row`."""
+    rp, ci = s.rowptr.copy(), s.colidx.copy()
+    a, b = int(rp[row]), int(rp[row + 1])
+    if kind == "unsorted":
+        ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    elif kind == "duplicate":
+        ci[a + 1] = ci[a]
+    elif kind == "out_of_range":
+        ci[b - 1] = s.nb + 5
+    elif kind == "negative":
+        ci[a] = -1
+    elif kind == "no_diagonal":
+        d = a + int(np.nonzero(ci[a:b] == row)[0][0])
+        # replace the diagonal by a column the row lacks, keeping the row sorted
+        free = sorted(set(range(s.nb)) - set(ci[a:b].tolist()))
+        ci[d] = min(free, key=lambda c: abs(c - row))
+        ci[a:b] = np.sort(ci[a:b])
+    return rp, ci
+
+
+@pytest.mark.parametrize("kind,status", [("unsorted", "PATTERN"), ("duplicate", "PATTERN"),
+                                         ("out_of_range", "PATTERN"), ("negative", "PATTERN"),
+                                         ("no_diagonal", "NO_DIAG")])
+def test_a_single_pattern_error_is_reported_with_its_row(kind, status):
+    """One error planted in a random row of several seeded patterns: the
+    host analysis returns its status and names that row, for every
+    schedule."""
+    rng = np.random.default_rng(7)
+    want = getattr(opm, f"OPM_ERR_{status}")
+    for seed in range(4):
+        s = synth.random_pattern_system(90, 3, 300 + seed)
+        rows = [i for i in range(s.nb) if s.rowptr[i + 1] - s.rowptr[i] >= 2]
+        row = int(rng.choice(rows))
+        rp, ci = _one_error(s, kind, row)
+        for schedule in ("natural", "level", "colour_kempe"):
+            st, perm, info = opm.opm_bsr_analyse(s.nb, rp, ci, schedule)
+            assert st == want and opm.opm_last_error_row(None) == row, (kind, seed, row, schedule, st)
