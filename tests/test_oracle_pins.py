@@ -595,6 +595,25 @@ def test_level_order_gives_the_natural_factors():
     np.testing.assert_allclose(lev.dinv, nat.dinv[perm], rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("rtol", [1e-2, 1e-8])
+def test_level_order_solves_along_the_natural_path(rtol):
+    """Level order relabels the natural factorisation, so BiCGStab in level
+    order takes the natural-order path: the same residual after every half
+    and full step (to rounding of the reordered sums), the same iteration
+    count, and the same x mapped back."""
+    s = synth.config1()
+    b = rhs(s)
+    x_nat, r_nat, _, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, rtol, 200, "natural")
+    x_lev, r_lev, perm, _ = O.solve_system(s.nb, s.rowptr, s.colidx, s.vals, b, rtol, 200, "level")
+    assert not np.array_equal(perm, np.arange(s.nb))  # the order did change
+    assert r_nat.status == r_lev.status == 0 and r_nat.iters == r_lev.iters
+    hn, hl = r_nat.res_hist, r_lev.res_hist
+    ok = ~np.isnan(hn)
+    np.testing.assert_array_equal(ok, ~np.isnan(hl))
+    np.testing.assert_allclose(hl[ok], hn[ok], rtol=1e-10)
+    np.testing.assert_allclose(x_lev, x_nat, rtol=1e-10, atol=1e-12)
+
+
 def test_colour_order_changes_the_preconditioner_but_still_solves():
     s = synth.config2()
     b = rhs(s)
