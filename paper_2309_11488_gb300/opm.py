@@ -41,8 +41,8 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_get_info", "opm_get_permutation", "opm_get_factors", "opm_get_timing",
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
-           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch", "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve",
-           "opm_bsr_analyse"]
+           "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch",
+           "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve", "opm_bsr_analyse"]
 
 
 class opm_options(ctypes.Structure):
