@@ -378,3 +378,20 @@ def test_a_single_pattern_error_is_reported_with_its_row(kind, status):
         for schedule in ("natural", "level", "colour_kempe"):
             st, perm, info = opm.opm_bsr_analyse(s.nb, rp, ci, schedule)
             assert st == want and opm.opm_last_error_row(None) == row, (kind, seed, row, schedule, st)
+
+
+def test_binding_defaults_are_the_papers_stopping_rule():
+    """The binding's default rtol and maxit are the stopping rule printed in
+    the paper (tests/golden/paper_facts.txt: relative reduction 0.01, at
+    most 200 iterations)."""
+    import inspect
+    facts = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_facts.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                facts[k] = float(v)
+    for fn in (opm.Solver.solve, opm.Batch.solve, opm.opm_bicgstab_solve):
+        sig = inspect.signature(fn).parameters
+        assert sig["rtol"].default == facts["default_rtol"] and sig["maxit"].default == facts["default_maxit"], fn

@@ -720,6 +720,23 @@ def test_one_million_cell_recipe():
     d = np.abs(kji[rows[off]] - kji[s.colidx[off]])
     far = d.sum(axis=1) > 1
     assert int(far.sum()) == 2 * nfault and d[far].max() <= 3
+    # a stand-in for the paper's BigModel: its size and its blocks per row
+    facts = paper_facts()
+    assert 0.8 < s.nb / facts["bigmodel_active_cells"] < 1.2
+    assert abs(s.nnzb / s.nb / facts["bigmodel_nnz_per_row"] - 1) < 0.1
+
+
+def test_defaults_are_the_papers_stopping_rule():
+    """The oracle's default rtol and maxit are the stopping rule the paper
+    states (relative reduction 0.01, at most 200 iterations); the blocks
+    are 3x3."""
+    import inspect
+    facts = paper_facts()
+    for fn in (O.bicgstab, O.solve_system):
+        sig = inspect.signature(fn).parameters
+        assert sig["rtol"].default == facts["default_rtol"] and sig["maxit"].default == facts["default_maxit"], fn
+    s = synth.config1()
+    assert s.vals.shape[1] == facts["block_size"] ** 2 and s.x_true.size == facts["block_size"] * s.nb
 
 
 # ------------------------------------------------------- block-Jacobi ILU0
