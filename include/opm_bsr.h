@@ -486,14 +486,24 @@ opm_status opm_autotune_batch(int32_t nsys, const int32_t *nb, const int32_t *co
  * caller's own BSR arrays, without a handle and without allocating.
  *   nb <= 2,097,152 block rows, else OPM_ERR_ARG; rowptr, colidx, vals (the
  *   layout of opm_bsr_create), x, b, r (3*nb doubles) and norms (2 doubles)
- *   must all be device memory of the current device, else OPM_ERR_ARG.
- *   Work is issued on stream (NULL = default stream) and has completed when
- *   the call returns.  Returns OPM_OK, OPM_ERR_ARG or OPM_ERR_CUDA.
+ *   must all be device memory of the current device (host memory and
+ *   another GPU's memory are refused with OPM_ERR_ARG).
+ *   The pattern must be well formed: rowptr[0] = 0, non-decreasing, and
+ *   rowptr[nb] no larger than the number of blocks in colidx and vals; each
+ *   column in [0, nb).  It is not copied to the host for checking.  The
+ *   kernel takes a row with a negative start or an end before its start as
+ *   empty and skips a column outside [0, nb); either makes both norms NaN
+ *   and the call return OPM_ERR_PATTERN.  A rowptr[nb] past the end of the
+ *   caller's arrays cannot be detected.
+ *   Work is issued on stream (NULL = default stream); the call synchronises
+ *   that stream before it returns.  Returns OPM_OK, OPM_ERR_ARG,
+ *   OPM_ERR_PATTERN or OPM_ERR_CUDA.
  * Its scratch is a fixed 131,328-byte array in device memory that every GPU
  * using the library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture.  All
- * calls share the array: calls that overlap on the GPU race and must be
+ * device current) and keeps it; make that first call before any stream
+ * capture.  Calls after a cudaDeviceReset of that device are not supported.
+ * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.
  */
 opm_status opm_bsr_residual_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *colidx,

@@ -9,13 +9,21 @@
 // ||r||_2, ||b||_2 on the caller's own BSR arrays without creating a handle
 // and without allocating anything.
 //
-// Its only scratch (one partial sum pair per 256-row tile and the
-// last-CTA counter) is the file-scope array below: every GPU that loads the
-// library holds these 131,328 bytes until the process exits, every call
-// shares them, and they keep the last call's contents.  The counter is
-// cleared at the start of every call.  Calls that overlap on the GPU (on two
-// streams, or from two host threads) race on the array and give wrong
-// results: serialise them.
+// Its only scratch (one partial sum pair per 256-row tile, the last-CTA
+// counter and a pattern-error word) is the file-scope array below: every GPU
+// that loads the library holds these 131,328 bytes until the process exits,
+// every call shares them, and they keep the last call's contents.  The
+// counter and the error word are cleared at the start of every call.  Calls
+// that overlap on the GPU (on two streams, or from two host threads) race on
+// the array and give wrong results: serialise them.
+//
+// The caller's pattern is not validated on the host (that would need a copy
+// of it).  The kernel checks what it can before each access: a row whose
+// start is negative or whose end lies before its start is taken as empty, a
+// column outside [0, nb) is skipped; either sets the error word, the norms
+// become NaN and the call returns OPM_ERR_PATTERN.  rowptr[nb] beyond the
+// length of colidx and vals cannot be detected without that length: a
+// well-formed pattern is the caller's precondition.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,7 +36,7 @@ namespace {
 
 constexpr int kNaTile = 256;                   // rows per CTA
 constexpr int kNaMaxTiles = 8192;              // => at most 2,097,152 block rows
-constexpr size_t kNaCounterBytes = 256;        // counter, padded to its own lines
+constexpr size_t kNaCounterBytes = 256;        // counter and error word, padded to their own lines
 constexpr size_t kNaScratchBytes = kNaCounterBytes + sizeof(double) * 2 * kNaMaxTiles;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
@@ -38,7 +46,9 @@ std::mutex g_setup_mutex;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array for the current device (looked up once
-// per device, with that device current).
+// per device, with that device current, and kept: calls after a
+// cudaDeviceReset of that device are not supported, since the reloaded
+// module may place the array elsewhere).
 opm_status scratch_address(unsigned char **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -58,18 +68,23 @@ opm_status scratch_address(unsigned char **out) {
   return OPM_OK;
 }
 
+// True for device (or managed) memory of the current device; host memory
+// and another GPU's memory are refused.
 bool on_device(const void *p) {
   cudaPointerAttributes at;
-  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+  int dev = -1;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 // One thread per block row of the caller's BSR matrix (row-major 3x3 blocks):
 // r_i = b_i - sum_j A_ij x_j; per-CTA partials of ||r||^2 and ||b||^2 in the
-// scratch array; the last CTA sums them in tile order.
+// scratch array; the last CTA sums them in tile order.  Pattern faults that
+// can be seen from the row (see the file header) skip the access and set the
+// error word; the last CTA then writes NaN norms.
 __global__ void __launch_bounds__(kNaTile) k_residual_noalloc(int32_t nb, const int32_t *__restrict__ rowptr,
                                                               const int32_t *__restrict__ colidx,
                                                               const double *__restrict__ vals,
@@ -77,14 +92,25 @@ __global__ void __launch_bounds__(kNaTile) k_residual_noalloc(int32_t nb, const 
                                                               const double *__restrict__ b, double *__restrict__ r,
                                                               double *__restrict__ norms, unsigned char *scratch) {
   unsigned int *counter = reinterpret_cast<unsigned int *>(scratch);
+  unsigned int *bad = counter + 1;
   double *partials = reinterpret_cast<double *>(scratch + kNaCounterBytes);
   const int i = blockIdx.x * kNaTile + threadIdx.x;
   double rr = 0.0, bb = 0.0;
   if (i < nb) {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    for (int m = rowptr[i]; m < rowptr[i + 1]; ++m) {
+    int m0 = rowptr[i], m1 = rowptr[i + 1];
+    if (m0 < 0 || m1 < m0) {
+      atomicOr(bad, 1u);
+      m1 = m0;
+    }
+    for (int m = m0; m < m1; ++m) {
+      const int c = colidx[m];
+      if (c < 0 || c >= nb) {
+        atomicOr(bad, 1u);
+        continue;
+      }
       const double *a = vals + 9ll * m;
-      const int64_t j = 3ll * colidx[m];
+      const int64_t j = 3ll * c;
       const double x0 = x[j], x1 = x[j + 1], x2 = x[j + 2];
       y0 = fma(a[0], x0, fma(a[1], x1, fma(a[2], x2, y0)));
       y1 = fma(a[3], x0, fma(a[4], x1, fma(a[5], x2, y1)));
@@ -128,8 +154,9 @@ __global__ void __launch_bounds__(kNaTile) k_residual_noalloc(int32_t nb, const 
     a += __ldcg(partials + 2 * t);
     c += __ldcg(partials + 2 * t + 1);
   }
-  norms[0] = sqrt(a);
-  norms[1] = sqrt(c);
+  const bool faulty = __ldcg(bad) != 0u;
+  norms[0] = faulty ? nan("") : sqrt(a);
+  norms[1] = faulty ? nan("") : sqrt(c);
   *counter = 0;
 }
 
@@ -156,14 +183,17 @@ extern "C" opm_status opm_bsr_residual_noalloc(int32_t nb, const int32_t *rowptr
   opm_status s = scratch_address(&scratch);
   if (s != OPM_OK) return s;
   const int tiles = (nb + kNaTile - 1) / kNaTile;
-  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st) != cudaSuccess) {
+  if (cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
     cudaGetLastError();
     return OPM_ERR_CUDA;
   }
   k_residual_noalloc<<<tiles, kNaTile, 0, st>>>(nb, rowptr, colidx, vals, x, b, r, norms, scratch);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+  unsigned int bad = 0;  // host copy of the error word (a pageable copy allocates no device memory)
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&bad, scratch + sizeof(unsigned int), sizeof bad, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return OPM_ERR_CUDA;
   }
-  return OPM_OK;
+  return bad ? OPM_ERR_PATTERN : OPM_OK;
 }
