@@ -48,6 +48,11 @@ MUTANTS = {
     "bicgstab_stops_late": [("    if (nr <= tol) {", "    if (nr <= 0.5 * tol) {")],
     "bicgstab_half_step_stops_late": [("    if (ns <= tol) { /* half-step exit */", "    if (ns <= 0.5 * tol) {")],
     "bicgstab_stops_early": [("    if (nr <= tol) {", "    if (nr <= 2.0 * tol) {")],
+    # the four breakdown tests: without one, the method divides by an exact zero
+    "bicgstab_rho_zero_unchecked": [("if (rho == 0.0) {", "if (rho != rho) {")],
+    "bicgstab_rhv_zero_unchecked": [("if (rhv == 0.0) {", "if (rhv != rhv) {")],
+    "bicgstab_tt_zero_unchecked": [("if (tt == 0.0) {", "if (tt != tt) {")],
+    "bicgstab_omega_zero_unchecked": [("if (omega == 0.0) {", "if (omega != omega) {")],
     # schedules (Section 4.4)
     "levels_not_incremented": [("if (j < i && level[j] + 1 > l) l = level[j] + 1;",
                                 "if (j < i && level[j] > l) l = level[j];")],
@@ -118,7 +123,7 @@ def _tree(dst):
     open(os.path.join(dst, "paper_2309_11488_gb300", "__init__.py"), "w").close()
     shutil.copy(os.path.join(ROOT, "paper_2309_11488_gb300", "synth.py"), os.path.join(dst, "paper_2309_11488_gb300"))
     os.makedirs(os.path.join(dst, "tests"))
-    for f in ("conftest.py", "test_oracle_pins.py"):
+    for f in ("conftest.py", "test_oracle_pins.py", "test_oracle_breakdown.py", "breakdown_fixture.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests"))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
 
@@ -141,7 +146,7 @@ def _run(name, root):
     env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                        "test_oracle_pins.py"], cwd=os.path.join(dst, "tests"), env=env, capture_output=True,
+                        "test_oracle_pins.py", "test_oracle_breakdown.py"], cwd=os.path.join(dst, "tests"), env=env, capture_output=True,
                        text=True, timeout=900)
     return r.returncode, r.stdout[-3000:]
 
