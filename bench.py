@@ -71,13 +71,19 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the C1 / C2 (L2-resident) leg")
+    p.add_argument("--no-tight", action="store_true", help="skip the rtol 1e-6 leg")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--patterns", type=int, default=32)
     p.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
-    p.add_argument("--serve-s", type=float, default=10.0, help="serving: measured seconds")
-    p.add_argument("--serve-warm-s", type=float, default=2.0)
+    p.add_argument("--serve-s", type=float, default=60.0, help="serving: measured seconds")
+    p.add_argument("--serve-warm-s", type=float, default=20.0)
     p.add_argument("--hbm-budget-gb", type=float, default=8.0)
+    p.add_argument("--class-size", type=int, default=8, help="serving: patterns per size class")
+    p.add_argument("--lanes-per-class", type=int, default=2, help="serving: lanes per size class")
+    p.add_argument("--sat-requests", type=int, default=4000, help="serving: requests of the saturating run")
+    p.add_argument("--bound-budget-gb", type=float, default=2.0, help="serving: budget of the bound run")
+    p.add_argument("--bound-s", type=float, default=10.0, help="serving: seconds of the bound run")
     p.add_argument("--ref-budget-s", type=float, default=90.0,
                    help="reference arm: seconds the timed oracle steps may take")
     return p.parse_args()
@@ -189,6 +195,51 @@ def iteration_work(info, fp32: bool):
     nbytes = 2 * matrix + 2 * factor + 27 * 24 * n
     fma = 18 * nnzb + (0 if fp32 else 18 * nnzb) + 36 * n
     return nbytes, fma
+
+
+def factor_work(info, fp32: bool):
+    """Algorithmic work of one refactorisation with the value permutation
+    fused (Algorithm 2 with Algorithm 3's index copy).  Bytes: the caller's
+    blocks read once through their gather index (72 + 4 per block); the
+    permuted copy of A written (72 per block); every factor slot written
+    once (9 values per kept block, with its 8-byte slot location); per L
+    block its column and update-list pointer (8) and one gathered inverse
+    pivot (9 values); per update product its two slots (16) and one gathered
+    U block (9 values); the row pointers of A and L.  FP64 FMAs (FP64
+    factors; with FP32 factors the arithmetic is FP32): 27 per L block (the
+    product with the inverse pivot), 27 per update product, about 30 per
+    3x3 pivot inverse."""
+    n, nnzb, nl, nu = info.nb, info.nnzb, info.nnzb_lower, info.nupdates
+    val = 4 if fp32 else 8
+    kept = nl + info.nnzb_upper + n
+    nbytes = 76 * nnzb + 72 * nnzb + (9 * val + 8) * kept + (8 + 9 * val) * nl + (16 + 9 * val) * nu \
+        + 2 * 4 * (n + 1)
+    fma = 0 if fp32 else 27 * nl + 27 * nu + 30 * n
+    return int(nbytes), int(fma)
+
+
+def kernel_work(info, fp32: bool):
+    """Algorithmic HBM bytes and FP64 FMAs per launch of the other kernel
+    groups.  A matrix pass is 76 bytes per block (9 values and a column
+    index) plus the row pointers; vectors are 24 bytes per row.
+      spmv (v = A p^ with (r^, v); t = A s^ with (t, s), (t, t), (s, s)):
+        a matrix pass, 3 vector passes; 9 FMAs per block, 3 or 9 per row
+        (the average of the two kinds is reported);
+      update (x += alpha p^ + omega s^, r = s - omega t, ||r||, (r^, r)):
+        6 vectors read, 2 written; 15 FMAs per row;
+      finish (true residual and x back to the caller's order): a matrix
+        pass, x gathered, b and the permutation read, x written; 9 FMAs per
+        block and 3 per row;
+      setup (b gathered through the permutation; r, r^, x, p, v written):
+        6 vector passes and the permutation; 3 FMAs per row."""
+    n, nnzb = info.nb, info.nnzb
+    mat = 76 * nnzb + 4 * (n + 1)
+    return {"factor": factor_work(info, fp32),
+            "apply": (algorithmic_apply_bytes(info, fp32), 0 if fp32 else int(9 * nnzb + 4.5 * n)),
+            "spmv": (mat + 72 * n, 9 * nnzb + 6 * n),
+            "update": (192 * n, 15 * n),
+            "setup": (148 * n, 3 * n),
+            "finish": (mat + 76 * n, 9 * nnzb + 3 * n)}
 
 
 def kernel_source_hash() -> str:
@@ -307,15 +358,21 @@ def run_ours(args, rank, world, dist):
             step(sv)
         sv.reset_timing()
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # an event after every step: the whole region gives the rate, the
+        # per-step times its spread
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         with ClockSampler(local) as clk:
-            e0.record()
-            for _ in range(args.steps):
+            evs[0].record()
+            for k in range(args.steps):
                 step(sv)
-            e1.record()
+                evs[k + 1].record()
             torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = evs[0].elapsed_time(evs[-1])
+        per = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
+        spread = {"median_ms": round(float(np.median(per)), 4), "p10_ms": round(float(np.percentile(per, 10)), 4),
+                  "p90_ms": round(float(np.percentile(per, 90)), 4), "min_ms": round(float(per.min()), 4),
+                  "max_ms": round(float(per.max()), 4), "steps": int(args.steps)}
         launches = sv.timing().launches
         err = float(np.linalg.norm(x.cpu().numpy() - s.x_true) / np.linalg.norm(s.x_true))
         # per-kernel device time from a second handle that records events
@@ -328,7 +385,7 @@ def run_ours(args, rank, world, dist):
                 step_profiled(sp)
             t = sp.timing()
         return sv, dict(ms=ms, timing=t, launches=launches, info=info, clocks=clk.summary(), err=err, options=kw,
-                        autotune=tune, **stat)
+                        autotune=tune, spread=spread, **stat)
 
     sv64, r64 = measure("fp64")
     sv32, r32 = measure("fp32")
@@ -433,11 +490,27 @@ def run_ours(args, rank, world, dist):
                              "peak_tflops": round(2 * FP64_FMA_PEAK / 1e12, 4), "frac": round(fmas / FP64_FMA_PEAK, 4),
                              "peak_source": "derived: 2 FP64 FMA lanes/SM/clock x 152 SMs x 2.07 GHz"}}
 
-    def kernels(r):
+    def kernels(r, precision):
+        """Per-kernel device time from the profiled handle, with each kernel
+        group's algorithmic bytes and FP64 FMAs per launch against the
+        measured HBM copy bandwidth and the derived FP64 FMA peak."""
         t = r["timing"]
-        return {k: {"ms_total": round(t.kernel_ms[q], 3), "launches": int(t.kernel_count[q]),
-                    "avg_us": round(1e3 * t.kernel_ms[q] / max(t.kernel_count[q], 1), 2)}
-                for q, k in enumerate(opm.KERNELS)}
+        work = kernel_work(r["info"], precision == "fp32")
+        peak, src = peaks()
+        out = {}
+        for q, k in enumerate(opm.KERNELS):
+            avg_ms = t.kernel_ms[q] / max(t.kernel_count[q], 1)
+            e = {"ms_total": round(t.kernel_ms[q], 3), "launches": int(t.kernel_count[q]),
+                 "avg_us": round(1e3 * avg_ms, 2)}
+            if k in work and avg_ms > 0:
+                nbytes, fma = work[k]
+                e.update({"bytes_per_launch": nbytes, "hbm_frac": round(nbytes / (avg_ms * 1e-3) / 1e9 / peak, 4),
+                          "fmas_per_launch": fma, "fp64_frac": round(fma / (avg_ms * 1e-3) / FP64_FMA_PEAK, 4)})
+            out[k] = e
+        out["peaks"] = {"hbm_gbs": peak, "hbm_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                        "fp64_fma_per_s": FP64_FMA_PEAK,
+                        "fp64_source": "derived: 2 FP64 FMA lanes/SM/clock x 152 SMs x 2.07 GHz"}
+        return out
 
     out = {
         "metric": METRIC,
@@ -447,6 +520,7 @@ def run_ours(args, rank, world, dist):
         "steps": args.steps,
         "warmup": max(3, args.warmup),
         "ms_per_step": round(ms64 / args.steps, 4),
+        "step_spread": r64["spread"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -469,12 +543,13 @@ def run_ours(args, rank, world, dist):
                                "x_equal_to_one_handle": bool(x_ok)}},
         "gpu_launches": int(r64["launches"]),
         "clocks": r64["clocks"],
-        "kernels": kernels(r64),
+        "kernels": kernels(r64, "fp64"),
         "iteration": iteration(r64, ms64, "fp64"),
         "fp32_factors": {"value": round(world * args.steps / (ms32 * 1e-3), 3), "unit": UNIT,
-                         "ms_per_step": round(ms32 / args.steps, 4), "iters": r32["iters"],
+                         "ms_per_step": round(ms32 / args.steps, 4), "step_spread": r32["spread"],
+                         "iters": r32["iters"],
                          "relres": r32["relres"], "x_err_vs_x_true": r32["err"], "dtype": "f64 Krylov + f32 factors",
-                         "roofline": roofline(r32, "fp32"), "kernels": kernels(r32), "options": r32["options"],
+                         "roofline": roofline(r32, "fp32"), "kernels": kernels(r32, "fp32"), "options": r32["options"],
                          "iteration": iteration(r32, ms32, "fp32"),
                          "autotune": r32["autotune"], "gpu_launches": int(r32["launches"]), "clocks": r32["clocks"]},
         "autotune": r64["autotune"],
@@ -482,6 +557,9 @@ def run_ours(args, rank, world, dist):
     sv64.close()
     sv32.close()
     del vals_h, b_h, x_h
+    tight_x = None
+    if not args.no_tight:
+        out["c3_rtol1e-6"], tight_x = measure_tight(args, s, r64, r32, barrier, max_over_ranks, world)
     if not args.no_jacobi:
         out["block_jacobi"] = measure_jacobi(args, s, barrier, max_over_ranks, world)
     if not args.no_wells:
@@ -501,6 +579,8 @@ def run_ours(args, rank, world, dist):
         out["serving"] = measure_serving(args, barrier, max_over_ranks, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s, n_solves=2)
+        if tight_x is not None:
+            out["c3_rtol1e-6"]["cpu_baseline"] = cpu_baseline_tight(s, out["c3_rtol1e-6"]["schedule"], tight_x)
     return out
 
 
@@ -603,6 +683,82 @@ def measure_gmres(args, s, options, barrier, max_over_ranks, world):
             res[name] = {"solves_per_s": round(world * reps / dt, 2), "iters": it, "status": st, "relres": rr,
                          "preconditioner_applications": it + (1 if name == "gmres" else it)}
     return res
+
+
+RTOL_TIGHT = 1e-6
+
+
+def measure_tight(args, s, r64, r32, barrier, max_over_ranks, world):
+    """The iteration-dominated regime: the same workload and launch options
+    at rtol 1e-6 (about five times the iterations of rtol 1e-3), FP64 and
+    FP32 factors.  Each step is one refactorisation + solve through
+    opm_solve_launch / opm_solve_wait, event-timed.  The iteration share is
+    the step's time outside the refactorisation, setup and final residual
+    (their profiled averages from the headline run).  Returns the figures
+    and the two solutions (host arrays) for the oracle comparison."""
+    import torch
+    from paper_2309_11488_gb300 import opm
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals, xt = dev(s.rowptr), dev(s.colidx), dev(s.vals), dev(s.x_true)
+    reps = max(5, args.steps // 2)
+    out, xs = {}, {}
+    for precision, r in (("fp64", r64), ("fp32", r32)):
+        with opm.Solver(s.nb, rp, ci, vals, precision=precision, **r["options"]) as sv:
+            b = sv.spmv(xt)
+            x = torch.empty_like(b)
+            for _ in range(2):
+                sv.launch(vals, b, x, rtol=RTOL_TIGHT, maxit=200)
+                st, it, rr = sv.wait()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                sv.launch(vals, b, x, rtol=RTOL_TIGHT, maxit=200)
+                st, it, rr = sv.wait()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1)) / reps
+            barrier()
+            t = r["timing"]
+            avg = lambda q: t.kernel_ms[q] / max(t.kernel_count[q], 1)
+            outside = avg(0) + avg(4) + avg(5)
+            xs[precision] = x.cpu().numpy()
+            nbytes, _ = iteration_work(r["info"], precision == "fp32")
+            t_it = (ms - outside) / max(it, 1)
+            peak, src = peaks()
+            out[precision] = {"value": round(world * 1e3 / ms, 3), "unit": UNIT, "ms_per_step": round(ms, 4),
+                              "iters": it, "status": st, "relres": rr,
+                              "iteration_share": round(1.0 - outside / ms, 4),
+                              "ms_per_iteration": round(t_it, 4),
+                              "iteration_hbm_frac": round(nbytes / (t_it * 1e-3) / 1e9 / peak, 4),
+                              "x_err_vs_x_true": float(np.linalg.norm(xs[precision] - s.x_true)
+                                                       / np.linalg.norm(s.x_true))}
+    out["schedule"] = {v: k for k, v in opm.SCHEDULES.items()}[r64["info"].schedule]
+    out["rtol"] = RTOL_TIGHT
+    return out, xs
+
+
+def cpu_baseline_tight(s, schedule, xs):
+    """The oracle at rtol 1e-6 in the library's order, one full step on one
+    host core: its rate, and the GPU solutions' distance from its x (the FP64
+    path's parity at this rtol, the FP32-factor path's accuracy)."""
+    import oracle as O
+    b = O.spmv(s.nb, s.rowptr, s.colidx, s.vals, s.x_true)
+    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
+    pb = b.reshape(-1, 3)[perm].ravel()
+    t0 = time.perf_counter()
+    prow, pcol, pval = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    fac = O.ilu0(s.nb, prow, pcol, pval)
+    res = O.bicgstab(s.nb, prow, pcol, pval, fac, pb, RTOL_TIGHT, 200)
+    dt = time.perf_counter() - t0
+    x = np.empty(3 * s.nb)
+    x.reshape(-1, 3)[perm] = res.x.reshape(-1, 3)
+    nx = np.linalg.norm(x)
+    return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "iters": res.iters,
+            "sample": f"1 full step at rtol 1e-6 ({res.iters} iterations) in the {schedule} order, "
+                      f"single-threaded C",
+            "x_err_fp64_vs_oracle": float(np.linalg.norm(xs["fp64"] - x) / nx),
+            "x_err_fp32_factors_vs_oracle": float(np.linalg.norm(xs["fp32"] - x) / nx)}
 
 
 def small_config_cases():
@@ -834,26 +990,46 @@ def measure_batched(args, barrier, max_over_ranks, world):
 def measure_serving(args, barrier, max_over_ranks, world):
     """Poisson request stream over 32 sparsity patterns of 5k-250k cells; each
     request is a Newton-step value update (blocks scaled by U(0.9, 1.1)) that
-    needs ILU0 refactorisation + BiCGStab to rtol 1e-2; factors stay resident
-    per pattern; admission by an HBM budget; latency = completion - arrival."""
+    needs ILU0 refactorisation + BiCGStab to rtol 1e-2.  Analyses are kept per
+    pattern, instances stay resident in lanes admitted by an HBM budget, and
+    the ready requests of a size class share one batched launch; latency =
+    completion - arrival.  Three runs after the warm one: the offered rate
+    (the headline p50/p99), a saturating stream (offered far above capacity:
+    the serving capacity), and a short run under a budget that binds (lanes
+    evicted and remade from the kept analyses)."""
     import torch
     from paper_2309_11488_gb300 import serve, synth
     pats = [synth.config5_pattern(p) for p in range(args.patterns)]
     tmpl = serve.request_templates(pats, 2, "fp32")
-    eng = serve.ServingEngine(pats, precision="fp32", hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)),
-                              max_instances_per_pattern=4)
-    eng.warm()
 
-    def requests(duration, seed):
-        t = serve.poisson_arrivals(args.rate, duration, seed)
+    def requests(rate, duration, seed):
+        t = serve.poisson_arrivals(rate, duration, seed)
         pick = serving_picks(len(pats), len(t), seed)
         return [serve.Request(i, float(ti), int(pick[i]), *tmpl[int(pick[i])][i % 2]) for i, ti in enumerate(t)]
 
-    eng.run(requests(args.serve_warm_s, 31))          # warm: instances, clocks
+    def engine(budget_gb, class_size, lanes):
+        return serve.ServingEngine(pats, precision="fp32", hbm_budget_bytes=int(budget_gb * (1 << 30)),
+                                   class_size=class_size, lanes_per_class=lanes)
+
+    eng = engine(args.hbm_budget_gb, args.class_size, args.lanes_per_class)
+    t0 = time.perf_counter()
+    eng.warm()
+    warm_setup_s = time.perf_counter() - t0
+    eng.run(requests(args.rate, args.serve_warm_s, 31))          # warm: lanes, clocks
     barrier()
-    stats = eng.run(requests(args.serve_s, 32))
+    stats = eng.run(requests(args.rate, args.serve_s, 32))
     barrier()
     summ = stats.summary()
+    sat_rate = 1e6  # every request arrives within a few ms: the run measures the capacity
+    sat = eng.run(requests(sat_rate, args.sat_requests / sat_rate, 33)).summary()
+    barrier()
+    eng.close()
+    # a budget below one lane per class (classes of half the size, one lane
+    # each): lanes are evicted and remade while the run goes on
+    bound_gb = args.bound_budget_gb
+    eng = engine(bound_gb, max(1, args.class_size // 2), 1)
+    eng.warm()
+    bound = eng.run(requests(args.rate, args.bound_s, 34)).summary()
     eng.close()
     if world == 1 and not args.no_cpu_baseline:
         try:
@@ -864,8 +1040,21 @@ def measure_serving(args, barrier, max_over_ranks, world):
     summ.update({"workload": f"{len(pats)} patterns of {min(cells)}..{max(cells)} cells, Poisson arrivals "
                              f"{args.rate:g} req/s for {args.serve_s:g} s (after {args.serve_warm_s:g} s warm), "
                              f"refactor + BiCGStab rtol 1e-2 per request, FP32 factors + FP64 Krylov",
-                 "hbm_budget_bytes": eng.budget, "offered_rate": args.rate,
-                 "solves_per_s_all_ranks": round(world * summ["solves_per_s"], 2)})
+                 "engine": f"size classes of {args.class_size} patterns, up to {args.lanes_per_class} lanes per "
+                           f"class, analyses kept per pattern, ready requests of a class in one batched launch",
+                 "analysis_and_warm_lanes_s": round(warm_setup_s, 2),
+                 "hbm_budget_bytes": int(args.hbm_budget_gb * (1 << 30)), "offered_rate": args.rate,
+                 "solves_per_s_all_ranks": round(world * summ["solves_per_s"], 2),
+                 "max_solves_per_s": round(sat["solves_per_s"], 2),
+                 "saturated": {**{k: sat[k] for k in ("requests", "completed", "failed", "solves_per_s", "p50_ms",
+                                                      "p99_ms", "mean_batch", "launches", "max_in_flight")},
+                               "offered_rate": sat_rate},
+                 "budget_bound": {**{k: bound[k] for k in ("requests", "completed", "failed", "solves_per_s",
+                                                           "p50_ms", "p99_ms", "max_ms", "evictions",
+                                                           "lanes_created_in_run", "hbm_bytes_peak")},
+                                  "hbm_budget_bytes": int(bound_gb * (1 << 30)), "seconds": args.bound_s,
+                                  "engine": f"size classes of {max(1, args.class_size // 2)} patterns, one lane "
+                                            f"per class"}})
     return summ
 
 

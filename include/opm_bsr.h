@@ -48,6 +48,7 @@ extern "C" {
 
 typedef struct opm_solver *opm_handle; /* opaque, owned by the library */
 typedef struct opm_batch_s *opm_batch; /* opaque set of handles solved together */
+typedef struct opm_analysis_s *opm_analysis; /* opaque symbolic analysis kept on the host */
 
 typedef enum {
   OPM_OK = 0,
@@ -222,9 +223,42 @@ typedef struct opm_analysis_info {
   int64_t nnzb_kept;   /* blocks in the preconditioner's pattern             */
   int64_t nnzb_lower;  /* strictly lower kept blocks of the permuted matrix  */
   int64_t nnzb_upper;
+  int64_t nupdates;    /* ILU0 update products A_ij -= L_ik U_kj per
+                          factorisation (Algorithm 2's inner loop)           */
 } opm_analysis_info;
 opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
                            int32_t schedule, int32_t *perm, opm_analysis_info *info);
+
+/*
+ * A kept symbolic analysis (Section 4.4: the pattern, hence its analysis,
+ * stays the same for the whole simulation).  opm_analysis_create runs the
+ * analysis of opm_bsr_create (or, with part non-NULL, of
+ * opm_bsr_create_jacobi) once and keeps its result in host memory;
+ * opm_bsr_create_from_analysis then makes handles of that pattern without
+ * analysing again: it allocates the handle's device memory, uploads the
+ * kept schedule, layouts and update lists, and factorises vals.  A server
+ * that frees a pattern's device memory (destroying its handles) and later
+ * needs the pattern again pays the upload and the first factorisation, not
+ * the analysis.
+ *   opm_analysis_create: rowptr, colidx, part as in opm_bsr_analyse (host
+ *     or device memory); schedule: OPM_SCHED_*.  Returns OPM_OK, OPM_ERR_ARG,
+ *     a pattern error (row via opm_last_error_row(NULL)) or OPM_ERR_OOM.
+ *   opm_bsr_create_from_analysis: vals as in opm_bsr_create (host or device,
+ *     9*nnzb doubles, the caller's block order); opt as in opm_bsr_create
+ *     except that its schedule is ignored (the analysis fixed it).  Returns
+ *     the statuses of opm_bsr_create.  The analysis may be destroyed while
+ *     handles made from it live: they hold their own copies.
+ *   opm_analysis_get_info: the analysis's counts (opm_bsr_analyse's info)
+ *     and, when perm is non-NULL, its permutation (nb entries).
+ * The analysis object is used by one host thread at a time.
+ */
+opm_status opm_analysis_create(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                               int32_t schedule, opm_analysis *out);
+opm_status opm_bsr_create_from_analysis(opm_analysis a, const double *vals, const opm_options *opt,
+                                        opm_handle *out);
+opm_status opm_analysis_get_info(opm_analysis a, int32_t *nb, int64_t *nnzb, int32_t *perm,
+                                 opm_analysis_info *info);
+void opm_analysis_destroy(opm_analysis a);
 
 /*
  * Restarted GMRES(m) (Section 2 names restarted GMRES as OPM's other Krylov
@@ -325,6 +359,8 @@ typedef struct opm_info {
                           (the levels or colours; for natural order, runs of
                           consecutive independent rows)                      */
   int32_t reserved;
+  int64_t nupdates;    /* ILU0 update products A_ij -= L_ik U_kj per
+                          factorisation (Algorithm 2's inner loop)          */
 } opm_info;
 
 opm_status opm_get_info(opm_handle h, opm_info *info);
@@ -416,7 +452,12 @@ opm_status opm_solve_wait(opm_handle h, int32_t *iters, double *relres);
  *   OPM_NOT_CONVERGED if a system did not converge, else OPM_OK.
  *   opm_batch_launch / _ready / _wait: the asynchronous form of an optional
  *   refactorisation (vals NULL = none) followed by a solve; device pointers
- *   only, valid until opm_batch_wait returns.
+ *   only, valid until opm_batch_wait returns.  A member with b[i] = NULL and
+ *   x[i] = NULL sits the launch out: its values, factors, state and x are
+ *   not touched (its vals[i] is ignored) and opm_batch_wait reports OPM_OK,
+ *   0 iterations and relres 0 for it; its share of every launch ends at
+ *   once.  A serving loop keeps one batch over several resident handles and
+ *   launches it with the members whose requests are ready.
  */
 opm_status opm_batch_create(int32_t nsys, const opm_handle *hs, const opm_options *opt, opm_batch *out);
 opm_status opm_batch_factor(opm_batch b, const double *const *vals, opm_status *st);

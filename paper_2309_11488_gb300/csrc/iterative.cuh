@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(256) k_cp_init(Batch B, int stage, int out) {
   if (e >= B.nall) return;
   const int4 E = B.all_ent[e];
   const Sys &S = B.sys[E.x];
+  if (S.skip) return;
   const int i = E.y * 32 + (threadIdx.x & 31);
   const bool act = i < S.n;
   TF *Y = factor_buf<TF>(S, out);
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(256) k_cp_sweep(Batch B, int out) {
   const int e = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (e >= B.nall) return;
   const int4 E = B.all_ent[e];
+  if (B.sys[E.x].skip) return;
   cp_sweep_rows<TF>(B.sys[E.x], E.y, out);
 }
 

@@ -47,6 +47,8 @@ struct Sys {
   const int32_t *upd_ptr;
   const int64_t *upd_dst, *upd_src;
   const uint2 *sl_mask;  // per slice: (rows without U blocks, rows whose y is read later)
+  const uint32_t *fz_mask;  // per slice: rows the factorisation walks in one pass
+  const int64_t *a_aux;     // per A block: slot of U_ki for a one-pass row's L block (i,k), else -1
   // standard wells applied separately (nwells = 0: none)
   int32_t nwells, pad1;
   const int32_t *w_ptr;     // [nwells+1] perforations of each well
@@ -78,7 +80,7 @@ struct Sys {
   const double *vals_in; // new matrix values for the factorisation (NULL: refactor A)
   double rtol;
   int32_t maxit;
-  int32_t pad;
+  int32_t skip;          // the system sits this batch launch out: no kernel touches it
 };
 
 // A launchable set of systems (kernel parameter).
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(256) k_wells(Batch B, int which) {
   pdl_enter();
   const Sys &S = B.sys[blockIdx.x];
   const int nw = S.nwells;
-  if (nw == 0) return;
+  if (nw == 0 || S.skip) return;
   const double *x = operator_input(S, which);
   const int lane = threadIdx.x & 31;
   for (int w = threadIdx.x >> 5; w < nw; w += blockDim.x >> 5) {
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
   red_begin<1>(rs_);
   OPM_TILE(B, S, lt);
   if (FINAL && blockIdx.x == 0 && threadIdx.x == 0) B.bar[0] = 0;
+  if (S.skip) return;
   double acc[1] = {0.0};
   const double *__restrict__ b_in = S.b_in;
   const int32_t *__restrict__ perm = S.perm;
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(256, 6) k_setup(Batch B) {
 __global__ void k_start(Batch B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) B.bar[0] = 0;
-  if (s < B.nsys) setup_scalars(B.sys[s], B.sys[s].st, B.sys[s].st->bb);
+  if (s < B.nsys && !B.sys[s].skip) setup_scalars(B.sys[s], B.sys[s].st, B.sys[s].st->bb);
 }
 
 // v = A p^ and (r^, v); alpha = rho / (r^, v).
@@ -666,6 +669,7 @@ __global__ void __launch_bounds__(256, 8) k_finish(Batch B) {
   __shared__ RedShared<1> rs_;
   red_begin<1>(rs_);
   OPM_TILE_S(B, S, lt);
+  if (S.skip) return;
   const int status = S.st->status;
   const bool ok = (status == OPM_OK || status == OPM_NOT_CONVERGED) && S.st->error == 0;
   double acc[1] = {0.0};
@@ -735,7 +739,7 @@ __global__ void __launch_bounds__(256, 6) k_scatter(Batch B) {
 __global__ void k_begin_factor(Batch B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) B.bar[0] = 0;
-  if (s < B.nsys) {
+  if (s < B.nsys && !B.sys[s].skip) {
     DevState *st = B.sys[s].st;
     st->ferror = 0;
     st->error = 0;
@@ -746,7 +750,7 @@ __global__ void k_begin_factor(Batch B) {
 // After a factorisation: a recorded error becomes the factorisation error.
 __global__ void k_end_factor(Batch B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < B.nsys) {
+  if (s < B.nsys && !B.sys[s].skip) {
     DevState *st = B.sys[s].st;
     if (st->error != 0) st->ferror = st->error;
   }
@@ -774,7 +778,7 @@ __global__ void k_loop_cond(Batch B, cudaGraphConditionalHandle h) {
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int s = threadIdx.x; s < B.nsys; s += blockDim.x)
-    if (running(B.sys[s].st)) any = 1;
+    if (!B.sys[s].skip && running(B.sys[s].st)) any = 1;
   __syncthreads();
   if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }

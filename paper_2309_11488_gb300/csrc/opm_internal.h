@@ -13,6 +13,9 @@
 //   cnt_k = popc(ballot(len > k)) and q = popc(ballot & lanemask_lt) itself,
 //   so only the CSR row pointer is needed to walk a row.
 //
+//   In A's layout a row's diagonal block comes first, then the others in
+//   column order (L and U layouts: column order).
+//
 //   A "slot" packs the location of one block: (entry-0 value index << 6) |
 //   stride, with stride = cnt_k <= 32; entry e lives at off + e*stride.
 //
@@ -52,6 +55,14 @@ struct Analysis {
   std::vector<int64_t> a_csr_slot;            // per A block in permuted CSR order: slot in the factor values
   std::vector<int32_t> upd_ptr;               // per L block (CSR order of L) into the update lists
   std::vector<int64_t> upd_dst, upd_src;      // slots: A_ij -= L_ik * U_kj
+  int64_t nupd = 0;                           // update products (the lists' length)
+  // Rows whose every update is A_ii -= L_ik U_ki (no fill-free product lands
+  // on an L or U block of the row): the factorisation walks them in one pass
+  // with A_ii in registers.  Bit r of fz_mask[s] marks row 32 s + r;
+  // a_aux (A's sliced order) holds, for a kept L block (i,k) of such a row,
+  // the slot of U_ki, or -1 (no such block, or any other block or row).
+  std::vector<uint32_t> fz_mask;
+  std::vector<int64_t> a_aux;
   // phases: maximal runs of consecutive (schedule-order) rows none of which
   // reads another row of its run in either sweep; rows [phase_ptr[p],
   // phase_ptr[p+1]) form phase p.  For level and colour orders the phases are

@@ -59,9 +59,14 @@ struct opm_solver {
   bool async_pending = false;
 };
 
+struct opm_analysis_s {
+  opm::Analysis an;  // the whole analysis, device lists included
+};
+
 struct opm_batch_s {
   opm::Runner *run = nullptr;
   std::vector<opm_solver *> members;
+  std::vector<char> sat_out;  // members that sit the pending launch out
   bool async_pending = false;
 };
 
@@ -221,12 +226,13 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
   // A small phase is bound by the FP64 rate of the SMs it occupies (a few
   // warps per row, dozens of FMAs per block): two warps per CTA spread it
   // over up to all SMs instead of one in eight.
+  constexpr bool kFp32 = sizeof(TF) == 4;
   int n = 0;
   for (int c = 0; c < R.nphases; ++c) {
     const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
     if (cnt == 0) continue;
-    if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF>, (cnt + 1) / 2, 64, st, R.B, c);
-    else launch_pdl(k_factor_phase<TF>, blocks8(cnt), 256, st, R.B, c);
+    if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF, true, 1>, (cnt + 1) / 2, 64, st, R.B, c);
+    else launch_pdl(k_factor_phase<TF, kFp32, 4>, blocks8(cnt), 256, st, R.B, c);
     ++n;
   }
   return n;
@@ -832,8 +838,7 @@ opm_status factor_impl(opm_solver *h, const double *vals) {
   return OPM_OK;
 }
 
-opm_status alloc_system(opm_solver *h) {
-  Analysis &an = h->an;
+opm_status alloc_system(opm_solver *h, const Analysis &an) {
   Sys &S = h->sys;
   const int32_t nb = h->n;
   std::vector<void *> &A = h->allocs;
@@ -863,9 +868,14 @@ opm_status alloc_system(opm_solver *h) {
   UP(p_upd, an.upd_ptr);
   UP(p_ud, an.upd_dst);
   UP(p_us, an.upd_src);
-  uint32_t *p_mask;
+  uint32_t *p_mask, *p_fz;
+  int64_t *p_aux;
   UP(p_mask, an.sl_mask);
+  UP(p_fz, an.fz_mask);
+  UP(p_aux, an.a_aux);
 #undef UP
+  S.fz_mask = p_fz;
+  S.a_aux = p_aux;
   S.sl_mask = reinterpret_cast<const uint2 *>(p_mask);
   S.perm = p_perm;
   S.a_rp = p_arp;
@@ -906,7 +916,12 @@ opm_status alloc_system(opm_solver *h) {
   init.status = OPM_OK;
   CK(cudaMemcpyAsync(S.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
-  // free the host copies the device now holds (keep perm, phases and the factor slots)
+  return OPM_OK;
+}
+
+// Frees the lists only the device needs from a handle's own analysis once
+// they are uploaded (perm, phases, masks and the factor slots stay).
+void drop_device_lists(Analysis &an) {
   std::vector<int32_t>().swap(an.a_col);
   std::vector<int32_t>().swap(an.a_src);
   std::vector<int64_t>().swap(an.a_dst);
@@ -915,7 +930,32 @@ opm_status alloc_system(opm_solver *h) {
   std::vector<int32_t>().swap(an.upd_ptr);
   std::vector<int64_t>().swap(an.upd_dst);
   std::vector<int64_t>().swap(an.upd_src);
-  return OPM_OK;
+  std::vector<int64_t>().swap(an.a_aux);
+  std::vector<uint32_t>().swap(an.fz_mask);
+}
+
+// The host part of an analysis a handle keeps (everything but the lists
+// drop_device_lists frees), copied from a kept analysis.
+void copy_host_part(Analysis &dst, const Analysis &src) {
+  dst.n = src.n;
+  dst.nnzb = src.nnzb;
+  dst.nnz_l = src.nnz_l;
+  dst.nnz_u = src.nnz_u;
+  dst.nnzb_kept = src.nnzb_kept;
+  dst.schedule = src.schedule;
+  dst.nsets = src.nsets;
+  dst.perm = src.perm;
+  dst.iperm = src.iperm;
+  dst.a_rowptr = src.a_rowptr;
+  dst.l_rowptr = src.l_rowptr;
+  dst.u_rowptr = src.u_rowptr;
+  dst.a_csr_slot = src.a_csr_slot;
+  dst.nupd = src.nupd;
+  dst.phase_ptr = src.phase_ptr;
+  dst.sl_mask = src.sl_mask;
+  dst.d_off = src.d_off;
+  dst.lu_vals = src.lu_vals;
+  dst.max_row_len = src.max_row_len;
 }
 
 opm_status check_options(const opm_options &o) {
@@ -1272,58 +1312,17 @@ opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, cons
 
 namespace {
 
-opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
-                       const int32_t *part, const opm_options *opt, opm_handle *out) {
-  if (!out) return OPM_ERR_ARG;
-  *out = nullptr;
-  t_create_err_row = -1;
-  if (nb < 0 || nb > OPM_MAX_ROWS || !rowptr || (nb > 0 && (!colidx || !vals))) return OPM_ERR_ARG;
-  opm_options o;
-  opm_options_default(&o);
-  if (opt) o = *opt;
-  if (check_options(o) != OPM_OK) return OPM_ERR_ARG;
-
-  opm_solver *h = new (std::nothrow) opm_solver();
-  if (!h) return OPM_ERR_OOM;
-  h->opt = o;
-  h->stream = (cudaStream_t)o.stream;
-  h->fp32 = o.precision == OPM_PREC_FP32_FACTORS;
+// The device part of a new handle h whose analysis is done: h->an (kept =
+// NULL) or a kept analysis, whose host part is copied into h->an.  Events,
+// device memory, the uploaded analysis, the handle's batch of one and the
+// first factorisation of vals.  Takes ownership of h.
+opm_status finish_create(opm_solver *h, const Analysis *kept, const double *vals, const opm_options &o,
+                         opm_handle *out) {
   auto fail = [&](opm_status s) {
     opm_destroy(h);
     return s;
   };
-
-  // ---- pattern on the host for the analysis
-  std::vector<int32_t> hrp, hci;
-  const int32_t *rp = rowptr, *ci = colidx;
-  if (is_device_ptr(rowptr)) {
-    hrp.resize((size_t)nb + 1);
-    if (cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return fail(OPM_ERR_CUDA);
-    rp = hrp.data();
-  }
-  const int64_t nnzb = rp[nb];
-  if (nnzb < 0) return fail(OPM_ERR_PATTERN);
-  if (nb > 0 && is_device_ptr(colidx)) {
-    hci.resize((size_t)nnzb);
-    if (cudaMemcpy(hci.data(), colidx, sizeof(int32_t) * hci.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return fail(OPM_ERR_CUDA);
-    ci = hci.data();
-  }
-  std::vector<int32_t> hpart;
-  const int32_t *pt = part;
-  if (part && nb > 0 && is_device_ptr(part)) {
-    hpart.resize((size_t)nb);
-    if (cudaMemcpy(hpart.data(), part, sizeof(int32_t) * hpart.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return fail(OPM_ERR_CUDA);
-    pt = hpart.data();
-  }
-  int32_t err_row = -1;
-  opm_status s = analyse(nb, rp, ci, pt, o.schedule, h->an, &err_row);
-  t_create_err_row = err_row;
-  if (s != OPM_OK) return fail(s);
-
-  // ---- CUDA resources (after the host checks, which need no device)
+  if (kept) copy_host_part(h->an, *kept);
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
     return fail(OPM_ERR_CUDA);
@@ -1333,8 +1332,9 @@ opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
       cudaGetLastError();
       return fail(OPM_ERR_CUDA);
     }
+  const int32_t nb = h->an.n;
   h->n = nb;
-  h->nnzb = nnzb;
+  h->nnzb = h->an.nnzb;
   h->nslices = (nb + kWarp - 1) / kWarp;
   h->ntiles = std::max(1, (nb + kTileRows - 1) / kTileRows);
   if (nb == 0) {
@@ -1342,10 +1342,11 @@ opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
     *out = h;
     return OPM_OK;
   }
-  if ((s = alloc_system(h)) != OPM_OK) return fail(s);
+  opm_status s = alloc_system(h, kept ? *kept : h->an);
+  if (!kept) drop_device_lists(h->an);
+  if (s != OPM_OK) return fail(s);
   std::vector<opm_solver *> one{h};
-  if ((s = runner_create(one, h->stream, o, &h->run)) != OPM_OK)
-    return fail(s);
+  if ((s = runner_create(one, h->stream, o, &h->run)) != OPM_OK) return fail(s);
   s = factor_impl(h, vals);
   if (s == OPM_ERR_ZERO_PIVOT) {
     // the handle stays usable: the row can be read and new values factored
@@ -1355,6 +1356,90 @@ opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx,
   if (s != OPM_OK) return fail(s);
   *out = h;
   return OPM_OK;
+}
+
+// A host copy of a pattern given in host or device memory; rp, ci, pt point
+// at the caller's arrays or at the copies.
+opm_status host_pattern(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                        std::vector<int32_t> &hrp, std::vector<int32_t> &hci, std::vector<int32_t> &hpart,
+                        const int32_t **rp, const int32_t **ci, const int32_t **pt) {
+  *rp = rowptr;
+  *ci = colidx;
+  *pt = part;
+  if (is_device_ptr(rowptr)) {
+    hrp.resize((size_t)nb + 1);
+    if (cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OPM_ERR_CUDA;
+    *rp = hrp.data();
+  }
+  const int64_t nnzb = (*rp)[nb];
+  if (nnzb < 0) return OPM_ERR_PATTERN;
+  if (nb > 0 && is_device_ptr(colidx)) {
+    hci.resize((size_t)nnzb);
+    if (cudaMemcpy(hci.data(), colidx, sizeof(int32_t) * hci.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OPM_ERR_CUDA;
+    *ci = hci.data();
+  }
+  if (part && nb > 0 && is_device_ptr(part)) {
+    hpart.resize((size_t)nb);
+    if (cudaMemcpy(hpart.data(), part, sizeof(int32_t) * hpart.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OPM_ERR_CUDA;
+    *pt = hpart.data();
+  }
+  return OPM_OK;
+}
+
+// Counts and permutation of an analysis for the caller.
+void analysis_info(const Analysis &an, int32_t *perm, opm_analysis_info *info) {
+  if (perm && an.n > 0) memcpy(perm, an.perm.data(), sizeof(int32_t) * (size_t)an.n);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->schedule = an.schedule;
+    info->nsets = an.nsets;
+    info->nphases = an.n > 0 ? (int32_t)an.phase_ptr.size() - 1 : 0;
+    info->nnzb_kept = an.nnzb_kept;
+    info->nnzb_lower = an.nnz_l;
+    info->nnzb_upper = an.nnz_u;
+    info->nupdates = an.nupd;
+  }
+}
+
+opm_status new_handle(const opm_options *opt, opm_options *o, opm_solver **h) {
+  opm_options_default(o);
+  if (opt) *o = *opt;
+  if (check_options(*o) != OPM_OK) return OPM_ERR_ARG;
+  *h = new (std::nothrow) opm_solver();
+  if (!*h) return OPM_ERR_OOM;
+  (*h)->opt = *o;
+  (*h)->stream = (cudaStream_t)o->stream;
+  (*h)->fp32 = o->precision == OPM_PREC_FP32_FACTORS;
+  return OPM_OK;
+}
+
+opm_status create_impl(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+                       const int32_t *part, const opm_options *opt, opm_handle *out) {
+  if (!out) return OPM_ERR_ARG;
+  *out = nullptr;
+  t_create_err_row = -1;
+  if (nb < 0 || nb > OPM_MAX_ROWS || !rowptr || (nb > 0 && (!colidx || !vals))) return OPM_ERR_ARG;
+  opm_options o;
+  opm_solver *h = nullptr;
+  opm_status s = new_handle(opt, &o, &h);
+  if (s != OPM_OK) return s;
+  std::vector<int32_t> hrp, hci, hpart;
+  const int32_t *rp, *ci, *pt;
+  if ((s = host_pattern(nb, rowptr, colidx, part, hrp, hci, hpart, &rp, &ci, &pt)) != OPM_OK) {
+    opm_destroy(h);
+    return s;
+  }
+  int32_t err_row = -1;
+  s = analyse(nb, rp, ci, pt, o.schedule, h->an, &err_row);
+  t_create_err_row = err_row;
+  if (s != OPM_OK) {
+    opm_destroy(h);
+    return s;
+  }
+  return finish_create(h, nullptr, vals, o, out);
 }
 
 }  // namespace
@@ -1382,18 +1467,57 @@ opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *col
   const opm_status s = analyse(nb, rowptr, colidx, part, schedule, an, &err_row);
   t_create_err_row = err_row;
   if (s != OPM_OK) return s;
-  if (perm && nb > 0) memcpy(perm, an.perm.data(), sizeof(int32_t) * (size_t)nb);
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->schedule = an.schedule;
-    info->nsets = an.nsets;
-    info->nphases = nb > 0 ? (int32_t)an.phase_ptr.size() - 1 : 0;
-    info->nnzb_kept = an.nnzb_kept;
-    info->nnzb_lower = an.nnz_l;
-    info->nnzb_upper = an.nnz_u;
-  }
+  analysis_info(an, perm, info);
   return OPM_OK;
 }
+
+opm_status opm_analysis_create(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
+                               int32_t schedule, opm_analysis *out) {
+  if (!out) return OPM_ERR_ARG;
+  *out = nullptr;
+  t_create_err_row = -1;
+  if (nb < 0 || nb > OPM_MAX_ROWS || !rowptr || (nb > 0 && !colidx) || schedule < OPM_SCHED_AUTO ||
+      schedule > OPM_SCHED_COLOUR_KEMPE)
+    return OPM_ERR_ARG;
+  std::vector<int32_t> hrp, hci, hpart;
+  const int32_t *rp, *ci, *pt;
+  opm_status s = host_pattern(nb, rowptr, colidx, part, hrp, hci, hpart, &rp, &ci, &pt);
+  if (s != OPM_OK) return s;
+  opm_analysis a = new (std::nothrow) opm_analysis_s();
+  if (!a) return OPM_ERR_OOM;
+  int32_t err_row = -1;
+  s = analyse(nb, rp, ci, pt, schedule, a->an, &err_row);
+  t_create_err_row = err_row;
+  if (s != OPM_OK) {
+    delete a;
+    return s;
+  }
+  *out = a;
+  return OPM_OK;
+}
+
+opm_status opm_bsr_create_from_analysis(opm_analysis a, const double *vals, const opm_options *opt,
+                                        opm_handle *out) {
+  if (!out) return OPM_ERR_ARG;
+  *out = nullptr;
+  if (!a || (a->an.n > 0 && !vals)) return OPM_ERR_ARG;
+  opm_options o;
+  opm_solver *h = nullptr;
+  opm_status s = new_handle(opt, &o, &h);
+  if (s != OPM_OK) return s;
+  return finish_create(h, &a->an, vals, o, out);
+}
+
+opm_status opm_analysis_get_info(opm_analysis a, int32_t *nb, int64_t *nnzb, int32_t *perm,
+                                 opm_analysis_info *info) {
+  if (!a) return OPM_ERR_ARG;
+  if (nb) *nb = a->an.n;
+  if (nnzb) *nnzb = a->an.nnzb;
+  analysis_info(a->an, perm, info);
+  return OPM_OK;
+}
+
+void opm_analysis_destroy(opm_analysis a) { delete a; }
 
 opm_status opm_ilu0_factor(opm_handle h, const double *vals) {
   if (!h || h->async_pending) return OPM_ERR_ARG;
@@ -1545,6 +1669,7 @@ opm_status opm_get_info(opm_handle h, opm_info *info) {
   info->device_bytes = h->dev_bytes + (h->run ? h->run->dev_bytes : 0);
   info->nphases = h->n > 0 ? (int32_t)h->an.phase_ptr.size() - 1 : 0;
   info->reserved = 0;
+  info->nupdates = h->an.nupd;
   return OPM_OK;
 }
 
@@ -1714,8 +1839,13 @@ opm_status opm_batch_launch(opm_batch b, const double *const *vals, const double
                             const double *rtol, int32_t maxit) {
   if (!b || !bv || !xv || b->async_pending) return OPM_ERR_ARG;
   Runner &R = *b->run;
+  b->sat_out.assign(R.nsys, 0);
   for (int i = 0; i < R.nsys; ++i) {
     opm_solver *h = b->members[i];
+    if (!bv[i] && !xv[i]) {  // sits this launch out
+      b->sat_out[i] = 1;
+      continue;
+    }
     const double *v = vals ? vals[i] : nullptr;
     const double rt = rtol ? rtol[i] : 1e-2;
     if (!bv[i] || !xv[i] || !is_device_ptr(bv[i]) || !is_device_ptr(xv[i]) || (v && !is_device_ptr(v)) ||
@@ -1725,14 +1855,19 @@ opm_status opm_batch_launch(opm_batch b, const double *const *vals, const double
   }
   for (int i = 0; i < R.nsys; ++i) {
     opm_solver *h = b->members[i];
-    h->sys.b_in = bv[i];
-    h->sys.x_out = xv[i];
+    const bool out = b->sat_out[i] != 0;
+    h->sys.skip = out ? 1 : 0;
+    h->sys.b_in = out ? nullptr : bv[i];
+    h->sys.x_out = out ? nullptr : xv[i];
     h->sys.rtol = rtol ? rtol[i] : 1e-2;
     h->sys.maxit = maxit;
-    h->sys.vals_in = vals ? vals[i] : nullptr;
+    h->sys.vals_in = (vals && !out) ? vals[i] : nullptr;
   }
   opm_status s = runner_enqueue(R, vals != nullptr, true);
-  for (auto *h : b->members) h->sys.vals_in = nullptr;
+  for (auto *h : b->members) {
+    h->sys.vals_in = nullptr;
+    h->sys.skip = 0;
+  }
   if (s != OPM_OK) return s;
   b->async_pending = true;
   return OPM_OK;
@@ -1755,6 +1890,12 @@ opm_status opm_batch_wait(opm_batch b, int32_t *iters, double *relres, opm_statu
   opm_status worst = OPM_OK;
   for (int i = 0; i < R.nsys; ++i) {
     opm_solver *h = b->members[i];
+    if (!b->sat_out.empty() && b->sat_out[i]) {
+      if (iters) iters[i] = 0;
+      if (relres) relres[i] = 0.0;
+      if (st) st[i] = OPM_OK;
+      continue;
+    }
     const Result &r = R.h_res[i];
     h->factors_ok = r.status != OPM_ERR_ZERO_PIVOT;
     if (iters) iters[i] = r.iters;

@@ -427,9 +427,15 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
   an.a_csr_slot.assign((size_t)nnzb, 0);
   an.l_col.assign((size_t)an.nnz_l, 0);
   an.u_col.assign((size_t)an.nnz_u, 0);
+  std::vector<int64_t> a_at((size_t)nnzb);  // sliced A position of permuted CSR block c
   for (int32_t ni = 0; ni < n; ++ni) {
     int64_t lc = an.l_rowptr[ni], uc = an.u_rowptr[ni];
+    int64_t cd = arp[ni];
+    while (pcol[cd] != ni) ++cd;  // every row holds its diagonal (checked above)
     for (int64_t c = arp[ni]; c < arp[ni + 1]; ++c) {
+      // A's order inside the row: the diagonal first, then column order
+      const int64_t rank = c == cd ? 0 : (c - arp[ni]) + (c < cd ? 1 : 0);
+      a_at[c] = a_pos[arp[ni] + rank];
       int32_t j = pcol[c];
       int64_t dst;
       if (!pk[c]) {
@@ -443,9 +449,9 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
       } else {
         dst = d_slot(ni);
       }
-      an.a_col[a_pos[c]] = j;
-      an.a_src[a_pos[c]] = psrc[c];
-      an.a_dst[a_pos[c]] = dst;
+      an.a_col[a_at[c]] = j;
+      an.a_src[a_at[c]] = psrc[c];
+      an.a_dst[a_at[c]] = dst;
       an.a_csr_slot[c] = dst;
     }
   }
@@ -472,11 +478,16 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
   }
 
   // ---- ILU0 update lists: for L block (i,k), every j > k present in row i
-  // and in row k gives A_ij -= L_ik * U_kj (Algorithm 2's inner loop).
+  // and in row k gives A_ij -= L_ik * U_kj (Algorithm 2's inner loop).  A row
+  // all of whose products land on its diagonal block is walked in one pass
+  // by the factorisation (fz_mask, a_aux).
   an.upd_ptr.assign((size_t)an.nnz_l + 1, 0);
   an.upd_dst.clear();
   an.upd_src.clear();
+  an.a_aux.assign((size_t)nnzb, -1);
+  an.fz_mask.assign((size_t)((n + kWarp - 1) / kWarp), 0u);
   for (int32_t ni = 0; ni < n; ++ni) {
+    bool fused = true;
     int64_t lc = an.l_rowptr[ni];
     for (int64_t c = arp[ni]; c < arp[ni + 1] && pcol[c] < ni; ++c) {
       if (!pk[c]) continue;
@@ -497,6 +508,8 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
         } else {
           an.upd_dst.push_back(an.a_csr_slot[ic]);
           an.upd_src.push_back(u_slot[ku]);
+          if (pcol[ic] == ni) an.a_aux[a_at[c]] = u_slot[ku];
+          else fused = false;
           do ++ic; while (ic < arp[ni + 1] && !pk[ic]);
           do ++kc; while (kc < arp[k + 1] && !pk[kc]);
           ++ku;
@@ -505,8 +518,14 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
       an.upd_ptr[lc + 1] = (int32_t)an.upd_dst.size();
       ++lc;
     }
+    if (fused) {
+      an.fz_mask[ni / kWarp] |= 1u << (ni % kWarp);
+    } else {
+      for (int64_t c = arp[ni]; c < arp[ni + 1]; ++c) an.a_aux[a_at[c]] = -1;
+    }
   }
   if (an.upd_dst.size() >= ((size_t)1 << 31)) return OPM_ERR_ARG;
+  an.nupd = (int64_t)an.upd_dst.size();
   return OPM_OK;
 }
 

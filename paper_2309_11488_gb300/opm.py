@@ -42,7 +42,9 @@ EXPORTS = ["opm_options_default", "opm_bsr_create", "opm_ilu0_factor", "opm_bicg
            "opm_reset_timing", "opm_bsr_residual_noalloc", "opm_solve_launch", "opm_solve_ready",
            "opm_solve_wait", "opm_batch_create", "opm_batch_factor", "opm_batch_solve", "opm_batch_launch",
            "opm_batch_ready", "opm_batch_wait", "opm_batch_destroy", "opm_autotune", "opm_autotune_batch",
-           "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve", "opm_bsr_analyse"]
+           "opm_bsr_create_jacobi", "opm_set_wells", "opm_gmres_solve", "opm_bsr_analyse",
+           "opm_analysis_create", "opm_bsr_create_from_analysis", "opm_analysis_get_info",
+           "opm_analysis_destroy"]
 
 
 class opm_options(ctypes.Structure):
@@ -70,13 +72,13 @@ class opm_info(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int32), ("schedule", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("nsets", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
                 ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("nphases", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nphases", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nupdates", ctypes.c_int64)]
 
 
 class opm_analysis_info(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("nsets", ctypes.c_int32), ("nphases", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("nnzb_kept", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
-                ("nnzb_upper", ctypes.c_int64)]
+                ("nnzb_upper", ctypes.c_int64), ("nupdates", ctypes.c_int64)]
 
 
 KERNELS = ["factor", "apply", "spmv", "update", "setup", "finish"]
@@ -110,6 +112,15 @@ def lib() -> ctypes.CDLL:
         L.opm_bsr_create_jacobi.restype = i32
         L.opm_bsr_analyse.argtypes = [i32, vp, vp, vp, i32, vp, ctypes.POINTER(opm_analysis_info)]
         L.opm_bsr_analyse.restype = i32
+        L.opm_analysis_create.argtypes = [i32, vp, vp, vp, i32, ctypes.POINTER(vp)]
+        L.opm_analysis_create.restype = i32
+        L.opm_bsr_create_from_analysis.argtypes = [vp, vp, ctypes.POINTER(opm_options), ctypes.POINTER(vp)]
+        L.opm_bsr_create_from_analysis.restype = i32
+        L.opm_analysis_get_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), vp,
+                                            ctypes.POINTER(opm_analysis_info)]
+        L.opm_analysis_get_info.restype = i32
+        L.opm_analysis_destroy.argtypes = [vp]
+        L.opm_analysis_destroy.restype = None
         L.opm_set_wells.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.opm_set_wells.restype = i32
         L.opm_gmres_solve.argtypes = [vp, vp, vp, f64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(f64)]
@@ -253,6 +264,60 @@ def opm_bsr_analyse(nb, rowptr, colidx, schedule="auto", part=None):
                                pt.ctypes.data if pt is not None and pt.size else None, int(schedule),
                                perm.ctypes.data if perm.size else None, ctypes.byref(info))
     return st, perm, info
+
+
+class Analysis:
+    """A kept symbolic analysis (opm_analysis_create): handles of its pattern
+    are made from it by Solver.from_analysis without analysing again."""
+
+    def __init__(self, nb, rowptr, colidx, schedule="auto", part=None):
+        if isinstance(schedule, str):
+            schedule = SCHEDULES[schedule]
+        out = ctypes.c_void_p()
+        self.status = lib().opm_analysis_create(int(nb), _ptr(rowptr, np.int32), _ptr(colidx, np.int32),
+                                                _ptr(part, np.int32), int(schedule), ctypes.byref(out))
+        self.ptr = out.value or 0
+        if self.status != OPM_OK:
+            raise OpmError(self.status, "opm_analysis_create")
+        nbv, nnzb = ctypes.c_int32(), ctypes.c_int64()
+        self.info = opm_analysis_info()
+        lib().opm_analysis_get_info(self.ptr, ctypes.byref(nbv), ctypes.byref(nnzb), None, ctypes.byref(self.info))
+        self.nb, self.nnzb = nbv.value, nnzb.value
+
+    def permutation(self) -> np.ndarray:
+        perm = np.empty(self.nb, dtype=np.int32)
+        lib().opm_analysis_get_info(self.ptr, None, None, perm.ctypes.data if self.nb else None, None)
+        return perm
+
+    def close(self):
+        if self.ptr:
+            lib().opm_analysis_destroy(self.ptr)
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def opm_bsr_create_from_analysis(an: Analysis, vals, options: opm_options | None = None, check=True):
+    """Returns (status, Handle or None): a handle of the analysed pattern."""
+    out = ctypes.c_void_p()
+    opt = ctypes.byref(options) if options is not None else None
+    st = lib().opm_bsr_create_from_analysis(an.ptr, _ptr(vals, np.float64), opt, ctypes.byref(out))
+    h = Handle(out.value or 0, an.nb, an.nnzb) if out.value else None
+    if check and st != OPM_OK:
+        if h:
+            opm_destroy(h)
+        raise OpmError(st, "opm_bsr_create_from_analysis")
+    return st, h
 
 
 def opm_ilu0_factor(h: Handle, vals=None) -> int:
@@ -451,6 +516,17 @@ class Solver:
                                            tri_sweeps=tri_sweeps)
         self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options, part=part)
         self.nb = nb
+
+    @classmethod
+    def from_analysis(cls, an: Analysis, vals, precision="fp64", stream=None, **kw):
+        """A handle of an analysed pattern (opm_bsr_create_from_analysis)."""
+        self = cls.__new__(cls)
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.options = opm_options_default(precision=precision, stream=stream, **kw)
+        self.status, self.h = opm_bsr_create_from_analysis(an, vals, self.options)
+        self.nb = an.nb
+        return self
 
     def factor(self, vals=None) -> int:
         return opm_ilu0_factor(self.h, vals)

@@ -3,18 +3,29 @@
 Each request carries new matrix values for one of the resident sparsity
 patterns and a right-hand side; it needs an ILU0 refactorisation and a
 BiCGStab solve (the per-Newton-step pair of the paper, Sections 4.2 and 4.4:
-the pattern, hence the symbolic analysis, never changes, only the values).
+the pattern, hence its symbolic analysis, never changes, only the values).
 
-The engine keeps, per pattern, one or more *instances*: library handles whose
-symbolic analysis, device matrix, factors and Krylov vectors stay resident in
-HBM.  Requests that arrive while others are on the GPU are admitted as soon as
-an instance of their pattern is idle, or a new instance fits in the HBM
-budget; every instance runs on its own CUDA stream, so the work of all
-admitted requests overlaps on the device.  A request's latency is measured
-from its arrival to the host seeing its completion (queueing included).
+Residency.  Every pattern's symbolic analysis is computed once
+(``opm.Analysis``) and kept in host memory for the whole run.  Device memory
+is organised in *lanes*: a lane holds one instance (a library handle: device
+matrix, factors, Krylov vectors) of every pattern of one size class, one
+batch over those instances and its own CUDA stream.  Lanes are admitted by
+free HBM under a budget.  When a size class needs a lane and the budget is
+full, the least recently used idle lane of another class is evicted (its
+device memory freed) and the new lane is made from the kept analyses: an
+upload and a first factorisation, never a new analysis.
 
-The scheduling here is host-side bookkeeping only; all numerical work runs in
-the library's kernels through ``opm_solve_launch`` / ``opm_solve_wait``.
+Batching.  Requests wait in a FIFO queue per pattern.  Whenever a lane is
+idle, the oldest waiting request of each of its patterns is taken and all of
+them go to the GPU in one ``opm_batch_launch`` (refactorisation + solve);
+the lane's other instances sit the launch out.  Lanes run at once on their
+own streams, so a request that arrives while others are on the GPU is
+admitted into the next idle lane of its class and its work overlaps theirs
+on the device.  A request's latency runs from its arrival to the host seeing
+its completion (queueing included).
+
+The scheduling is host-side bookkeeping only; all numerical work runs in the
+library's kernels.
 """
 from __future__ import annotations
 
@@ -40,21 +51,23 @@ class Request:
     status: int = 0
     iters: int = 0
     relres: float = float("nan")
-    instance: int = -1
+    lane: int = -1
     x: object = None          # copy of the solution (with keep_results)
 
 
 @dataclass
-class Instance:
-    iid: int
-    pattern: int
-    solver: opm.Solver
+class Lane:
+    lid: int
+    cls: int                  # size class
+    patterns: list            # member patterns, in member order
+    solvers: list             # one opm.Solver per member
+    batch: object             # opm.Batch over the members
     stream: object
-    x: object                 # device output buffer
+    xs: list                  # device output buffer per member
     device_bytes: int
-    busy: Request | None = None
-    served: int = 0
+    running: list | None = None  # requests of the launch in flight (None: a member sits out)
     last_used: float = 0.0
+    launches: int = 0
 
 
 @dataclass
@@ -63,12 +76,14 @@ class ServeStats:
     failed: int = 0
     latencies_ms: list = field(default_factory=list)
     wall_s: float = 0.0
-    instances: int = 0
-    instances_per_pattern_max: int = 0
+    lanes: int = 0
     hbm_bytes_peak: int = 0
-    max_in_flight: int = 0
-    deferred_admissions: int = 0
+    max_in_flight: int = 0     # requests on the device at once
+    deferred: int = 0          # requests that found no idle lane on arrival
     evictions: int = 0
+    lanes_created: int = 0     # lanes made during the run (from the kept analyses)
+    launches: int = 0
+    batched_requests: int = 0  # requests over all launches
 
     def summary(self):
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.array([np.nan])
@@ -76,180 +91,237 @@ class ServeStats:
                 "solves_per_s": self.completed / self.wall_s if self.wall_s > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(np.mean(lat)), "max_ms": float(np.max(lat)),
-                "instances": self.instances, "max_in_flight": self.max_in_flight,
-                "hbm_bytes_peak": self.hbm_bytes_peak, "deferred_admissions": self.deferred_admissions,
-                "evictions": self.evictions}
+                "lanes": self.lanes, "max_in_flight": self.max_in_flight,
+                "hbm_bytes_peak": self.hbm_bytes_peak, "deferred": self.deferred,
+                "evictions": self.evictions, "lanes_created_in_run": self.lanes_created,
+                "launches": self.launches,
+                "mean_batch": self.batched_requests / self.launches if self.launches else 0.0}
 
 
 class ServingEngine:
-    """Admission by free HBM, resident factors per pattern, overlap by streams."""
+    """Kept analyses, lanes admitted by free HBM, batched launches per lane."""
 
-    def __init__(self, patterns, precision="fp32", schedule="auto", hbm_budget_bytes=8 << 30,
-                 max_instances_per_pattern=4, maxit=200):
+    def __init__(self, patterns, precision="fp32", schedule="auto", hbm_budget_bytes=8 << 30, class_size=8,
+                 lanes_per_class=2, maxit=200):
         import torch
         self.torch = torch
         self.patterns = patterns
         self.precision = precision
         self.schedule = schedule
         self.budget = int(hbm_budget_bytes)
-        self.max_per_pattern = max_instances_per_pattern
+        self.lanes_per_class = lanes_per_class
         self.maxit = maxit
-        self.instances: dict[int, Instance] = {}
-        self.by_pattern = collections.defaultdict(list)
+        # size classes: patterns by cell count, class_size per class
+        order = sorted(range(len(patterns)), key=lambda p: (patterns[p].nb, p))
+        self.classes = [order[i:i + class_size] for i in range(0, len(order), class_size)]
+        self.class_of = {p: c for c, members in enumerate(self.classes) for p in members}
+        self.analyses = {}
+        self.lanes: dict[int, Lane] = {}
+        self.by_class = collections.defaultdict(list)
         self.hbm_bytes = 0
-        self._dev = {}
-        self._next_iid = 0
+        self._next_lid = 0
         self._bytes_seen = {}
         self.evictions = 0
+        self.lanes_created = 0
 
-    def _device_pattern(self, p):
-        if p not in self._dev:
-            s = self.patterns[p]
-            t = self.torch
-            self._dev[p] = (t.from_numpy(np.ascontiguousarray(s.rowptr)).cuda(),
-                            t.from_numpy(np.ascontiguousarray(s.colidx)).cuda(),
-                            t.from_numpy(np.ascontiguousarray(s.vals)).cuda())
-        return self._dev[p]
+    # ---------------------------------------------------------------- memory
 
     def estimate_bytes(self, p):
-        """Device bytes of one instance of pattern p (measured once created)."""
+        """Device bytes of one instance of pattern p and its output buffer
+        (measured once an instance was created)."""
         if p in self._bytes_seen:
             return self._bytes_seen[p]
         s = self.patterns[p]
         per_val = 4 if self.precision == "fp32" else 8
         # conservative: values, factors, index and slot arrays, 14 vectors, work lists
-        return int(s.nnzb * (72 + 9 * per_val + 48) + s.nb * (24 * 14 + 96) + (1 << 20))
+        return int(s.nnzb * (72 + 9 * per_val + 48) + s.nb * (24 * 15 + 96) + (1 << 20))
+
+    def lane_bytes(self, c):
+        return sum(self.estimate_bytes(p) for p in self.classes[c])
 
     def fits_alone(self, p):
-        return self.estimate_bytes(p) <= self.budget
+        return self.lane_bytes(self.class_of[p]) <= self.budget
 
-    def _evict_one(self, keep_pattern):
-        """Destroy the least recently used idle instance (not the only
-        instance of keep_pattern); True if one was freed."""
-        idle = [i for i in self.instances.values() if i.busy is None]
-        idle.sort(key=lambda i: i.last_used)
-        for inst in idle:
-            if inst.pattern == keep_pattern and len(self.by_pattern[keep_pattern]) <= 1:
-                continue
-            inst.solver.close()
-            self.by_pattern[inst.pattern].remove(inst.iid)
-            del self.instances[inst.iid]
-            self.hbm_bytes -= inst.device_bytes
-            self.evictions += 1
-            return True
-        return False
+    def analyse(self):
+        """The symbolic analysis of every pattern, once, kept for the run."""
+        for p, s in enumerate(self.patterns):
+            if p not in self.analyses:
+                self.analyses[p] = opm.Analysis(s.nb, s.rowptr, s.colidx, self.schedule)
 
-    def add_instance(self, p):
-        """Create a resident instance of pattern p if it fits in the budget,
-        evicting idle instances of other patterns when needed."""
-        if len(self.by_pattern[p]) >= self.max_per_pattern or not self.fits_alone(p):
+    def _evict_one(self, keep_class, wanted=()):
+        """Free the least recently used idle lane of another class, lanes of
+        classes in `wanted` (classes with requests waiting) last; True if one
+        was freed."""
+        idle = [ln for ln in self.lanes.values() if ln.running is None and ln.cls != keep_class]
+        idle.sort(key=lambda ln: (ln.cls in wanted, ln.last_used))
+        if not idle:
+            return False
+        ln = idle[0]
+        self._close_lane(ln)
+        self.evictions += 1
+        return True
+
+    def _close_lane(self, ln):
+        ln.batch.close()
+        for sv in ln.solvers:
+            sv.close()
+        self.by_class[ln.cls].remove(ln.lid)
+        del self.lanes[ln.lid]
+        self.hbm_bytes -= ln.device_bytes
+
+    def add_lane(self, c, evict=True, wanted=()):
+        """A new lane of class c if it fits in the budget (evicting idle
+        lanes of other classes when allowed), else None.  Its instances come
+        from the kept analyses, factorised once with the base values."""
+        if len(self.by_class[c]) >= self.lanes_per_class or self.lane_bytes(c) > self.budget:
             return None
-        while self.hbm_bytes + self.estimate_bytes(p) > self.budget:
-            if not self._evict_one(p):
+        while self.hbm_bytes + self.lane_bytes(c) > self.budget:
+            if not evict or not self._evict_one(c, wanted):
                 return None
-        rp, ci, va = self._device_pattern(p)
+        self.analyse()
         stream = self.torch.cuda.Stream()
-        sv = opm.Solver(self.patterns[p].nb, rp, ci, va, schedule=self.schedule, precision=self.precision,
-                        stream=stream)
-        info = sv.info()
-        inst = Instance(self._next_iid, p, sv, stream,
-                        self.torch.empty(3 * self.patterns[p].nb, dtype=self.torch.float64, device="cuda"),
-                        int(info.device_bytes))
-        self._next_iid += 1
-        self._bytes_seen[p] = inst.device_bytes
-        self.instances[inst.iid] = inst
-        self.by_pattern[p].append(inst.iid)
-        self.hbm_bytes += inst.device_bytes
-        return inst
+        solvers, xs, nbytes = [], [], 0
+        for p in self.classes[c]:
+            base = self.torch.from_numpy(np.ascontiguousarray(self.patterns[p].vals)).cuda()
+            sv = opm.Solver.from_analysis(self.analyses[p], base, precision=self.precision, stream=stream)
+            del base
+            solvers.append(sv)
+            xs.append(self.torch.empty(3 * self.patterns[p].nb, dtype=self.torch.float64, device="cuda"))
+            b = int(sv.info().device_bytes) + 24 * self.patterns[p].nb
+            self._bytes_seen[p] = b
+            nbytes += b
+        batch = opm.Batch([sv.h for sv in solvers], stream=stream)
+        ln = Lane(self._next_lid, c, list(self.classes[c]), solvers, batch, stream, xs, nbytes)
+        self._next_lid += 1
+        self.lanes[ln.lid] = ln
+        self.by_class[c].append(ln.lid)
+        self.hbm_bytes += nbytes
+        return ln
 
     def warm(self):
-        """One resident instance per pattern while the budget allows (the
-        symbolic analysis happens here, outside the measured run)."""
-        for p in range(len(self.patterns)):
-            if not self.by_pattern[p] and self.hbm_bytes + self.estimate_bytes(p) <= self.budget:
-                self.add_instance(p)
+        """The analyses, then lanes class by class (a first lane for every
+        class before any second one) while they fit the budget; no eviction."""
+        self.analyse()
+        for _ in range(self.lanes_per_class):
+            for c in range(len(self.classes)):
+                if self.hbm_bytes + self.lane_bytes(c) <= self.budget:
+                    self.add_lane(c, evict=False)
         self.torch.cuda.synchronize()
 
-    def _idle_instance(self, p):
-        for iid in self.by_pattern[p]:
-            if self.instances[iid].busy is None:
-                return self.instances[iid]
-        return self.add_instance(p)
+    # --------------------------------------------------------------- serving
+
+    def _launch(self, ln, queues, t0):
+        """Launch lane ln with the oldest waiting request of each of its
+        patterns; False if none waits."""
+        picked = [queues[p].popleft() if queues[p] else None for p in ln.patterns]
+        k = sum(r is not None for r in picked)
+        if k == 0:
+            return False
+        now = time.perf_counter() - t0
+        for r in picked:
+            if r is not None:
+                r.t_start, r.lane = now, ln.lid
+        vals = [r.vals if r is not None else None for r in picked]
+        bs = [r.b if r is not None else None for r in picked]
+        xs = [x if r is not None else None for x, r in zip(ln.xs, picked)]
+        rt = [r.rtol if r is not None else 1e-2 for r in picked]
+        st = ln.batch.launch(vals, bs, xs, rtol=rt, maxit=self.maxit)
+        if st != opm.OPM_OK:
+            raise opm.OpmError(st, "opm_batch_launch")
+        ln.running = picked
+        ln.launches += 1
+        return k
 
     def run(self, requests, poll_sleep_s=0.0, keep_results=False):
         """Serve requests (sorted by arrival time); returns ServeStats.  A
-        request whose pattern cannot fit in the budget even alone fails with
-        OPM_ERR_OOM."""
+        request whose pattern's class cannot fit in the budget even alone
+        fails with OPM_ERR_OOM."""
         stats = ServeStats()
-        queue = collections.deque()
-        in_flight = []
-        nxt = 0
-        total = len(requests)
+        queues = collections.defaultdict(collections.deque)
+        waiting = collections.Counter()  # requests queued per class
+        nxt, done, total = 0, 0, len(requests)
+        in_flight = 0
+        lanes0 = self.lanes_created
         t0 = time.perf_counter()
-        done = 0
         while done < total:
             now = time.perf_counter() - t0
             while nxt < total and requests[nxt].t_arrival <= now:
-                queue.append(requests[nxt])
+                r = requests[nxt]
                 nxt += 1
-            # admit every queued request whose pattern has an idle (or new) instance
-            waiting = collections.deque()
-            while queue:
-                r = queue.popleft()
                 if not self.fits_alone(r.pattern):
                     r.status = opm.OPM_ERR_OOM
                     r.t_done = time.perf_counter() - t0
                     stats.failed += 1
                     done += 1
                     continue
-                inst = self._idle_instance(r.pattern)
-                if inst is None:
-                    waiting.append(r)
-                    stats.deferred_admissions += 1
-                    continue
-                r.t_start = time.perf_counter() - t0
-                r.instance = inst.iid
-                inst.busy = r
-                inst.solver.launch(r.vals, r.b, inst.x, rtol=r.rtol, maxit=self.maxit)
-                in_flight.append(inst)
-            queue = waiting
-            stats.max_in_flight = max(stats.max_in_flight, len(in_flight))
+                c = self.class_of[r.pattern]
+                if not any(self.lanes[i].running is None for i in self.by_class[c]):
+                    stats.deferred += 1
+                queues[r.pattern].append(r)
+                waiting[c] += 1
+            # admit, classes in the order of their oldest waiting request:
+            # every idle lane of a class with waiting requests takes the
+            # oldest request of each of its patterns; a class without an idle
+            # lane gets a new one when the budget allows
+            def oldest(c):
+                return min((queues[p][0].t_arrival, queues[p][0].rid) for p in self.classes[c] if queues[p])
+            for c in sorted((c for c, n in waiting.items() if n > 0), key=oldest):
+                for lid in list(self.by_class[c]):
+                    ln = self.lanes[lid]
+                    if ln.running is None and waiting[c] > 0:
+                        k = self._launch(ln, queues, t0)
+                        waiting[c] -= k
+                        in_flight += k
+                        stats.launches += k > 0
+                        stats.batched_requests += k
+                while waiting[c] > 0 and len(self.by_class[c]) < self.lanes_per_class:
+                    ln = self.add_lane(c, wanted={k for k, n in waiting.items() if n > 0})
+                    if ln is None:
+                        break
+                    self.lanes_created += 1
+                    k = self._launch(ln, queues, t0)
+                    waiting[c] -= k
+                    in_flight += k
+                    stats.launches += k > 0
+                    stats.batched_requests += k
+            stats.max_in_flight = max(stats.max_in_flight, in_flight)
             stats.hbm_bytes_peak = max(stats.hbm_bytes_peak, self.hbm_bytes)
-            # retire finished work
-            still = []
-            for inst in in_flight:
-                if inst.solver.ready():
-                    st, it, rr = inst.solver.wait()
-                    r = inst.busy
-                    r.t_done = time.perf_counter() - t0
-                    r.status, r.iters, r.relres = st, it, rr
+            # retire finished launches
+            for ln in list(self.lanes.values()):
+                if ln.running is None or not ln.batch.ready():
+                    continue
+                _, st, it, rr = ln.batch.wait()
+                t_done = time.perf_counter() - t0
+                for m, r in enumerate(ln.running):
+                    if r is None:
+                        continue
+                    r.t_done = t_done
+                    r.status, r.iters, r.relres = st[m], it[m], rr[m]
                     if keep_results:
-                        r.x = inst.x.clone()
-                    inst.busy = None
-                    inst.served += 1
-                    inst.last_used = r.t_done
+                        r.x = ln.xs[m].clone()
                     done += 1
-                    if st in (opm.OPM_OK, opm.OPM_NOT_CONVERGED):
+                    in_flight -= 1
+                    if st[m] in (opm.OPM_OK, opm.OPM_NOT_CONVERGED):
                         stats.completed += 1
                         stats.latencies_ms.append(1e3 * (r.t_done - r.t_arrival))
                     else:
                         stats.failed += 1
-                else:
-                    still.append(inst)
-            in_flight = still
+                ln.running = None
+                ln.last_used = t_done
             if poll_sleep_s:
                 time.sleep(poll_sleep_s)
         stats.wall_s = time.perf_counter() - t0
-        stats.instances = len(self.instances)
+        stats.lanes = len(self.lanes)
         stats.evictions = self.evictions
-        stats.instances_per_pattern_max = max(len(v) for v in self.by_pattern.values()) if self.by_pattern else 0
+        stats.lanes_created = self.lanes_created - lanes0
         return stats
 
     def close(self):
-        for inst in self.instances.values():
-            inst.solver.close()
-        self.instances.clear()
-        self.by_pattern.clear()
+        for ln in list(self.lanes.values()):
+            self._close_lane(ln)
+        for an in self.analyses.values():
+            an.close()
+        self.analyses.clear()
         self.hbm_bytes = 0
 
 

@@ -395,3 +395,45 @@ def test_binding_defaults_are_the_papers_stopping_rule():
     for fn in (opm.Solver.solve, opm.Batch.solve, opm.opm_bicgstab_solve):
         sig = inspect.signature(fn).parameters
         assert sig["rtol"].default == facts["default_rtol"] and sig["maxit"].default == facts["default_maxit"], fn
+
+
+def _update_products(nb, rowptr, colidx):
+    """Brute-force count of ILU0's update products on a pattern (Algorithm
+    2's inner loop): for every block (i, k) with k < i, the j > k present in
+    both row i and row k."""
+    rows = [set(colidx[rowptr[i]:rowptr[i + 1]].tolist()) for i in range(nb)]
+    return sum(1 for i in range(nb) for k in rows[i] if k < i for j in rows[i] if j > k and j in rows[k])
+
+
+@pytest.mark.parametrize("schedule", ["natural", "level", "colour_kempe"])
+def test_kept_analysis_matches_the_one_shot_analysis(schedule):
+    """opm_analysis_create (host only) keeps the analysis opm_bsr_analyse
+    computes: the same permutation and counts; its update-product count
+    equals a brute-force count on the permuted pattern."""
+    import oracle as O
+    s = synth.one_way_system(synth.random_pattern_system(150, 4, 77), 0.4, 78)
+    st, perm, info = opm.opm_bsr_analyse(s.nb, s.rowptr, s.colidx, schedule)
+    assert st == opm.OPM_OK
+    with opm.Analysis(s.nb, s.rowptr, s.colidx, schedule) as an:
+        np.testing.assert_array_equal(an.permutation(), perm)
+        assert (an.nb, an.nnzb) == (s.nb, s.nnzb)
+        for f in ("schedule", "nsets", "nphases", "nnzb_kept", "nnzb_lower", "nnzb_upper", "nupdates"):
+            assert getattr(an.info, f) == getattr(info, f), f
+    prow, pcol, _ = O.permute(s.nb, s.rowptr, s.colidx, s.vals, perm)
+    assert info.nupdates == _update_products(s.nb, prow, pcol) > 0
+
+
+def test_kept_analysis_reports_pattern_errors_and_bad_arguments():
+    s = synth.config1()
+    ci = s.colidx.copy()
+    a = s.rowptr[5]
+    ci[a] = ci[a + 1]  # duplicate column in row 5
+    with pytest.raises(opm.OpmError) as e:
+        opm.Analysis(s.nb, s.rowptr, ci, "colour")
+    assert e.value.status == opm.OPM_ERR_PATTERN and opm.opm_last_error_row(None) == 5
+    with pytest.raises(opm.OpmError):
+        opm.Analysis(s.nb, s.rowptr, s.colidx, 99)
+    import ctypes
+    out = ctypes.c_void_p()
+    assert opm.lib().opm_bsr_create_from_analysis(None, s.vals.ctypes.data, None, ctypes.byref(out)) == \
+        opm.OPM_ERR_ARG and not out.value

@@ -156,3 +156,78 @@ def test_batch_async_launch():
     assert (s1, st1, it1, rr1) == (s2, st2, it2, rr2)
     for a, c in zip(xs, xs2):
         np.testing.assert_array_equal(a.cpu().numpy(), c.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("part", [False, True])
+def test_handle_from_kept_analysis_equals_a_created_one(precision, part):
+    """A handle made from a kept analysis (opm_bsr_create_from_analysis) has
+    the created handle's order, factors and solves, bitwise, also after the
+    analysis object is gone and after a refactorisation with new values."""
+    s = synth.config2() if not part else synth.config1()
+    pt = synth.partition_grid(s, 6) if part else None
+    b = dev(rhs(s))
+    an = opm.Analysis(s.nb, dev(s.rowptr), dev(s.colidx), "colour_kempe", part=pt)
+    with opm.Solver(s.nb, dev(s.rowptr), dev(s.colidx), dev(s.vals), schedule="colour_kempe", precision=precision,
+                    part=pt) as ref:
+        h = opm.Solver.from_analysis(an, dev(s.vals), precision=precision)
+        an.close()
+        with h:
+            assert h.status == ref.status == opm.OPM_OK
+            np.testing.assert_array_equal(h.permutation(), ref.permutation())
+            assert h.info().nupdates == ref.info().nupdates > 0
+            for k in range(2):
+                if k == 1:
+                    v = dev(synth.newton_update(s, 5)[0])
+                    assert h.factor(v) == ref.factor(v) == opm.OPM_OK
+                la, da = h.factors()
+                lb, db = ref.factors()
+                np.testing.assert_array_equal(la, lb)
+                np.testing.assert_array_equal(da, db)
+                # the Newton-updated values need more than 200 iterations at 1e-6
+                xa, sta, ita, rra = h.solve(b, rtol=1e-6)
+                xb, stb, itb, rrb = ref.solve(b, rtol=1e-6)
+                assert (sta, ita, rra) == (stb, itb, rrb) and sta in (opm.OPM_OK, opm.OPM_NOT_CONVERGED)
+                np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_members_can_sit_a_launch_out(precision):
+    """opm_batch_launch with b[i] = x[i] = NULL: the member's x, values,
+    factors and state are untouched (its later solve alone equals a fresh
+    handle's), the others' results are bitwise those of their solves alone,
+    with and without a refactorisation in the launch."""
+    syss = systems()[:6]
+    bs = [dev(rhs(s)) for s in syss]
+    new_vals = [dev(synth.newton_update(s, 9)[0]) for s in syss]
+    handles = [make(s, precision) for s in syss]
+    active = [k % 2 == 0 for k in range(len(syss))]
+    xs = [torch.full_like(b, np.nan) for b in bs]
+    with opm.Batch([h.h for h in handles]) as bt:
+        for refactor in (False, True):
+            vals = [v if a else None for v, a in zip(new_vals, active)] if refactor else None
+            assert bt.launch(vals, [b if a else None for b, a in zip(bs, active)],
+                             [x if a else None for x, a in zip(xs, active)], rtol=1e-8) == opm.OPM_OK
+            s_all, st, it, rr = bt.wait()
+            assert s_all == opm.OPM_OK
+            for k, s in enumerate(syss):
+                if not active[k]:
+                    assert (st[k], it[k], rr[k]) == (opm.OPM_OK, 0, 0.0)
+                    assert torch.isnan(xs[k]).all()
+                    continue
+                vk = new_vals[k] if refactor else dev(s.vals)
+                with opm.Solver(s.nb, dev(s.rowptr), dev(s.colidx), vk, schedule="colour", precision=precision) as sv:
+                    xa, sta, ita, rra = sv.solve(bs[k], rtol=1e-8)
+                assert (st[k], it[k], rr[k]) == (sta, ita, rra)
+                np.testing.assert_array_equal(xs[k].cpu().numpy(), xa.cpu().numpy())
+    # the members that sat out still hold their original factors
+    for k, s in enumerate(syss):
+        if active[k]:
+            continue
+        xa, sta, ita, rra = handles[k].solve(bs[k], rtol=1e-8)
+        with make(s, precision) as fresh:
+            xb, stb, itb, rrb = fresh.solve(bs[k], rtol=1e-8)
+        assert (sta, ita, rra) == (stb, itb, rrb)
+        np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    for h in handles:
+        h.close()
