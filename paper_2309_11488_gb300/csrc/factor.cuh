@@ -239,12 +239,14 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
 // One launch per phase, one 32-row slice per warp.  ONE_PASS takes the
 // one-pass walk for the rows that allow it; MINB is the launch's resident
 // CTAs per SM.  Measured at the 949,871-cell workload (event-timed
-// refactorisations): FP32 factors 0.513 -> 0.464 ms with the one-pass walk
-// at four CTAs per SM; FP64 factors are bound by the FP64 pipe in the large
-// phases (54 FMAs per L block), where the one-pass walk's registers cost
-// more occupancy than its shorter load chains gain (0.685 -> 0.696 ms at
-// three CTAs per SM), so they keep the two-step path there and take the
-// one-pass walk only in the small phases, which are latency chains.
+// refactorisations, A/B in one process): FP32 factors 0.509 -> 0.460 ms
+// with the one-pass walk at four CTAs per SM.  FP64 factors are bound by
+// the FP64 pipe in the large phases (54 FMAs per L block), where the
+// one-pass walk's registers cost more occupancy than its shorter load
+// chains gain (0.685 -> 0.696 ms at three CTAs per SM), and in the small
+// phases its 104 registers made them slower too (0.668 -> 0.694 ms): FP64
+// factors keep the two-step path, which copies before the dependency wait
+// (0.705 -> 0.694 ms).
 template <typename TF, bool ONE_PASS, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_factor_phase(Batch B, int c) {
   // the two-step path waits after its copy (EARLY_COPY); the one-pass walk

@@ -4,7 +4,9 @@
 // twice: all projections of a pass in one launch (partial sums per 256-row
 // tile, then a fixed-order reduction), the corrections in another.  The
 // scalar part (Hessenberg column, Givens rotations, the small triangular
-// solve) runs on the host in FP64, as in the oracle.
+// solve, the restart test) runs in FP64 on the device, in one warp, in the
+// oracle's order; the whole solve is one graph launch whose Arnoldi steps
+// are the body of a device-side while loop.
 #pragma once
 
 #include "kernels.cuh"
@@ -26,15 +28,36 @@ __global__ void __launch_bounds__(256) k_gm_operator(Batch B, const double *x, d
   }
 }
 
-// part[tile][q] = sum over the tile's entries of V_q . w, q < nv (V_q at
-// V + q * stride): per row, then a warp butterfly, then the warps in order.
-__global__ void __launch_bounds__(256) k_gm_dots(int64_t n3, const double *V, int64_t stride, int nv,
-                                                 const double *w, double *part) {
+// ------------------------------------------------------------------
+// Device-side control of one GMRES(m) solve (the oracle's steps in its
+// order).  sel arguments pick a vector from the state: the Arnoldi column
+// j (0), or a fixed one (1).
+
+struct GmState {
+  double tol, n0, beta, nrm2;  // nrm2: the last ||w||^2 or ||r||^2
+  double relres;
+  int32_t m, maxit, j, k;      // restart length, step limit, column, steps taken
+  int32_t status;              // kRunning while the solve goes on, then an opm_status
+  int32_t conv;                // the cycle ended by the stopping rule
+  int32_t update;              // the closing cycle updates x (not after a breakdown)
+  int32_t pad;
+  double h1[kGmMaxVec], h2[kGmMaxVec], y[kGmMaxVec];
+  double cs[kGmMaxVec], sn[kGmMaxVec], g[kGmMaxVec];
+  double H[kGmMaxVec * kGmMaxVec];  // H[i * kGmMaxVec + c], (m + 1) x m used
+};
+
+__device__ __forceinline__ int gm_nv(const GmState *gs, int sel) { return sel == 0 ? gs->j + 1 : 1; }
+
+// part[tile][q] = V_q . w for q < nv (sel 0: the columns 0..j; sel 1: V = w
+// itself, nv = 1), as k_gm_dots.
+__global__ void __launch_bounds__(256) k_gm_dots_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
+                                                   int sel, const double *w, double *part) {
   __shared__ double sm[kGmMaxVec][8];
+  const int nv = gm_nv(gs, sel);
   const int64_t e0 = (int64_t)blockIdx.x * 3 * kSpmvRows + 3 * threadIdx.x;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-  if (e0 + 2 < n3 + 0) {
+  if (e0 + 2 < n3) {
     w0 = __ldcg(w + e0);
     w1 = __ldcg(w + e0 + 1);
     w2 = __ldcg(w + e0 + 2);
@@ -56,8 +79,11 @@ __global__ void __launch_bounds__(256) k_gm_dots(int64_t n3, const double *V, in
   }
 }
 
-// out[q] = sum over tiles (in a fixed order) of part[tile][q]; one CTA per q.
-__global__ void __launch_bounds__(256) k_gm_reduce(const double *part, int ntiles, double *out) {
+// out[q] = sum over tiles of part[tile][q], q < nv; one CTA per q (a grid of
+// kGmMaxVec CTAs, the ones past nv return).
+__global__ void __launch_bounds__(256) k_gm_reduce_s(const double *part, int ntiles, const GmState *gs, int sel,
+                                                     double *out) {
+  if ((int)blockIdx.x >= gm_nv(gs, sel)) return;
   __shared__ double sm[8];
   const int q = blockIdx.x;
   double acc[1] = {0.0};
@@ -72,29 +98,161 @@ __global__ void __launch_bounds__(256) k_gm_reduce(const double *part, int ntile
   }
 }
 
-// mode 0: w -= sum_q coef[q] V_q; 1: w = sum_q coef[q] V_q (q ascending).
-__global__ void __launch_bounds__(256) k_gm_combine(int64_t n3, const double *V, int64_t stride, int nv,
-                                                    const double *coef, double *w, int mode) {
+// mode 0: w -= sum_{q <= j} coef[q] V_q (a Gram-Schmidt pass); mode 1:
+// w = sum_{q < j} y[q] V_q (the cycle's correction, only when it updates x).
+__global__ void __launch_bounds__(256) k_gm_combine_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
+                                                      const double *coef, double *w, int mode) {
+  __shared__ double c[kGmMaxVec];
+  if (mode == 1 && !gs->update) return;
+  const int nv = mode == 0 ? gs->j + 1 : gs->j;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) c[q] = coef[q];
+  __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int q = 0; q < nv; ++q) acc = fma(__ldcg(coef + q), __ldcg(V + q * stride + e), acc);
+    for (int q = 0; q < nv; ++q) acc = fma(c[q], __ldcg(V + q * stride + e), acc);
     w[e] = mode == 0 ? w[e] - acc : acc;
   }
 }
 
-// out = w / sqrt(*nrm2) (zero when *nrm2 == 0), or w / beta when nrm2 is null.
-__global__ void __launch_bounds__(256) k_gm_scale(int64_t n3, const double *w, const double *nrm2, double beta,
-                                                  double *out) {
-  const double d = nrm2 ? sqrt(__ldcg(nrm2)) : beta;
+// sel 0: V_{j+1} = w / sqrt(nrm2) (zero when the norm is); sel 1: V_0 = w /
+// beta at the start of a cycle (only while the solve runs).
+__global__ void __launch_bounds__(256) k_gm_scale_s(int64_t n3, const double *w, const GmState *gs, int sel,
+                                                    double *V, int64_t stride) {
+  if (sel == 1 && gs->status != kRunning) return;
+  const double d = sel == 0 ? sqrt(gs->nrm2) : gs->beta;
+  double *out = V + (sel == 0 ? (int64_t)(gs->j + 1) * stride : 0);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = d != 0.0 ? w[e] / d : 0.0;
 }
 
-// out = a - b (mode 0), out += a (mode 1)
-__global__ void __launch_bounds__(256) k_gm_vec(int64_t n3, const double *a, const double *b, double *out,
-                                                int mode) {
+// dst = V_j (sel 0) or src (sel 1).
+__global__ void __launch_bounds__(256) k_gm_copy_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
+                                                   int sel, const double *src, double *dst) {
+  const double *from = sel == 0 ? V + (int64_t)gs->j * stride : src;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = mode == 0 ? a[e] - b[e] : out[e] + a[e];
+    dst[e] = from[e];
+}
+
+// mode 0: out = a - b; mode 1: out += a when the closing cycle updates x;
+// mode 2: out = 0 when the solve failed (negative status).
+__global__ void __launch_bounds__(256) k_gm_vec_s(int64_t n3, const double *a, const double *b, double *out, int mode,
+                                                  const GmState *gs) {
+  if (mode == 1 && !gs->update) return;
+  if (mode == 2 && gs->status >= 0) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = mode == 0 ? a[e] - b[e] : mode == 1 ? out[e] + a[e] : 0.0;
+}
+
+// Start: n0 = ||b||, the stopping threshold, the first cycle's g; the loop
+// runs only when there is something to solve.  gs->tol holds rtol on entry.
+__global__ void k_gm_init(GmState *gs, cudaGraphConditionalHandle loop) {
+  const double n0 = sqrt(gs->nrm2);
+  gs->n0 = n0;
+  gs->j = 0;
+  gs->k = 0;
+  gs->conv = 0;
+  gs->update = 0;
+  if (!isfinite(n0)) gs->status = OPM_ERR_NONFINITE;
+  else if (n0 == 0.0) gs->status = OPM_OK;
+  else if (gs->maxit == 0) gs->status = OPM_NOT_CONVERGED;
+  else gs->status = kRunning;
+  gs->tol = gs->tol * n0;
+  gs->beta = n0;
+  for (int i = 0; i < kGmMaxVec; ++i) gs->g[i] = 0.0;
+  gs->g[0] = n0;
+  cudaGraphSetConditional(loop, gs->status == kRunning ? 1u : 0u);
+}
+
+// One Arnoldi step's scalar part: the Hessenberg column from the two
+// Gram-Schmidt passes and the norm, the earlier rotations, the new
+// rotation, g, and the end-of-cycle test (stopping rule, restart length,
+// step limit); a zero rotation is a breakdown and a non-finite g a failure,
+// both ending the solve without an update.  Opens the end-of-cycle branch.
+__global__ void k_gm_step(GmState *gs, cudaGraphConditionalHandle cycle_end) {
+  const int j = gs->j, m = gs->m;
+  constexpr int L = kGmMaxVec;
+  double *H = gs->H;
+  gs->k += 1;
+  for (int i = 0; i <= j; ++i) H[i * L + j] = gs->h1[i] + gs->h2[i];
+  const double hn = sqrt(gs->nrm2);
+  H[(j + 1) * L + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * L + j], c = H[(i + 1) * L + j];
+    H[i * L + j] = gs->cs[i] * a + gs->sn[i] * c;
+    H[(i + 1) * L + j] = -gs->sn[i] * a + gs->cs[i] * c;
+  }
+  const double a = H[j * L + j], c = H[(j + 1) * L + j];
+  const double den = sqrt(a * a + c * c);
+  bool end = false;
+  if (den == 0.0) {
+    gs->status = OPM_ERR_BREAKDOWN;
+    gs->update = 0;
+    end = true;
+  } else {
+    gs->cs[j] = a / den;
+    gs->sn[j] = c / den;
+    H[j * L + j] = den;
+    H[(j + 1) * L + j] = 0.0;
+    gs->g[j + 1] = -gs->sn[j] * gs->g[j];
+    gs->g[j] = gs->cs[j] * gs->g[j];
+    if (!isfinite(gs->g[j + 1])) {
+      gs->status = OPM_ERR_NONFINITE;
+      gs->update = 0;
+      end = true;
+    } else {
+      const bool conv = fabs(gs->g[j + 1]) <= gs->tol || hn == 0.0;
+      gs->j = j + 1;
+      gs->conv = conv;
+      end = conv || j + 1 == m || gs->k >= gs->maxit;
+      gs->update = end;
+    }
+  }
+  cudaGraphSetConditional(cycle_end, end ? 1u : 0u);
+}
+
+// End of a cycle: H y = g by back substitution over the cycle's j columns.
+__global__ void k_gm_trisolve(GmState *gs) {
+  if (!gs->update) return;
+  const int j = gs->j;
+  constexpr int L = kGmMaxVec;
+  for (int i = j - 1; i >= 0; --i) {
+    double acc = gs->g[i];
+    for (int l = i + 1; l < j; ++l) acc -= gs->H[i * L + l] * gs->y[l];
+    gs->y[i] = acc / gs->H[i * L + i];
+  }
+}
+
+// After a cycle's update and the residual norm: stop (the stopping rule,
+// the step limit, or a failure), or restart with beta = ||r||.
+__global__ void k_gm_restart(GmState *gs) {
+  if (gs->status == kRunning) {
+    if (gs->conv) {
+      gs->status = OPM_OK;
+    } else if (gs->k >= gs->maxit) {
+      gs->status = OPM_NOT_CONVERGED;
+    } else {
+      const double beta = sqrt(gs->nrm2);
+      gs->beta = beta;
+      if (beta <= gs->tol) {
+        gs->status = OPM_OK;
+      } else {
+        gs->j = 0;
+        for (int i = 0; i < kGmMaxVec; ++i) gs->g[i] = 0.0;
+        gs->g[0] = beta;
+      }
+    }
+  }
+  gs->update = 0;
+  gs->conv = 0;
+}
+
+__global__ void k_gm_cond(const GmState *gs, cudaGraphConditionalHandle loop) {
+  cudaGraphSetConditional(loop, gs->status == kRunning ? 1u : 0u);
+}
+
+// The true residual's norm (relres; NaN after a non-finite failure).
+__global__ void k_gm_final(GmState *gs) {
+  gs->relres = gs->status == OPM_ERR_NONFINITE ? nan("") : gs->n0 > 0.0 ? sqrt(gs->nrm2) / gs->n0 : 0.0;
 }
 
 }  // namespace opm

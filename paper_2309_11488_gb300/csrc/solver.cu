@@ -45,9 +45,12 @@ struct opm_solver {
   std::vector<void *> well_allocs;  // arrays of the current wells (replaced by opm_set_wells)
   double *gm_V = nullptr;           // GMRES: Krylov basis, gm_m + 1 vectors
   double *gm_part = nullptr;        // GMRES: per-tile partial sums
-  double *gm_sc = nullptr;          // GMRES: device scalars (projections, norm, y)
-  double *gm_host = nullptr;        // GMRES: pinned host mirror of gm_sc
   int gm_m = 0;
+  opm::GmState *gm_state = nullptr; // GMRES: device-side control state
+  opm::GmState *gm_hstate = nullptr;  // GMRES: pinned host copy (inputs and outcome)
+  cudaGraphExec_t gm_exec = nullptr;  // GMRES: the whole solve, built on first use
+  double *gm_exec_V = nullptr;        // basis the graph was built for
+  bool gm_exec_wells = false;         // wells the graph was built for
   int64_t dev_bytes = 0;
   double *vals_stage = nullptr;  // caller's values when given from host
   double *vec_in = nullptr, *vec_out = nullptr;  // caller-order staging
@@ -231,7 +234,7 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
   for (int c = 0; c < R.nphases; ++c) {
     const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
     if (cnt == 0) continue;
-    if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF, true, 1>, (cnt + 1) / 2, 64, st, R.B, c);
+    if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF, kFp32, 1>, (cnt + 1) / 2, 64, st, R.B, c);
     else launch_pdl(k_factor_phase<TF, kFp32, 4>, blocks8(cnt), 256, st, R.B, c);
     ++n;
   }
@@ -1022,17 +1025,155 @@ void opm_destroy(opm_handle h) {
   for (void *p : h->well_allocs) cudaFree(p);
   if (h->gm_V) cudaFree(h->gm_V);
   if (h->gm_part) cudaFree(h->gm_part);
-  if (h->gm_sc) cudaFree(h->gm_sc);
-  if (h->gm_host) cudaFreeHost(h->gm_host);
+  if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
+  if (h->gm_state) cudaFree(h->gm_state);
+  if (h->gm_hstate) cudaFreeHost(h->gm_hstate);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   delete h;
 }
 
-// Restarted GMRES(m), the steps of the oracle's orc_gmres in the same order:
-// vector work in the kernels of gmres.cuh and the sweeps/SpMV of the
-// BiCGStab path, the Hessenberg column, Givens rotations and the small
-// triangular solve on the host (FP64), one host read per Arnoldi step.
+// Adds a conditional node of the given type at the current point of the
+// capture on cap (the capture then continues after it) and returns its body.
+opm_status capture_conditional(cudaStream_t cap, cudaGraphConditionalHandle ch, cudaGraphConditionalNodeType type,
+                               cudaGraph_t *body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = ch;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = cp.conditional.phGraph_out[0];
+  return OPM_OK;
+}
+
+// The conditional handle of the graph being captured on cap.
+opm_status capture_handle(cudaStream_t cap, cudaGraphConditionalHandle *ch) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  CK(cudaGraphConditionalHandleCreate(ch, g, 0, cudaGraphCondAssignDefault));
+  return OPM_OK;
+}
+
+// Restarted GMRES(m), the steps of the oracle's orc_gmres in the same order,
+// as one graph: the start (b gathered, r = b, x = 0, ||b||, v_0 = r / beta),
+// a device-side while loop whose body is one Arnoldi step (v_j through the
+// preconditioner and the operator, classical Gram-Schmidt twice, the norm,
+// v_{j+1}, then the Hessenberg column, Givens rotations and g in one
+// thread) with a conditional end-of-cycle branch (H y = g, x += inv(M) V y,
+// r = b - A x, the restart test, v_0 = r / beta), and the end (true
+// residual, x back to the caller's order, zero on failure).  The host reads
+// the outcome once.
+opm_status gm_build(opm_solver *h) {
+  Runner &R = *h->run;
+  const Sys &S = h->sys;
+  const int64_t n3 = 3ll * h->n;
+  const int ntile = S.ntiles_s;
+  const int egrid = (int)std::min<int64_t>((n3 + 255) / 256, 152 * 8);
+  double *V = h->gm_V;
+  GmState *gs = h->gm_state;
+  double *part = h->gm_part;
+  cudaStream_t cap;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  opm_status s = OPM_OK;
+  cudaGraph_t g = nullptr, body = nullptr, tail_body = nullptr;
+  cudaGraphConditionalHandle ch_loop = 0, ch_end = 0;
+  auto dots = [&](const double *Vb, int sel, const double *w, double *out) {
+    k_gm_dots_s<<<ntile, 256, 0, cap>>>(n3, Vb, n3, gs, sel, w, part);
+    k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile, gs, sel, out);
+  };
+  auto op = [&](int which, const double *in, double *out) {  // out = A in - wells
+    if (R.has_wells) k_wells<<<1, 256, 0, cap>>>(R.B, which);
+    k_gm_operator<<<ntile, 256, 0, cap>>>(R.B, in, out);
+  };
+  // ---- start, loop node, end
+  if (cudaGraphCreate(&g, 0) != cudaSuccess ||
+      cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    s = OPM_ERR_CUDA;
+  if (s == OPM_OK) {
+    k_gather<<<R.ntiles, 256, 0, cap>>>(R.B);
+    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.w, S.p);
+    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.w, S.r);
+    if (cudaMemsetAsync(S.x, 0, sizeof(double) * (size_t)n3, cap) != cudaSuccess) s = OPM_ERR_CUDA;
+    dots(S.r, 1, S.r, &gs->nrm2);
+    s = capture_handle(cap, &ch_loop);
+    if (s == OPM_OK) {
+      k_gm_init<<<1, 1, 0, cap>>>(gs, ch_loop);
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3);
+      s = capture_conditional(cap, ch_loop, cudaGraphCondTypeWhile, &body);
+    }
+    if (s == OPM_OK) {
+      op(2, S.x, S.v);
+      k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);
+      dots(S.r, 1, S.r, &gs->nrm2);
+      k_gm_final<<<1, 1, 0, cap>>>(gs);
+      k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.x, S.x, S.x, 2, gs);  // x = 0 on failure
+      k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.x, S.t);
+      k_scatter<<<R.ntiles, 256, 0, cap>>>(R.B);
+    }
+    if (cudaStreamEndCapture(cap, &g) != cudaSuccess) s = OPM_ERR_CUDA;
+  }
+  // ---- loop body: one Arnoldi step, then the end-of-cycle branch
+  if (s == OPM_OK) {
+    if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) {
+      s = OPM_ERR_CUDA;
+    } else {
+      k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 0, nullptr, S.w);  // w = v_j
+      launch_apply<kModePlain>(R, cap);                                    // t = inv(M) v_j
+      op(4, S.t, S.v);                                                     // v = A t
+      dots(V, 0, S.v, gs->h1);
+      k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->h1, S.v, 0);
+      dots(V, 0, S.v, gs->h2);
+      k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, 0);
+      dots(S.v, 1, S.v, &gs->nrm2);
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.v, gs, 0, V, n3);
+      s = capture_handle(cap, &ch_end);
+      if (s == OPM_OK) {
+        k_gm_step<<<1, 1, 0, cap>>>(gs, ch_end);
+        s = capture_conditional(cap, ch_end, cudaGraphCondTypeIf, &tail_body);
+      }
+      if (s == OPM_OK) k_gm_cond<<<1, 1, 0, cap>>>(gs, ch_loop);
+      if (cudaStreamEndCapture(cap, &body) != cudaSuccess) s = OPM_ERR_CUDA;
+    }
+  }
+  // ---- end of a cycle
+  if (s == OPM_OK) {
+    if (cudaStreamBeginCaptureToGraph(cap, tail_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) {
+      s = OPM_ERR_CUDA;
+    } else {
+      k_gm_trisolve<<<1, 1, 0, cap>>>(gs);
+      k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->y, S.w, 1);  // w = V y
+      launch_apply<kModePlain>(R, cap);                                       // t = inv(M) V y
+      k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.t, S.t, S.x, 1, gs);           // x += t
+      op(2, S.x, S.v);
+      k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);           // r = b - A x
+      dots(S.r, 1, S.r, &gs->nrm2);
+      k_gm_restart<<<1, 1, 0, cap>>>(gs);
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3);             // v_0 = r / beta
+      if (cudaStreamEndCapture(cap, &tail_body) != cudaSuccess) s = OPM_ERR_CUDA;
+    }
+  }
+  if (s == OPM_OK && cudaGraphInstantiate(&h->gm_exec, g, 0) != cudaSuccess) s = OPM_ERR_CUDA;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (s != OPM_OK) {
+    fprintf(stderr, "opm_bsr: GMRES graph construction failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+    cudaGetLastError();
+    h->gm_exec = nullptr;
+  }
+  return s;
+}
+
 opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
                            int32_t *iters, double *relres) {
   if (!h || (h->n > 0 && (!b || !x)) || !(rtol >= 0.0) || maxit < 0 || restart < 0 || restart > kGmMaxVec - 1 ||
@@ -1053,6 +1194,8 @@ opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol
   const int ntile = h->sys.ntiles_s;
   // ---- buffers (kept for later calls; the basis grows with m)
   if (h->gm_m < m) {
+    if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
+    h->gm_exec = nullptr;
     if (h->gm_V) cudaFree(h->gm_V);
     h->gm_V = nullptr;
     h->gm_m = 0;
@@ -1065,154 +1208,35 @@ opm_status opm_gmres_solve(opm_handle h, const double *b, double *x, double rtol
   }
   // each buffer on its own: one that failed before is retried, none is used unallocated
   if ((!h->gm_part && cudaMalloc(&h->gm_part, sizeof(double) * (size_t)ntile * kGmMaxVec) != cudaSuccess) ||
-      (!h->gm_sc && cudaMalloc(&h->gm_sc, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess) ||
-      (!h->gm_host && cudaMallocHost(&h->gm_host, sizeof(double) * 4 * kGmMaxVec) != cudaSuccess)) {
+      (!h->gm_state && cudaMalloc(&h->gm_state, sizeof(GmState)) != cudaSuccess) ||
+      (!h->gm_hstate && cudaMallocHost(&h->gm_hstate, sizeof(GmState)) != cudaSuccess)) {
     cudaGetLastError();
     return OPM_ERR_OOM;
   }
   if ((s = runner_push(R)) != OPM_OK) return s;
-  const Sys &S = h->sys;
-  double *V = h->gm_V, *d_h1 = h->gm_sc, *d_h2 = h->gm_sc + kGmMaxVec, *d_nrm = h->gm_sc + 2 * kGmMaxVec,
-         *d_y = h->gm_sc + 3 * kGmMaxVec;
-  double *hh = h->gm_host;
-  const int egrid = (int)std::min<int64_t>((n3 + 255) / 256, 152 * 8);
-  auto dots = [&](const double *Vb, int nv, const double *w, double *out) {
-    k_gm_dots<<<ntile, 256, 0, st>>>(n3, Vb, n3, nv, w, h->gm_part);
-    k_gm_reduce<<<nv, 256, 0, st>>>(h->gm_part, ntile, out);
-  };
-  auto apply = [&](const double *in) {  // S.t = inv(M) in
-    CK(cudaMemcpyAsync(S.w, in, vbytes, cudaMemcpyDeviceToDevice, st));
-    launch_apply<kModePlain>(R, st);
-    return OPM_OK;
-  };
-  auto op = [&](int which, const double *in, double *out) {  // out = A in - wells
-    if (R.has_wells) k_wells<<<1, 256, 0, st>>>(R.B, which);
-    k_gm_operator<<<ntile, 256, 0, st>>>(R.B, in, out);
-  };
-  auto read = [&](int count) {
-    CK(cudaMemcpyAsync(hh, h->gm_sc, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return OPM_OK;
-  };
-  // ---- r = b (schedule order, kept in S.p), x = 0, n0 = ||r||
-  k_gather<<<R.ntiles, 256, 0, st>>>(R.B);
-  CK(cudaMemcpyAsync(S.p, S.w, vbytes, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(S.r, S.w, vbytes, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(S.x, 0, vbytes, st));
-  dots(S.r, 1, S.r, d_h1);
-  if ((s = read(1)) != OPM_OK) return s;
-  const double n0 = std::sqrt(hh[0]);
-  opm_status status = OPM_NOT_CONVERGED;
-  int32_t k = 0;
-  if (!std::isfinite(n0)) {
-    status = OPM_ERR_NONFINITE;
-  } else if (n0 == 0.0) {
-    status = OPM_OK;
-  } else {
-    const double tol = rtol * n0;
-    double beta = n0;
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
-    for (bool done = false; !done;) {
-      k_gm_scale<<<egrid, 256, 0, st>>>(n3, S.r, nullptr, beta, V);
-      std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
-      int j = 0;
-      bool conv = false;
-      for (; j < m && k < maxit; ++j) {
-        ++k;
-        double *vj = V + (size_t)j * n3, *w = S.v;
-        apply(vj);
-        op(4, S.t, w);
-        dots(V, j + 1, w, d_h1);
-        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j + 1, d_h1, w, 0);
-        dots(V, j + 1, w, d_h2);
-        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j + 1, d_h2, w, 0);
-        dots(w, 1, w, d_nrm);
-        k_gm_scale<<<egrid, 256, 0, st>>>(n3, w, d_nrm, 0.0, V + (size_t)(j + 1) * n3);
-        if ((s = read(2 * kGmMaxVec + 1)) != OPM_OK) return s;
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[kGmMaxVec + i];
-        const double hn = std::sqrt(hh[2 * kGmMaxVec]);
-        H[(size_t)(j + 1) * m + j] = hn;
-        for (int i = 0; i < j; ++i) {
-          const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-          H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-        }
-        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-        const double den = std::sqrt(a * a + c * c);
-        if (den == 0.0) {
-          status = OPM_ERR_BREAKDOWN;
-          done = true;
-          break;
-        }
-        cs[j] = a / den;
-        sn[j] = c / den;
-        H[(size_t)j * m + j] = den;
-        H[(size_t)(j + 1) * m + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        if (!std::isfinite(g[j + 1])) {
-          status = OPM_ERR_NONFINITE;
-          done = true;
-          break;
-        }
-        if (std::fabs(g[j + 1]) <= tol || hn == 0.0) {
-          conv = true;
-          ++j;
-          break;
-        }
-      }
-      if (done) break;
-      // ---- x += inv(M) V y with H y = g
-      for (int i = j - 1; i >= 0; --i) {
-        double acc = g[i];
-        for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
-        y[i] = acc / H[(size_t)i * m + i];
-      }
-      if (j > 0) {
-        CK(cudaMemcpyAsync(d_y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
-        k_gm_combine<<<egrid, 256, 0, st>>>(n3, V, n3, j, d_y, S.v, 1);
-        apply(S.v);
-        k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.t, nullptr, S.x, 1);
-      }
-      if (conv) {
-        status = OPM_OK;
-        break;
-      }
-      if (k >= maxit) {
-        status = OPM_NOT_CONVERGED;
-        break;
-      }
-      op(2, S.x, S.v);
-      k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.p, S.v, S.r, 0);
-      dots(S.r, 1, S.r, d_h1);
-      if ((s = read(1)) != OPM_OK) return s;
-      beta = std::sqrt(hh[0]);
-      if (beta <= tol) {
-        status = OPM_OK;
-        break;
-      }
-    }
+  if (h->gm_exec && (h->gm_exec_V != h->gm_V || h->gm_exec_wells != R.has_wells)) {
+    cudaGraphExecDestroy(h->gm_exec);
+    h->gm_exec = nullptr;
   }
-  // ---- true residual, x back to the caller's order (zeros on failure)
-  double rr = 0.0;
-  if (status == OPM_ERR_NONFINITE) {
-    rr = NAN;
-  } else if (n0 > 0.0) {
-    op(2, S.x, S.v);
-    k_gm_vec<<<egrid, 256, 0, st>>>(n3, S.p, S.v, S.r, 0);
-    dots(S.r, 1, S.r, d_h1);
-    if ((s = read(1)) != OPM_OK) return s;
-    rr = std::sqrt(hh[0]) / n0;
+  if (!h->gm_exec) {
+    if ((s = gm_build(h)) != OPM_OK) return s;
+    h->gm_exec_V = h->gm_V;
+    h->gm_exec_wells = R.has_wells;
   }
-  if (status < 0) CK(cudaMemsetAsync(S.x, 0, vbytes, st));
-  CK(cudaMemcpyAsync(S.t, S.x, vbytes, cudaMemcpyDeviceToDevice, st));
-  k_scatter<<<R.ntiles, 256, 0, st>>>(R.B);
+  // ---- inputs, the solve, the outcome
+  GmState *hs = h->gm_hstate;
+  hs->tol = rtol;
+  hs->m = m;
+  hs->maxit = maxit;
+  hs->status = OPM_OK;
+  CK(cudaMemcpyAsync(h->gm_state, hs, offsetof(GmState, h1), cudaMemcpyHostToDevice, st));
+  CK(cudaGraphLaunch(h->gm_exec, st));
+  CK(cudaMemcpyAsync(hs, h->gm_state, offsetof(GmState, h1), cudaMemcpyDeviceToHost, st));
   if (!x_dev) CK(cudaMemcpyAsync(x, h->vec_out, vbytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (iters) *iters = k;
-  if (relres) *relres = rr;
-  return status;
+  if (iters) *iters = hs->k;
+  if (relres) *relres = hs->relres;
+  return (opm_status)hs->status;
 }
 
 opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, const int32_t *cells, const double *B,

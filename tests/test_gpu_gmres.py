@@ -91,3 +91,37 @@ def test_gmres_with_block_jacobi_and_wells():
     r = b - O.spmv_wells(s.nb, s.rowptr, s.colidx, s.vals, w, x)
     np.testing.assert_allclose(np.linalg.norm(r) / np.linalg.norm(b), rr, rtol=1e-6, atol=1e-14)
     assert np.linalg.norm(x - s.x_true) <= 1e-5 * np.linalg.norm(s.x_true)
+
+
+def test_gmres_graph_reused_across_restart_lengths_and_edge_cases():
+    """The solve runs as one graph built on first use: calls with other
+    restart lengths, host buffers and wells set afterwards keep the
+    oracle's step counts and x; maxit = 0 and a non-finite b take their
+    documented outcomes."""
+    s = synth.config1()
+    b = rhs(s)
+    with opm.Solver(s.nb, dev(s.rowptr), dev(s.colidx), dev(s.vals), schedule="colour_sl") as sv:
+        for restart, on_device in ((5, True), (30, False), (5, True), (12, False)):
+            x_ref, res, _ = O.solve_system_gmres(s.nb, s.rowptr, s.colidx, s.vals, b, 1e-8, 300, restart,
+                                                 "colour_sl")
+            xb = dev(b) if on_device else b.copy()
+            x, st, it, rr = sv.gmres(xb, rtol=1e-8, maxit=300, restart=restart)
+            x = x.cpu().numpy() if on_device else x
+            assert (st, it) == (res.status, res.iters) == (0, res.iters)
+            assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+        x, st, it, rr = sv.gmres(dev(b), rtol=1e-8, maxit=0, restart=5)
+        assert (st, it) == (opm.OPM_NOT_CONVERGED, 0) and rr == 1.0 and float(torch.abs(x).max()) == 0.0
+        bad = b.copy()
+        bad[7] = np.inf
+        x = np.full(3 * s.nb, 3.0)
+        x, st, it, rr = sv.gmres(bad, x, rtol=1e-8, restart=5)
+        assert st == opm.OPM_ERR_NONFINITE and np.isnan(rr) and not x.any()
+        # wells added after the graph was built: the graph is rebuilt with them
+        w = synth.wells(s, 2, 3)
+        bw = O.spmv_wells(s.nb, s.rowptr, s.colidx, s.vals, w, s.x_true)
+        assert sv.set_wells(w) == opm.OPM_OK
+        x, st, it, rr = sv.gmres(dev(bw), rtol=1e-8, maxit=300, restart=30)
+        x = x.cpu().numpy()
+        assert st == opm.OPM_OK
+        r = bw - O.spmv_wells(s.nb, s.rowptr, s.colidx, s.vals, w, x)
+        np.testing.assert_allclose(np.linalg.norm(r) / np.linalg.norm(bw), rr, rtol=1e-6, atol=1e-14)
