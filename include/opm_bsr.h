@@ -335,7 +335,13 @@ opm_status opm_spmv(opm_handle h, const double *x, double *y);
  * r, z host or device, 3*nb doubles, caller's order. */
 opm_status opm_ilu_apply(opm_handle h, const double *r, double *z);
 
-/* Release the handle and all its device memory.  NULL is ignored. */
+/* Release the handle and all its device memory.  NULL is ignored.
+ * Device memory of handles, batches and wells comes from one memory pool per
+ * device that the library owns, allocated and freed in stream order on the
+ * owner's stream (so creating or destroying a handle does not wait for work
+ * on other streams); memory a destroyed handle frees stays in the pool for
+ * later handles and batches and is not returned to the system before the
+ * process exits. */
 void opm_destroy(opm_handle h);
 
 /* Static text of a status code. */

@@ -355,12 +355,13 @@ __device__ __forceinline__ void row_spmv(const int32_t *__restrict__ rp, const i
     if (len > k) {
       const int cnt = __popc(m);
       const int q = __popc(m & lt);
-      const int j = __ldg(col + base + q);
+      // the matrix is read once per product: streaming loads leave L2 to the vectors
+      const int j = __ldcs(col + base + q);
       const double *a = val + 9ll * base + q;
       const double x0 = __ldg(x + 3ll * j), x1 = __ldg(x + 3ll * j + 1), x2 = __ldg(x + 3ll * j + 2);
-      const double a0 = __ldg(a), a1 = __ldg(a + cnt), a2 = __ldg(a + 2 * cnt);
-      const double a3 = __ldg(a + 3 * cnt), a4 = __ldg(a + 4 * cnt), a5 = __ldg(a + 5 * cnt);
-      const double a6 = __ldg(a + 6 * cnt), a7 = __ldg(a + 7 * cnt), a8 = __ldg(a + 8 * cnt);
+      const double a0 = __ldcs(a), a1 = __ldcs(a + cnt), a2 = __ldcs(a + 2 * cnt);
+      const double a3 = __ldcs(a + 3 * cnt), a4 = __ldcs(a + 4 * cnt), a5 = __ldcs(a + 5 * cnt);
+      const double a6 = __ldcs(a + 6 * cnt), a7 = __ldcs(a + 7 * cnt), a8 = __ldcs(a + 8 * cnt);
       y0 = fma(a0, x0, fma(a1, x1, fma(a2, x2, y0)));
       y1 = fma(a3, x0, fma(a4, x1, fma(a5, x2, y1)));
       y2 = fma(a6, x0, fma(a7, x1, fma(a8, x2, y2)));

@@ -17,6 +17,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -90,6 +92,7 @@ struct Runner {
   Batch B{};
   Sys *h_sys = nullptr;      // pinned staging of the descriptors
   Result *h_res = nullptr;   // pinned results
+  size_t h_sys_cls = 0, h_res_cls = 0;  // their size classes in the pinned free list
   Result *d_res = nullptr;
   std::vector<void *> allocs;
   int64_t dev_bytes = 0;
@@ -129,6 +132,16 @@ const char *const kStatusText[] = {"ok",
     }                                                                             \
   } while (0)
 
+std::mutex &pinned_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+std::map<size_t, std::vector<void *>> &pinned_free_list() {
+  static std::map<size_t, std::vector<void *>> fl;
+  return fl;
+}
+
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -139,13 +152,50 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of handles, batches and wells comes from one memory pool per
+// device, allocated and freed in stream order (cudaMallocFromPoolAsync /
+// cudaFreeAsync on the owner's stream), and the pool keeps what is freed
+// for the next allocation.  Unlike cudaMalloc / cudaFree, creating or
+// destroying a handle then does not serialise with work running on other
+// streams (a serving loop evicting and remaking instances while others
+// solve).  The pool's memory stays with the process.
+cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
 template <typename T>
-opm_status dalloc(std::vector<void *> &allocs, int64_t &bytes_acc, T **p, size_t count) {
+opm_status dalloc(std::vector<void *> &allocs, int64_t &bytes_acc, cudaStream_t st, T **p, size_t count) {
   *p = nullptr;
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc((void **)p, bytes);
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return OPM_ERR_CUDA;
+  cudaError_t e = cudaMallocFromPoolAsync((void **)p, bytes, pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     return e == cudaErrorMemoryAllocation ? OPM_ERR_OOM : OPM_ERR_CUDA;
   }
   allocs.push_back(*p);
@@ -153,10 +203,47 @@ opm_status dalloc(std::vector<void *> &allocs, int64_t &bytes_acc, T **p, size_t
   return OPM_OK;
 }
 
+// Frees allocations of dalloc in stream order on st.
+void dfree(std::vector<void *> &allocs, cudaStream_t st) {
+  for (void *p : allocs) cudaFreeAsync(p, st);
+  allocs.clear();
+  cudaGetLastError();
+}
+
+// Page-locked host buffers of batches (descriptors, results), kept in a
+// process-wide free list by size class: cudaMallocHost blocks concurrency
+// with other streams, so it runs only when no freed buffer of the size is
+// left.
+void *pinned_alloc(size_t bytes, size_t *cls) {
+  static_assert(sizeof(size_t) >= 8, "64-bit sizes");
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  *cls = c;
+  std::lock_guard<std::mutex> lock(pinned_mutex());
+  auto &fl = pinned_free_list()[c];
+  if (!fl.empty()) {
+    void *p = fl.back();
+    fl.pop_back();
+    return p;
+  }
+  void *p = nullptr;
+  if (cudaMallocHost(&p, c) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void pinned_release(void *p, size_t cls) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(pinned_mutex());
+  pinned_free_list()[cls].push_back(p);
+}
+
 template <typename T>
 opm_status upload(std::vector<void *> &allocs, int64_t &bytes_acc, cudaStream_t st, T **p,
                   const std::vector<T> &v) {
-  opm_status s = dalloc(allocs, bytes_acc, p, v.size());
+  opm_status s = dalloc(allocs, bytes_acc, st, p, v.size());
   if (s != OPM_OK) return s;
   if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   return OPM_OK;
@@ -504,9 +591,9 @@ void runner_destroy(Runner *R) {
   if (R->iter_exec) cudaGraphExecDestroy(R->iter_exec);
   if (R->factor_exec) cudaGraphExecDestroy(R->factor_exec);
   if (R->fs_exec) cudaGraphExecDestroy(R->fs_exec);
-  for (void *p : R->allocs) cudaFree(p);
-  if (R->h_sys) cudaFreeHost(R->h_sys);
-  if (R->h_res) cudaFreeHost(R->h_res);
+  dfree(R->allocs, R->stream);
+  pinned_release(R->h_sys, R->h_sys_cls);
+  pinned_release(R->h_res, R->h_res_cls);
   for (auto &e : R->kev)
     if (e) cudaEventDestroy(e);
   if (R->ev_done) cudaEventDestroy(R->ev_done);
@@ -555,14 +642,14 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
     if (R->cp_sweeps > 0 && !h->sys.lu2) {
       uint8_t *p = nullptr;
-      sa = dalloc(h->allocs, h->dev_bytes, &p, esz * (size_t)h->an.lu_vals);
+      sa = dalloc(h->allocs, h->dev_bytes, stream, &p, esz * (size_t)h->an.lu_vals);
       h->sys.lu2 = p;
     }
     if (sa == OPM_OK && R->tri_sweeps > 0 && !h->sys.y2) {
       uint8_t *p = nullptr;
-      sa = dalloc(h->allocs, h->dev_bytes, &p, esz * 3 * (size_t)h->n);
+      sa = dalloc(h->allocs, h->dev_bytes, stream, &p, esz * 3 * (size_t)h->n);
       h->sys.y2 = p;
-      if (sa == OPM_OK) sa = dalloc(h->allocs, h->dev_bytes, &h->sys.z2, 3 * (size_t)h->n);
+      if (sa == OPM_OK) sa = dalloc(h->allocs, h->dev_bytes, stream, &h->sys.z2, 3 * (size_t)h->n);
     }
     if (sa != OPM_OK) return fail(sa);
   }
@@ -633,12 +720,13 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_bwd, R->bwd_ptr)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles, tiles)) != OPM_OK) return fail(s);
   if ((s = upload(R->allocs, R->dev_bytes, stream, &d_tiles_s, tiles_s)) != OPM_OK) return fail(s);
-  if ((s = dalloc(R->allocs, R->dev_bytes, &d_bar, 64)) != OPM_OK) return fail(s);
-  if ((s = dalloc(R->allocs, R->dev_bytes, &d_sys, (size_t)R->nsys)) != OPM_OK) return fail(s);
-  if ((s = dalloc(R->allocs, R->dev_bytes, &R->d_res, (size_t)R->nsys)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, stream, &d_bar, 64)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, stream, &d_sys, (size_t)R->nsys)) != OPM_OK) return fail(s);
+  if ((s = dalloc(R->allocs, R->dev_bytes, stream, &R->d_res, (size_t)R->nsys)) != OPM_OK) return fail(s);
   if (cudaMemsetAsync(d_bar, 0, 64 * sizeof(uint32_t), stream) != cudaSuccess) return fail(OPM_ERR_CUDA);
-  if (cudaMallocHost((void **)&R->h_sys, sizeof(Sys) * R->nsys) != cudaSuccess ||
-      cudaMallocHost((void **)&R->h_res, sizeof(Result) * R->nsys) != cudaSuccess) {
+  R->h_sys = static_cast<Sys *>(pinned_alloc(sizeof(Sys) * R->nsys, &R->h_sys_cls));
+  R->h_res = static_cast<Result *>(pinned_alloc(sizeof(Result) * R->nsys, &R->h_res_cls));
+  if (!R->h_sys || !R->h_res) {
     cudaGetLastError();
     return fail(OPM_ERR_OOM);
   }
@@ -790,7 +878,7 @@ opm_status staged_vals(opm_solver *h, const double *vals, const double **dev) {
     return OPM_OK;
   }
   if (!h->vals_stage) {
-    opm_status s = dalloc(h->allocs, h->dev_bytes, &h->vals_stage, 9 * (size_t)h->nnzb);
+    opm_status s = dalloc(h->allocs, h->dev_bytes, h->stream, &h->vals_stage, 9 * (size_t)h->nnzb);
     if (s != OPM_OK) return s;
   }
   CK(cudaMemcpyAsync(h->vals_stage, vals, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyHostToDevice,
@@ -892,29 +980,29 @@ opm_status alloc_system(opm_solver *h, const Analysis &an) {
   S.upd_ptr = p_upd;
   S.upd_dst = p_ud;
   S.upd_src = p_us;
-  if ((s = dalloc(A, bytes, &S.a_val, 9 * (size_t)h->nnzb)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, st, &S.a_val, 9 * (size_t)h->nnzb)) != OPM_OK) return s;
   if (h->fp32) {
     float *lu, *y;
-    if ((s = dalloc(A, bytes, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
-    if ((s = dalloc(A, bytes, &y, 3 * (size_t)nb)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, st, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, st, &y, 3 * (size_t)nb)) != OPM_OK) return s;
     S.lu = lu;
     S.y = y;
   } else {
     double *lu, *y;
-    if ((s = dalloc(A, bytes, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
-    if ((s = dalloc(A, bytes, &y, 3 * (size_t)nb)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, st, &lu, (size_t)an.lu_vals)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, st, &y, 3 * (size_t)nb)) != OPM_OK) return s;
     S.lu = lu;
     S.y = y;
   }
   double **vecs[] = {&S.x, &S.r, &S.rh, &S.p, &S.v, &S.ph, &S.s, &S.sh, &S.t, &S.w, &h->vec_in, &h->vec_out};
   for (double **pv : vecs)
-    if ((s = dalloc(A, bytes, pv, 3 * (size_t)nb)) != OPM_OK) return s;
-  if ((s = dalloc(A, bytes, &S.partials, 4 * (size_t)S.ntiles_s)) != OPM_OK) return s;
+    if ((s = dalloc(A, bytes, st, pv, 3 * (size_t)nb)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, st, &S.partials, 4 * (size_t)S.ntiles_s)) != OPM_OK) return s;
   const size_t ngroups = ((size_t)S.ntiles_s + 31) / 32;
-  if ((s = dalloc(A, bytes, &S.grp_partials, 4 * ngroups)) != OPM_OK) return s;
-  if ((s = dalloc(A, bytes, &S.grp_count, ngroups)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, st, &S.grp_partials, 4 * ngroups)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, st, &S.grp_count, ngroups)) != OPM_OK) return s;
   CK(cudaMemsetAsync(S.grp_count, 0, sizeof(uint32_t) * ngroups, st));
-  if ((s = dalloc(A, bytes, &S.st, 1)) != OPM_OK) return s;
+  if ((s = dalloc(A, bytes, st, &S.st, 1)) != OPM_OK) return s;
   DevState init{};
   init.status = OPM_OK;
   CK(cudaMemcpyAsync(S.st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st));
@@ -1019,10 +1107,9 @@ const char *opm_status_str(opm_status s) {
 void opm_destroy(opm_handle h) {
   if (!h) return;
   if (h->run) runner_destroy(h->run);
-  if (!h->allocs.empty()) cudaStreamSynchronize(h->stream);
-  for (void *p : h->allocs) cudaFree(p);
-  if (!h->well_allocs.empty()) cudaStreamSynchronize(h->stream);
-  for (void *p : h->well_allocs) cudaFree(p);
+  if (!h->allocs.empty() || !h->well_allocs.empty()) cudaStreamSynchronize(h->stream);
+  dfree(h->allocs, h->stream);
+  dfree(h->well_allocs, h->stream);
   if (h->gm_V) cudaFree(h->gm_V);
   if (h->gm_part) cudaFree(h->gm_part);
   if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
@@ -1258,8 +1345,7 @@ opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, cons
   }
   // ---- drop the previous wells (no kernel of this handle is in flight after the sync)
   CK(cudaStreamSynchronize(h->stream));
-  for (void *p : h->well_allocs) cudaFree(p);
-  h->well_allocs.clear();
+  dfree(h->well_allocs, h->stream);
   Sys &S = h->sys;
   S.nwells = 0;
   S.w_ptr = S.w_cell = S.w_of = S.w_rptr = S.w_rperf = nullptr;
@@ -1300,12 +1386,12 @@ opm_status opm_set_wells(opm_handle h, int32_t nwells, const int32_t *wptr, cons
   UPW(d_rperf, rperf);
   UPW(d_mask, mask);
 #undef UPW
-  if ((s = dalloc(h->well_allocs, bytes, &d_B, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
-  if ((s = dalloc(h->well_allocs, bytes, &d_C, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
-  if ((s = dalloc(h->well_allocs, bytes, &d_D, 16 * (size_t)nwells)) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, h->stream, &d_B, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, h->stream, &d_C, 12 * (size_t)std::max(nperf, 1))) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, h->stream, &d_D, 16 * (size_t)nwells)) != OPM_OK) return s;
   double *d_t2, *d_corr;
-  if ((s = dalloc(h->well_allocs, bytes, &d_t2, 4 * (size_t)nwells)) != OPM_OK) return s;
-  if ((s = dalloc(h->well_allocs, bytes, &d_corr, 3 * (size_t)h->n)) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, h->stream, &d_t2, 4 * (size_t)nwells)) != OPM_OK) return s;
+  if ((s = dalloc(h->well_allocs, bytes, h->stream, &d_corr, 3 * (size_t)h->n)) != OPM_OK) return s;
   std::vector<int32_t> wrows;
   for (int32_t i = 0; i < h->n; ++i)
     if (rptr[i + 1] > rptr[i]) wrows.push_back(i);

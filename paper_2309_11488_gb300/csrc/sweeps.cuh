@@ -31,13 +31,16 @@ __device__ __forceinline__ void blk_sub_r(const TF (&b)[9], TF v0, TF v1, TF v2,
   a2 = fma(-b[6], v0, fma(-b[7], v1, fma(-b[8], v2, a2)));
 }
 
-// The same for a block in memory, entry-planar with stride c.
+// The same for a block in memory, entry-planar with stride c.  Factor
+// values and their column indices are read once per application: streaming
+// loads (evict-first in L1 and L2) leave the cache to the vectors that the
+// next kernels read again.
 template <typename TF>
 __device__ __forceinline__ void blk_sub(const TF *__restrict__ Bv, int c, TF v0, TF v1, TF v2, TF &a0, TF &a1,
                                         TF &a2) {
   TF b[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) b[e] = __ldg(Bv + e * c);
+  for (int e = 0; e < 9; ++e) b[e] = __ldcs(Bv + e * c);
   blk_sub_r<TF>(b, v0, v1, v2, a0, a1, a2);
 }
 
@@ -59,8 +62,8 @@ __device__ __forceinline__ void row_sub(const int32_t *__restrict__ col, const T
     const bool u0 = act && len > k, u1 = act && len > k + 1;
     const int q0 = __popc(m0 & lt), q1 = __popc(m1 & lt);
     int j0 = 0, j1 = 0;
-    if (u0) j0 = __ldg(col + b0 + q0);
-    if (u1) j1 = __ldg(col + b1 + q1);
+    if (u0) j0 = __ldcs(col + b0 + q0);
+    if (u1) j1 = __ldcs(col + b1 + q1);
     if (u0) {
       const Vec3<TV> v = load3cg(vec + 3ll * j0);
       blk_sub<TF>(vals + 9ll * b0 + q0, __popc(m0), (TF)v.c0, (TF)v.c1, (TF)v.c2, a0, a1, a2);
@@ -83,9 +86,9 @@ __device__ __forceinline__ int preload_slabs(const int32_t *__restrict__ col, co
     const unsigned m = __ballot_sync(0xffffffffu, len > k);
     if (act && len > k) {
       const int q = __popc(m & lt), cnt = __popc(m);
-      jp[k] = __ldg(col + base + q);
+      jp[k] = __ldcs(col + base + q);
 #pragma unroll
-      for (int e = 0; e < 9; ++e) bp[k][e] = __ldg(vals + 9ll * base + q + e * cnt);
+      for (int e = 0; e < 9; ++e) bp[k][e] = __ldcs(vals + 9ll * base + q + e * cnt);
     }
     base += __popc(m);
   }
@@ -114,7 +117,7 @@ __device__ __forceinline__ void preloaded_sub(int len, bool act, const TF (&bp)[
 template <typename TF>
 __device__ __forceinline__ void load_dinv(const TF *D, TF (&d)[9]) {
 #pragma unroll
-  for (int e = 0; e < 9; ++e) d[e] = __ldg(D + 32 * e);
+  for (int e = 0; e < 9; ++e) d[e] = __ldcs(D + 32 * e);
 }
 
 template <typename TF>

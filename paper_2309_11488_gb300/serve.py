@@ -169,10 +169,12 @@ class ServingEngine:
         del self.lanes[ln.lid]
         self.hbm_bytes -= ln.device_bytes
 
-    def add_lane(self, c, evict=True, wanted=()):
+    def add_lane(self, c, evict=True, wanted=(), first_vals=None):
         """A new lane of class c if it fits in the budget (evicting idle
         lanes of other classes when allowed), else None.  Its instances come
-        from the kept analyses, factorised once with the base values."""
+        from the kept analyses, factorised once with the values of
+        first_vals (pattern -> device values, e.g. a waiting request's) or
+        the pattern's base values."""
         if len(self.by_class[c]) >= self.lanes_per_class or self.lane_bytes(c) > self.budget:
             return None
         while self.hbm_bytes + self.lane_bytes(c) > self.budget:
@@ -182,9 +184,12 @@ class ServingEngine:
         stream = self.torch.cuda.Stream()
         solvers, xs, nbytes = [], [], 0
         for p in self.classes[c]:
-            base = self.torch.from_numpy(np.ascontiguousarray(self.patterns[p].vals)).cuda()
-            sv = opm.Solver.from_analysis(self.analyses[p], base, precision=self.precision, stream=stream)
-            del base
+            if first_vals and p in first_vals:
+                v = first_vals[p]  # already on the device: no upload
+            else:
+                v = self.torch.from_numpy(np.ascontiguousarray(self.patterns[p].vals)).cuda()
+            sv = opm.Solver.from_analysis(self.analyses[p], v, precision=self.precision, stream=stream)
+            del v
             solvers.append(sv)
             xs.append(self.torch.empty(3 * self.patterns[p].nb, dtype=self.torch.float64, device="cuda"))
             b = int(sv.info().device_bytes) + 24 * self.patterns[p].nb
@@ -275,7 +280,8 @@ class ServingEngine:
                         stats.launches += k > 0
                         stats.batched_requests += k
                 while waiting[c] > 0 and len(self.by_class[c]) < self.lanes_per_class:
-                    ln = self.add_lane(c, wanted={k for k, n in waiting.items() if n > 0})
+                    first = {p: queues[p][0].vals for p in self.classes[c] if queues[p]}
+                    ln = self.add_lane(c, wanted={k for k, n in waiting.items() if n > 0}, first_vals=first)
                     if ln is None:
                         break
                     self.lanes_created += 1
