@@ -374,7 +374,8 @@ def run_ours(args, rank, world, dist):
                   "p90_ms": round(float(np.percentile(per, 90)), 4), "min_ms": round(float(per.min()), 4),
                   "max_ms": round(float(per.max()), 4), "steps": int(args.steps)}
         launches = sv.timing().launches
-        err = float(np.linalg.norm(x.cpu().numpy() - s.x_true) / np.linalg.norm(s.x_true))
+        x_host = x.cpu().numpy()
+        err = float(np.linalg.norm(x_host - s.x_true) / np.linalg.norm(s.x_true))
         # per-kernel device time from a second handle that records events
         # around every kernel group (a host-driven loop, so not the timed one)
         with opm.Solver(s.nb, rp, ci, vals, precision=precision, profile_kernels=True, **kw) as sp:
@@ -385,7 +386,7 @@ def run_ours(args, rank, world, dist):
                 step_profiled(sp)
             t = sp.timing()
         return sv, dict(ms=ms, timing=t, launches=launches, info=info, clocks=clk.summary(), err=err, options=kw,
-                        autotune=tune, spread=spread, **stat)
+                        autotune=tune, spread=spread, x=x_host, **stat)
 
     sv64, r64 = measure("fp64")
     sv32, r32 = measure("fp32")
@@ -578,7 +579,8 @@ def run_ours(args, rank, world, dist):
     if not args.no_serving:
         out["serving"] = measure_serving(args, barrier, max_over_ranks, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(s, n_solves=2)
+        sched = {v: k for k, v in opm.SCHEDULES.items()}[r64["info"].schedule]
+        out["cpu_baseline"] = cpu_baseline(s, n_solves=2, schedule=sched, xs={"fp64": r64["x"], "fp32": r32["x"]})
         if tight_x is not None:
             out["c3_rtol1e-6"]["cpu_baseline"] = cpu_baseline_tight(s, out["c3_rtol1e-6"]["schedule"], tight_x)
     return out
@@ -1069,13 +1071,13 @@ def measure_serving(args, barrier, max_over_ranks, world):
     return summ
 
 
-def cpu_oracle_setup(s):
+def cpu_oracle_setup(s, schedule="colour_kempe"):
     """The oracle's inputs for the workload: b = A x_true and the schedule's
-    permutation (the smallest-last colouring reduced by Kempe exchanges, as
-    in the library's default)."""
+    permutation (by default the smallest-last colouring reduced by Kempe
+    exchanges, the library's default)."""
     import oracle as O
     b = O.spmv(s.nb, s.rowptr, s.colidx, s.vals, s.x_true)
-    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, "colour_kempe")
+    perm, _ = O.schedule_perm(s.nb, s.rowptr, s.colidx, schedule)
     pb = b.reshape(-1, 3)[perm].ravel()
     return O, perm, pb
 
@@ -1088,16 +1090,26 @@ def oracle_solve(O, s, perm, pb):
     return O.bicgstab(s.nb, prow, pcol, pval, fac, pb, RTOL, 200)
 
 
-def cpu_baseline(s, n_solves=2):
-    O, perm, pb = cpu_oracle_setup(s)
+def cpu_baseline(s, n_solves=2, schedule="colour_kempe", xs=None):
+    """The oracle's rate on one host core; with xs (the GPU solutions of the
+    headline step, FP64 and FP32 factors), their distance from the oracle's
+    x in the same row order."""
+    O, perm, pb = cpu_oracle_setup(s, schedule)
     t0 = time.perf_counter()
     for _ in range(n_solves):
         res = oracle_solve(O, s, perm, pb)
     dt = time.perf_counter() - t0
-    return {"value": round(n_solves / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_solves} full steps (value permutation, ILU0, BiCGStab to rtol 1e-3 in {res.iters} "
-                      f"iterations, true residual) of the same system in the library's default order, "
-                      f"single-threaded C, {os.cpu_count()} host cores present"}
+    out = {"value": round(n_solves / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n_solves} full steps (value permutation, ILU0, BiCGStab to rtol 1e-3 in {res.iters} "
+                     f"iterations, true residual) of the same system in the library's order ({schedule}), "
+                     f"single-threaded C, {os.cpu_count()} host cores present", "iters": res.iters}
+    if xs:
+        x = np.empty(3 * s.nb)
+        x.reshape(-1, 3)[perm] = res.x.reshape(-1, 3)
+        nx = np.linalg.norm(x)
+        for k, v in xs.items():
+            out[f"x_err_{k}_vs_oracle"] = float(np.linalg.norm(v - x) / nx)
+    return out
 
 
 def _oracle_worker(conn, kind, jobs, nsys, rtol, repeats):

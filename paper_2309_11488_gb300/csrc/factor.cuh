@@ -66,7 +66,10 @@ __device__ __forceinline__ void copy_row_to_factors(const Sys &S, int sl, bool a
 // expressions, in the same order, as the general path below, so both paths
 // give the same bits.  Loads of a block (its indices, the caller's values,
 // the pivot's inverse and U_ki) do not wait for the previous block's stores.
-template <typename TF>
+// With DREG false the diagonal stays in its factor slot (read-modify-write
+// per update, as the two-step path does) instead of registers: fewer
+// registers, the same expressions.
+template <typename TF, bool DREG>
 __device__ __forceinline__ void one_pass_rows(const Sys &S, int sl, bool fz, const double *__restrict__ vals_user,
                                               TF *lu, TF (&D)[9]) {
   const int lane = threadIdx.x & 31;
@@ -100,9 +103,15 @@ __device__ __forceinline__ void one_pass_rows(const Sys &S, int sl, bool fz, con
       }
       const int64_t doff = dst >> 6;
       const int dstr = (int)(dst & 63);
+      TF *Dp = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
       if (k == 0) {
+        if (DREG) {
 #pragma unroll
-        for (int c = 0; c < 9; ++c) D[c] = (TF)e[c];
+          for (int c = 0; c < 9; ++c) D[c] = (TF)e[c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) Dp[32 * c] = (TF)e[c];
+        }
       } else if (col < i && dst >= 0) {
         const TF *Dk = lu + S.d_off + (int64_t)kSliceVals * (col >> 5) + (col & 31);
         TF d[9], l[9];
@@ -126,9 +135,10 @@ __device__ __forceinline__ void one_pass_rows(const Sys &S, int sl, bool fz, con
 #pragma unroll
           for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-              D[3 * r + c] = fma(-l[3 * r], uu[c], fma(-l[3 * r + 1], uu[3 + c], fma(-l[3 * r + 2], uu[6 + c],
-                                                                                    D[3 * r + c])));
+            for (int c = 0; c < 3; ++c) {
+              TF &dv = DREG ? D[3 * r + c] : Dp[32 * (3 * r + c)];
+              dv = fma(-l[3 * r], uu[c], fma(-l[3 * r + 1], uu[3 + c], fma(-l[3 * r + 2], uu[6 + c], dv)));
+            }
         }
       } else if (dst >= 0) {
 #pragma unroll
@@ -153,7 +163,7 @@ __device__ __forceinline__ void one_pass_rows(const Sys &S, int sl, bool fz, con
 // copy reads only the caller's values and writes only the phase's own rows,
 // so it overlaps the tail of the previous phase; the elimination, which
 // reads earlier phases' pivots, comes after the wait.
-template <typename TF, bool ONE_PASS, bool EARLY_COPY = false>
+template <typename TF, bool ONE_PASS, bool EARLY_COPY = false, bool DREG = true>
 __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1) {
   if (S.skip) return;  // warp-uniform: the entry belongs to one system
   const int lane = threadIdx.x & 31;
@@ -168,7 +178,7 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
   const unsigned lt = lanemask_lt();
   DevState *st = S.st;
   TF D[9];
-  if (ONE_PASS && __any_sync(0xffffffffu, fz)) one_pass_rows<TF>(S, sl, fz, vals_user, lu, D);
+  if (ONE_PASS && __any_sync(0xffffffffu, fz)) one_pass_rows<TF, DREG>(S, sl, fz, vals_user, lu, D);
   if (__any_sync(0xffffffffu, gen)) {
     copy_row_to_factors<TF>(S, sl, gen, vals_user, lu);
     if (EARLY_COPY) pdl_wait();
@@ -226,7 +236,7 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
     TF *Dp = lu + S.d_off + (int64_t)kSliceVals * sl + lane;
     TF a[9], o[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) a[c] = fz ? D[c] : Dp[32 * c];
+    for (int c = 0; c < 9; ++c) a[c] = (fz && DREG) ? D[c] : Dp[32 * c];
     if (!inv3<TF>(a, o)) {
       atomicCAS(&st->error, 0, (int32_t)OPM_ERR_ZERO_PIVOT);
       atomicMin(&st->err_row, i);
@@ -237,17 +247,19 @@ __device__ __forceinline__ void factor_rows(const Sys &S, int sl, int r0, int r1
 }
 
 // One launch per phase, one 32-row slice per warp.  ONE_PASS takes the
-// one-pass walk for the rows that allow it; MINB is the launch's resident
-// CTAs per SM.  Measured at the 949,871-cell workload (event-timed
-// refactorisations, A/B in one process): FP32 factors 0.509 -> 0.460 ms
-// with the one-pass walk at four CTAs per SM.  FP64 factors are bound by
-// the FP64 pipe in the large phases (54 FMAs per L block), where the
-// one-pass walk's registers cost more occupancy than its shorter load
-// chains gain (0.685 -> 0.696 ms at three CTAs per SM), and in the small
-// phases its 104 registers made them slower too (0.668 -> 0.694 ms): FP64
-// factors keep the two-step path, which copies before the dependency wait
-// (0.705 -> 0.694 ms).
-template <typename TF, bool ONE_PASS, int MINB>
+// one-pass walk for the rows that allow it, DREG keeps its diagonal in
+// registers; MINB is the launch's resident CTAs per SM.  Measured at the
+// 949,871-cell workload (event-timed refactorisations, A/B in one process):
+// FP32 factors 0.509 -> 0.460 ms with the one-pass walk (diagonal in
+// registers) at four CTAs per SM.  FP64 factors are bound by the FP64 pipe
+// in the large phases (54 FMAs per L block): with the diagonal in registers
+// (104 registers) the walk lost more occupancy than its shorter load chains
+// gained (0.685 -> 0.696 ms at three CTAs per SM); with the diagonal in its
+// slot (64 registers, four CTAs per SM) it gains 0.668 -> 0.655 ms over the
+// two-step path.  The small phases, latency chains, keep the two-step path
+// for FP64 (the walk's registers made them slower: 0.668 -> 0.694 ms); the
+// two-step path copies before the dependency wait (0.705 -> 0.694 ms).
+template <typename TF, bool ONE_PASS, int MINB, bool DREG = true>
 __global__ void __launch_bounds__(256, MINB) k_factor_phase(Batch B, int c) {
   // the two-step path waits after its copy (EARLY_COPY); the one-pass walk
   // needs earlier phases from its first L block on
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(256, MINB) k_factor_phase(Batch B, int c) {
   const int e = __ldg(B.fwd_ptr + c) + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e >= __ldg(B.fwd_ptr + c + 1)) return;
   const int4 E = B.ent[e];
-  factor_rows<TF, ONE_PASS, !ONE_PASS>(B.sys[E.x], E.y, E.z, E.w);
+  factor_rows<TF, ONE_PASS, !ONE_PASS, DREG>(B.sys[E.x], E.y, E.z, E.w);
 }
 
 template <typename TF>

@@ -322,7 +322,7 @@ int launch_factor_t(Runner &R, cudaStream_t st) {
     const int cnt = R.fwd_ptr[c + 1] - R.fwd_ptr[c];
     if (cnt == 0) continue;
     if (cnt <= R.small_entries) launch_pdl(k_factor_phase<TF, kFp32, 1>, (cnt + 1) / 2, 64, st, R.B, c);
-    else launch_pdl(k_factor_phase<TF, kFp32, 4>, blocks8(cnt), 256, st, R.B, c);
+    else launch_pdl(k_factor_phase<TF, true, 4, kFp32>, blocks8(cnt), 256, st, R.B, c);
     ++n;
   }
   return n;
