@@ -231,3 +231,38 @@ def test_batch_members_can_sit_a_launch_out(precision):
         np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
     for h in handles:
         h.close()
+
+
+def test_handles_made_and_freed_while_another_solves():
+    """Device memory comes from a stream-ordered pool: handles made and
+    destroyed on other streams while a solve runs (the serving loop's
+    eviction) leave that solve's result bitwise unchanged, and a handle made
+    in memory another one freed solves like a fresh one."""
+    s = synth.config2()
+    b = dev(rhs(s))
+    with make(s, "fp64") as ref:
+        x_ref, st, it, rr = ref.solve(b, rtol=1e-6)
+        x_ref = x_ref.cpu().numpy()
+    main_stream = torch.cuda.Stream()
+    side = torch.cuda.Stream()
+    small = synth.config1()
+    an = opm.Analysis(small.nb, small.rowptr, small.colidx, "auto")
+    with opm.Solver(s.nb, dev(s.rowptr), dev(s.colidx), dev(s.vals), schedule="colour", stream=main_stream) as sv:
+        x = torch.empty_like(b)
+        vals = dev(s.vals)
+        for rep in range(3):
+            sv.launch(vals, b, x, rtol=1e-6, maxit=200)
+            for _ in range(4):  # churn on another stream while the solve runs
+                h = opm.Solver.from_analysis(an, dev(small.vals), precision="fp32", stream=side)
+                h.close()
+            st2, it2, rr2 = sv.wait()
+            assert (st2, it2) == (st, it)
+            np.testing.assert_array_equal(x.cpu().numpy(), x_ref)
+    bs = dev(O.spmv(small.nb, small.rowptr, small.colidx, small.vals, small.x_true))
+    with opm.Solver.from_analysis(an, dev(small.vals), precision="fp64", stream=side) as h, \
+            make(small, "fp64", schedule="colour_kempe") as fresh:
+        xa, sta, ita, rra = h.solve(bs, rtol=1e-8)
+        xb, stb, itb, rrb = fresh.solve(bs, rtol=1e-8)
+        assert (sta, ita, rra) == (stb, itb, rrb)
+        np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    an.close()
