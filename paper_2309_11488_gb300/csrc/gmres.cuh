@@ -98,6 +98,58 @@ __global__ void __launch_bounds__(256) k_gm_reduce_s(const double *part, int nti
   }
 }
 
+// A Gram-Schmidt correction fused with what follows it, over the tiles of
+// k_gm_dots_s: w -= sum_{q <= j} coef[q] V_q, then (NEXT_DOTS) the partial
+// projections V_q . w of the corrected w for q <= j, or (!NEXT_DOTS) the
+// partial ||w||^2.  Each entry's correction is the same expression as in
+// k_gm_combine_s and each partial the same as in k_gm_dots_s, so the results
+// are those of the separate kernels, with one pass over V and w fewer.
+template <bool NEXT_DOTS>
+__global__ void __launch_bounds__(256) k_gm_correct_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
+                                                      const double *coef, double *w, double *part) {
+  __shared__ double c[kGmMaxVec];
+  __shared__ double sm[kGmMaxVec][8];
+  const int nv = gs->j + 1;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) c[q] = coef[q];
+  __syncthreads();
+  const int64_t e0 = (int64_t)blockIdx.x * 3 * kSpmvRows + 3 * threadIdx.x;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool in = e0 + 2 < n3;
+  double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+  if (in) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int q = 0; q < nv; ++q) {
+      const double *v = V + q * stride + e0;
+      a0 = fma(c[q], __ldcg(v), a0);
+      a1 = fma(c[q], __ldcg(v + 1), a1);
+      a2 = fma(c[q], __ldcg(v + 2), a2);
+    }
+    w0 = w[e0] - a0;
+    w1 = w[e0 + 1] - a1;
+    w2 = w[e0 + 2] - a2;
+    w[e0] = w0;
+    w[e0 + 1] = w1;
+    w[e0 + 2] = w2;
+  }
+  const int nd = NEXT_DOTS ? nv : 1;
+  for (int q = 0; q < nd; ++q) {
+    double d[1] = {0.0};
+    if (in) {
+      const double *v = NEXT_DOTS ? V + q * stride + e0 : nullptr;
+      d[0] = NEXT_DOTS ? fma(__ldcg(v + 2), w2, fma(__ldcg(v + 1), w1, __ldcg(v) * w0))
+                       : fma(w2, w2, fma(w1, w1, w0 * w0));
+    }
+    warp_sum<1>(d);
+    if (lane == 0) sm[q][wp] = d[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < nd) {
+    double acc = 0.0;
+    for (int k = 0; k < 8; ++k) acc += sm[threadIdx.x][k];
+    part[(int64_t)blockIdx.x * kGmMaxVec + threadIdx.x] = acc;
+  }
+}
+
 // mode 0: w -= sum_{q <= j} coef[q] V_q (a Gram-Schmidt pass); mode 1:
 // w = sum_{q < j} y[q] V_q (the cycle's correction, only when it updates x).
 __global__ void __launch_bounds__(256) k_gm_combine_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,

@@ -1218,10 +1218,12 @@ opm_status gm_build(opm_solver *h) {
       launch_apply<kModePlain>(R, cap);                                    // t = inv(M) v_j
       op(4, S.t, S.v);                                                     // v = A t
       dots(V, 0, S.v, gs->h1);
-      k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->h1, S.v, 0);
-      dots(V, 0, S.v, gs->h2);
-      k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, 0);
-      dots(S.v, 1, S.v, &gs->nrm2);
+      // first correction with the second pass's projections, second
+      // correction with the norm: one pass over V and w fewer each
+      k_gm_correct_s<true><<<ntile, 256, 0, cap>>>(n3, V, n3, gs, gs->h1, S.v, part);
+      k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile, gs, 0, gs->h2);
+      k_gm_correct_s<false><<<ntile, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, part);
+      k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile, gs, 1, &gs->nrm2);
       k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.v, gs, 0, V, n3);
       s = capture_handle(cap, &ch_end);
       if (s == OPM_OK) {
