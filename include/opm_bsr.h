@@ -548,8 +548,8 @@ opm_status opm_autotune_batch(int32_t nsys, const int32_t *nb, const int32_t *co
  * Its scratch is a fixed 131,328-byte array in device memory that every GPU
  * using the library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with the
- * device current) and keeps it; make that first call before any stream
- * capture.  Calls after a cudaDeviceReset of that device are not supported.
+ * device current) and keeps it.  Calls after a cudaDeviceReset of that
+ * device are not supported.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.
  */
