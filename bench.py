@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the C1 / C2 (L2-resident) leg")
     p.add_argument("--no-tight", action="store_true", help="skip the rtol 1e-6 leg")
+    p.add_argument("--no-product-reuse", action="store_true",
+                   help="FP64 products walk all of A (opm_options.product_reuse = -1)")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--patterns", type=int, default=32)
@@ -149,15 +151,45 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def product_terms(info):
+    """What a BiCGStab product after an application reads beyond a plain
+    matrix pass (opm_options.product_reuse, reported by opm_get_info):
+    (blocks of A it walks, rows that add one 3-vector -- p_i where the row
+    has no block left of its diagonal, the backward sweep's upper sum where
+    the row reuses it -- rows whose upper sum the backward sweep stores).
+    Without the reuse: (nnzb, 0, 0)."""
+    nprod = getattr(info, "nnzb_product", info.nnzb)
+    if nprod >= info.nnzb:
+        return info.nnzb, 0, 0
+    return nprod, info.rows_identity + info.rows_reuse, info.rows_reuse
+
+
+def product_bytes(info) -> int:
+    """One product's matrix bytes: 76 per walked block (9 values, a column
+    index), A's row pointers; with the reuse also the per-row walk length
+    (4), the per-slice row classes (8) and the added 3-vectors (24 each)."""
+    n = info.nb
+    nprod, extra, _ = product_terms(info)
+    nbytes = 76 * nprod + 4 * (n + 1)
+    if nprod < info.nnzb:
+        nbytes += 4 * n + 8 * ((n + 31) // 32) + 24 * extra
+    return nbytes
+
+
 def algorithmic_apply_bytes(info, fp32: bool) -> int:
     """Bytes one preconditioner application must move at least: every factor
     block once (L, U and the inverted diagonal, 9 values each), L's and U's
     column indices and row pointers, and the vectors: r, p, v read, p and z
-    written, the intermediate y written and read back."""
+    written, the intermediate y written and read back; with the product
+    reuse, the row classes (8 per slice) and the stored upper sums (24 per
+    reusing row)."""
     n, nnzb = info.nb, info.nnzb
     val = 4 if fp32 else 8
     factors = 9 * val * nnzb + 4 * (nnzb - n) + 2 * 4 * (n + 1)
     vectors = 5 * 24 * n + 2 * 3 * val * n
+    nprod, _, stored = product_terms(info)
+    if nprod < nnzb:
+        vectors += 8 * ((n + 31) // 32) + 24 * stored
     return factors + vectors
 
 
@@ -187,15 +219,19 @@ FP64_FMA_PEAK = 2 * 152 * 2.07e9
 
 def iteration_work(info, fp32: bool):
     """Algorithmic work of one BiCGStab + ILU0 iteration: HBM bytes (two
-    matrix passes, two factor passes, 27 fused vector passes of 24 n bytes)
-    and FP64 FMAs (two SpMVs of 9 per block; two preconditioner
+    products, two factor passes, 27 fused vector passes of 24 n bytes) and
+    FP64 FMAs (two products of 9 per walked block; two preconditioner
     applications of 9 per factor block when the factors are FP64; the dot
-    products, right-hand sides and vector updates: 36 per block row)."""
+    products, right-hand sides and vector updates: 36 per block row).  A
+    product walks all of A, or with the reuse only the blocks of
+    product_terms (product_bytes)."""
     n, nnzb = info.nb, info.nnzb
-    matrix = 76 * nnzb + 4 * n
+    nprod, _, stored = product_terms(info)
     factor = (40 if fp32 else 76) * nnzb + 4 * n
-    nbytes = 2 * matrix + 2 * factor + 27 * 24 * n
-    fma = 18 * nnzb + (0 if fp32 else 18 * nnzb) + 36 * n
+    if nprod < nnzb:
+        factor += 8 * ((n + 31) // 32) + 24 * stored
+    nbytes = 2 * (product_bytes(info) - 4) + 2 * factor + 27 * 24 * n
+    fma = 18 * nprod + (0 if fp32 else 18 * nnzb) + 36 * n
     return nbytes, fma
 
 
@@ -225,8 +261,9 @@ def kernel_work(info, fp32: bool):
     groups.  A matrix pass is 76 bytes per block (9 values and a column
     index) plus the row pointers; vectors are 24 bytes per row.
       spmv (v = A p^ with (r^, v); t = A s^ with (t, s), (t, t), (s, s)):
-        a matrix pass, 3 vector passes; 9 FMAs per block, 3 or 9 per row
-        (the average of the two kinds is reported);
+        a product (product_bytes: all of A, or with the reuse the walked
+        blocks and the added 3-vectors), 3 vector passes; 9 FMAs per walked
+        block, 3 or 9 per row (the average of the two kinds is reported);
       update (x += alpha p^ + omega s^, r = s - omega t, ||r||, (r^, r)):
         6 vectors read, 2 written; 15 FMAs per row;
       finish (true residual and x back to the caller's order): a matrix
@@ -238,7 +275,7 @@ def kernel_work(info, fp32: bool):
     mat = 76 * nnzb + 4 * (n + 1)
     return {"factor": factor_work(info, fp32),
             "apply": (algorithmic_apply_bytes(info, fp32), 0 if fp32 else int(9 * nnzb + 4.5 * n)),
-            "spmv": (mat + 72 * n, 9 * nnzb + 6 * n),
+            "spmv": (product_bytes(info) + 72 * n, 9 * product_terms(info)[0] + 6 * n),
             "update": (192 * n, 15 * n),
             "setup": (148 * n, 3 * n),
             "finish": (mat + 76 * n, 9 * nnzb + 3 * n)}
@@ -339,6 +376,8 @@ def run_ours(args, rank, world, dist):
 
     def measure(precision):
         kw, tune = tuned(precision)
+        if args.no_product_reuse:
+            kw = dict(kw, product_reuse=-1)
         sv = opm.Solver(s.nb, rp, ci, vals, precision=precision, **kw)
         b = sv.spmv(xt)  # b = A x_true on the GPU
         x = torch.empty_like(b)

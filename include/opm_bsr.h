@@ -152,7 +152,24 @@ typedef struct opm_options {
                             preconditioner application (BiCGStab, GMRES,
                             opm_ilu_apply).  For a batch both counts are the
                             batch's own options                               */
-  int32_t reserved[2];
+  int32_t product_reuse; /* 0 = default: with FP64 factors and exact
+                            triangular solves (tri_sweeps = 0), the two
+                            BiCGStab products that follow a preconditioner
+                            application, v = A p^ with p^ = inv(LU) p, use
+                            that ILU0 makes (LU)_ij = A_ij on the pattern: a
+                            row with no block left of its diagonal (all of
+                            its blocks in the preconditioner) takes
+                            (A p^)_i = p_i, and a row whose upper blocks no
+                            elimination product changed takes
+                            sum_{j>i} A_ij p^_j from the backward sweep's
+                            sum_{j>i} U_ij p^_j, walking only its diagonal
+                            and lower blocks.  Equal to the plain product in
+                            exact arithmetic (Eisenstat's observation for
+                            such preconditioners, SIAM J. Sci. Stat. Comput.
+                            2, 1981).  -1 = off: every product walks all of
+                            A.  FP32 factors never use it (their U is not
+                            A's to FP64 accuracy)                            */
+  int32_t reserved;
 } opm_options;
 
 /* Largest nb a handle or an analysis accepts: row counts rounded up to
@@ -219,12 +236,19 @@ typedef struct opm_analysis_info {
   int32_t schedule;    /* schedule used (never OPM_SCHED_AUTO)               */
   int32_t nsets;       /* levels or colours (1 for natural order)            */
   int32_t nphases;     /* runs of mutually independent rows the sweeps walk  */
-  int32_t reserved;
+  int32_t rows_identity; /* rows with no block left of the diagonal and all
+                          blocks kept: a product after an application takes
+                          (A p^)_i = p_i there (opm_options.product_reuse)   */
   int64_t nnzb_kept;   /* blocks in the preconditioner's pattern             */
   int64_t nnzb_lower;  /* strictly lower kept blocks of the permuted matrix  */
   int64_t nnzb_upper;
   int64_t nupdates;    /* ILU0 update products A_ij -= L_ik U_kj per
                           factorisation (Algorithm 2's inner loop)           */
+  int64_t nnzb_product; /* blocks of A a product after an application walks
+                          with product_reuse (nnzb without it)             */
+  int32_t rows_reuse;  /* rows that take their upper sum from the backward
+                          sweep with product_reuse                         */
+  int32_t reserved2;
 } opm_analysis_info;
 opm_status opm_bsr_analyse(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const int32_t *part,
                            int32_t schedule, int32_t *perm, opm_analysis_info *info);
@@ -364,9 +388,15 @@ typedef struct opm_info {
   int32_t nphases;     /* runs of mutually independent rows the sweeps walk
                           (the levels or colours; for natural order, runs of
                           consecutive independent rows)                      */
-  int32_t reserved;
+  int32_t rows_identity; /* as in opm_analysis_info                          */
   int64_t nupdates;    /* ILU0 update products A_ij -= L_ik U_kj per
                           factorisation (Algorithm 2's inner loop)          */
+  int64_t nnzb_product; /* blocks of A each BiCGStab product after an
+                          application walks in this handle's own solves
+                          (nnzb when product_reuse does not apply)         */
+  int32_t rows_reuse;  /* as in opm_analysis_info (0 when product_reuse
+                          does not apply)                                  */
+  int32_t reserved2;
 } opm_info;
 
 opm_status opm_get_info(opm_handle h, opm_info *info);

@@ -49,6 +49,15 @@ struct Sys {
   const uint2 *sl_mask;  // per slice: (rows without U blocks, rows whose y is read later)
   const uint32_t *fz_mask;  // per slice: rows the factorisation walks in one pass
   const int64_t *a_aux;     // per A block: slot of U_ki for a one-pass row's L block (i,k), else -1
+  // products after an application (Analysis::sp_mask, sp_len): per slice
+  // (rows with (A p^)_i = p_i, rows taking their upper sum from the
+  // backward sweep); per row the leading blocks of A the product walks
+  const uint2 *sp_mask;
+  const int32_t *sp_len;
+  // per row: sum_{j>i} U_ij z_j of the last BiCGStab application, stored by
+  // the backward sweep for the rows of sp_mask.y.  NULL: the products walk
+  // all of A (FP32 factors, Jacobi triangular sweeps, or turned off)
+  double *uz;
   // standard wells applied separately (nwells = 0: none)
   int32_t nwells, pad1;
   const int32_t *w_ptr;     // [nwells+1] perforations of each well
@@ -438,6 +447,76 @@ __device__ __forceinline__ void row_operator(const Sys &S, const double *__restr
   row_spmv(S.a_rp, S.a_col, S.a_val, x, i, S.n, y0, y1, y2);
 }
 
+// y += the first lead blocks of lane's row i of A's warp-sliced layout
+// (FP64).  The slab layout is walked with every row's full length; lanes
+// issue loads only for their first lead blocks, and the walk stops after
+// the longest lead of the warp.  All lanes of the warp must call it.
+__device__ __forceinline__ void row_spmv_lead(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                              const double *__restrict__ val, const double *__restrict__ x,
+                                              int i, int n, int lead, double &y0, double &y1, double &y2) {
+  const int maxlead = __reduce_max_sync(0xffffffffu, lead);
+  if (maxlead == 0) return;  // warp-uniform: no lane walks a block
+  const int lane = threadIdx.x & 31;
+  const int s0 = i - lane;
+  const int len = (i < n) ? rp[i + 1] - rp[i] : 0;
+  int base = (s0 < n) ? rp[s0] : 0;
+  const unsigned lt = lanemask_lt();
+  for (int k = 0; k < maxlead; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, len > k);
+    if (lead > k) {
+      const int cnt = __popc(m);
+      const int q = __popc(m & lt);
+      const int j = __ldcs(col + base + q);
+      const double *a = val + 9ll * base + q;
+      const double x0 = __ldg(x + 3ll * j), x1 = __ldg(x + 3ll * j + 1), x2 = __ldg(x + 3ll * j + 2);
+      const double a0 = __ldcs(a), a1 = __ldcs(a + cnt), a2 = __ldcs(a + 2 * cnt);
+      const double a3 = __ldcs(a + 3 * cnt), a4 = __ldcs(a + 4 * cnt), a5 = __ldcs(a + 5 * cnt);
+      const double a6 = __ldcs(a + 6 * cnt), a7 = __ldcs(a + 7 * cnt), a8 = __ldcs(a + 8 * cnt);
+      y0 = fma(a0, x0, fma(a1, x1, fma(a2, x2, y0)));
+      y1 = fma(a3, x0, fma(a4, x1, fma(a5, x2, y1)));
+      y2 = fma(a6, x0, fma(a7, x1, fma(a8, x2, y2)));
+    }
+    base += __popc(m);
+  }
+}
+
+// The operator's row right after a BiCGStab application xh = inv(LU) xin
+// (REUSE; without it, row_operator).  ILU0 gives (LU)_ij = A_ij on the
+// pattern.  A row with no block left of its diagonal and all blocks in the
+// preconditioner has an empty L row and U's row equal to A's, so
+// (A xh)_i = (U xh)_i = (L U xh)_i = xin_i: no product at all.  A row whose
+// upper blocks all equal U's (sp_mask.y) starts from the backward sweep's
+// sum_{j>i} U_ij xh_j (uz) and adds its diagonal and lower blocks.  Equal
+// to row_operator in exact arithmetic; the wells' term is applied as there.
+template <bool REUSE>
+__device__ __forceinline__ void row_operator_applied(const Sys &S, const double *__restrict__ xh,
+                                                     const double *__restrict__ xin, int i, double &y0,
+                                                     double &y1, double &y2) {
+  if (!REUSE) {
+    row_operator(S, xh, i, y0, y1, y2);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int n = S.n;
+  int lead = 0;
+  if (i < n) {
+    if (S.nwells > 0 && ((__ldg(S.w_mask + (i >> 5)) >> lane) & 1u)) {
+      y0 = -__ldcg(S.w_corr + 3ll * i);
+      y1 = -__ldcg(S.w_corr + 3ll * i + 1);
+      y2 = -__ldcg(S.w_corr + 3ll * i + 2);
+    }
+    const uint2 M = __ldg(S.sp_mask + (i >> 5));
+    lead = __ldg(S.sp_len + i);
+    const double *e = ((M.x >> lane) & 1u) ? xin + 3ll * i : ((M.y >> lane) & 1u) ? S.uz + 3ll * i : nullptr;
+    if (e) {
+      y0 += __ldcg(e);
+      y1 += __ldcg(e + 1);
+      y2 += __ldcg(e + 2);
+    }
+  }
+  row_spmv_lead(S.a_rp, S.a_col, S.a_val, xh, i, n, lead, y0, y1, y2);
+}
+
 // ------------------------------------------------------------ tile kernels
 //
 // One CTA per (system, tile).  Streaming kernels use tiles of kTileRows =
@@ -530,7 +609,9 @@ __global__ void k_start(Batch B) {
   if (s < B.nsys && !B.sys[s].skip) setup_scalars(B.sys[s], B.sys[s].st, B.sys[s].st->bb);
 }
 
-// v = A p^ and (r^, v); alpha = rho / (r^, v).
+// v = A p^ and (r^, v); alpha = rho / (r^, v).  REUSE: the product takes
+// the application's sums where the factors allow (row_operator_applied).
+template <bool REUSE>
 __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
   __shared__ RedShared<1> rs_;
   red_begin<1>(rs_);
@@ -541,7 +622,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
   const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_operator(S, S.ph, i, y0, y1, y2);
+    row_operator_applied<REUSE>(S, S.ph, S.p, i, y0, y1, y2);
     if (i < S.n) {
       double *v = S.v + 3ll * i;
       v[0] = y0; v[1] = y1; v[2] = y2;
@@ -562,8 +643,10 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
   }
 }
 
-// t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.
-__global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
+// t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.  REUSE as
+// for k_spmv_v.
+template <bool REUSE>
+__global__ void __launch_bounds__(256, REUSE ? 6 : 8) k_spmv_t(Batch B) {
 
   pdl_enter();
   OPM_TILE_S(B, S, lt);
@@ -572,7 +655,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
   const int i = lt * kSpmvRows + threadIdx.x;
   {
     double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-    row_operator(S, S.sh, i, y0, y1, y2);
+    row_operator_applied<REUSE>(S, S.sh, S.s, i, y0, y1, y2);
     if (i < S.n) {
       double *t = S.t + 3ll * i;
       t[0] = y0; t[1] = y1; t[2] = y2;

@@ -72,6 +72,25 @@ struct Analysis {
   // so its backward step runs inside the forward sweep; (y) its forward
   // result y is read later (by its own backward step or another row's L).
   std::vector<uint32_t> sl_mask;              // 2 per slice: x, y
+  // The BiCGStab products that follow a preconditioner application,
+  // v = A p^ with p^ = inv(LU) p.  ILU0 makes (LU)_ij = A_ij on the
+  // pattern, so per 32-row slice, bit r for row 32*slice + r:
+  // (x) the row has no block left of its diagonal and every block in the
+  //     preconditioner: L's row is empty and U's row is A's, so
+  //     (A p^)_i = (U p^)_i = p_i;
+  // (y) otherwise, U's upper row is A's (every upper block kept, no ILU0
+  //     product landed on one): sum_{j>i} A_ij p^_j is the backward
+  //     sweep's sum_{j>i} U_ij p^_j, and the product walks only the
+  //     diagonal and the blocks left of it.
+  // sp_len[i]: the leading blocks of A's row (A's order: the diagonal, then
+  // columns ascending) the product walks: 0 (x), 1 + the lower blocks (y),
+  // all of them otherwise.
+  std::vector<uint32_t> sp_mask;              // 2 per slice: x, y
+  std::vector<int32_t> sp_len;
+  int64_t nnzb_product = 0;                   // sum of sp_len
+  int32_t rows_identity = 0;                  // rows with bit x
+  int32_t rows_reuse = 0;                     // rows with bit y
+  std::vector<int32_t> sp_tile;               // per 256-row SpMV tile: the blocks the products walk
   int64_t d_off = 0;                          // first value of Dinv inside the factor values
   int64_t lu_vals = 0;                        // total factor values
   int32_t max_row_len = 0;

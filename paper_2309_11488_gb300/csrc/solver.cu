@@ -82,6 +82,7 @@ struct Runner {
   cudaStream_t stream = nullptr;
   int device = 0;
   bool fp32 = false, cooperative = false, profile = false;
+  bool reuse = false;     // products after an application use Sys::uz (opm_options.product_reuse)
   int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
   int small_entries = 0;  // sweep phases with at most this many slices take the latency form
   int cp_sweeps = 0;      // > 0: iterative ILU0 with this many sweeps instead of the phases
@@ -418,7 +419,8 @@ int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
     launch_pdl(k_wells, R.nsys, 256, st, R.B, 0);
     ++n;
   }
-  launch_pdl(k_spmv_v, R.ntiles_s, 256, st, R.B);
+  if (R.reuse) launch_pdl(k_spmv_v<true>, R.ntiles_s, 256, st, R.B);
+  else launch_pdl(k_spmv_v<false>, R.ntiles_s, 256, st, R.B);
   mark(2);
   n += launch_apply<kModeS>(R, st);
   mark(3);
@@ -426,7 +428,8 @@ int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
     launch_pdl(k_wells, R.nsys, 256, st, R.B, 1);
     ++n;
   }
-  launch_pdl(k_spmv_t, R.ntiles_s, 256, st, R.B);
+  if (R.reuse) launch_pdl(k_spmv_t<true>, R.ntiles_s, 256, st, R.B);
+  else launch_pdl(k_spmv_t<false>, R.ntiles_s, 256, st, R.B);
   mark(4);
   launch_pdl(k_update, R.ntiles, 256, st, R.B);
   mark(5);
@@ -601,6 +604,14 @@ void runner_destroy(Runner *R) {
 }
 
 // Work lists and graphs for a set of analysed, allocated systems.
+// Whether the BiCGStab products after an application take their upper sums
+// from the backward sweep (Sys::uz): FP64 factors (an FP32 U is not A's to
+// FP64 accuracy) and exact triangular solves (a Jacobi-swept p^ does not
+// satisfy LU p^ = p), unless the options turn it off.
+bool product_reuse_applies(const opm_options &o, bool fp32) {
+  return !fp32 && o.tri_sweeps == 0 && o.product_reuse == 0;
+}
+
 uint64_t spin_ns(const opm_options &o) {
   return (uint64_t)(o.spin_limit_us > 0 ? o.spin_limit_us : 2000000) * 1000ull;
 }
@@ -636,6 +647,7 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
   R->small_entries = o.small_phase_slices > 0 ? o.small_phase_slices : o.small_phase_slices < 0 ? 0 : 10 * sms;
   R->cp_sweeps = o.cp_sweeps;
   R->tri_sweeps = o.tri_sweeps;
+  R->reuse = product_reuse_applies(o, R->fp32);
   // second buffers of the iterative sweeps, kept by the members
   for (auto *h : mem) {
     opm_status sa = OPM_OK;
@@ -699,9 +711,27 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     for (int sl = 0; sl < mem[s]->nslices; ++sl) all_ent.push_back(make_int4(s, sl, 0, mem[s]->n));
   R->nall = (int)all_ent.size();
   std::vector<int2> tiles, tiles_s;
+  std::vector<int32_t> work_s;
   for (int s = 0; s < R->nsys; ++s) {
     for (int t = 0; t < mem[s]->sys.ntiles; ++t) tiles.push_back(make_int2(s, t));
-    for (int t = 0; t < mem[s]->sys.ntiles_s; ++t) tiles_s.push_back(make_int2(s, t));
+    for (int t = 0; t < mem[s]->sys.ntiles_s; ++t) {
+      tiles_s.push_back(make_int2(s, t));
+      const auto &st = mem[s]->an.sp_tile;
+      work_s.push_back(t < (int)st.size() ? st[t] : 0);
+    }
+  }
+  // With the product reuse a tile's work ranges from no block (rows whose
+  // product is p_i) to whole rows: the 256-row tiles of the products go
+  // longest first, so the heavy ones start in the first wave and the light
+  // ones fill the last.  Only the launch order changes: the reductions sum
+  // per tile index, in a fixed order.
+  if (R->reuse) {
+    std::vector<int> ord(tiles_s.size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work_s[a] > work_s[b]; });
+    std::vector<int2> sorted(tiles_s.size());
+    for (size_t q = 0; q < ord.size(); ++q) sorted[q] = tiles_s[ord[q]];
+    tiles_s.swap(sorted);
   }
   R->ntiles = (int)tiles.size();
   R->ntiles_s = (int)tiles_s.size();
@@ -785,7 +815,10 @@ opm_status runner_sync_wells(Runner &R) {
 opm_status runner_push(Runner &R) {
   opm_status ws = runner_sync_wells(R);
   if (ws != OPM_OK) return ws;
-  for (int s = 0; s < R.nsys; ++s) R.h_sys[s] = R.mem[s]->sys;
+  for (int s = 0; s < R.nsys; ++s) {
+    R.h_sys[s] = R.mem[s]->sys;
+    if (!R.reuse) R.h_sys[s].uz = nullptr;
+  }
   CK(cudaMemcpyAsync((void *)R.B.sys, R.h_sys, sizeof(Sys) * R.nsys, cudaMemcpyHostToDevice, R.stream));
   return OPM_OK;
 }
@@ -959,12 +992,17 @@ opm_status alloc_system(opm_solver *h, const Analysis &an) {
   UP(p_upd, an.upd_ptr);
   UP(p_ud, an.upd_dst);
   UP(p_us, an.upd_src);
-  uint32_t *p_mask, *p_fz;
+  uint32_t *p_mask, *p_fz, *p_spm;
   int64_t *p_aux;
+  int32_t *p_spl;
   UP(p_mask, an.sl_mask);
   UP(p_fz, an.fz_mask);
   UP(p_aux, an.a_aux);
+  UP(p_spm, an.sp_mask);
+  UP(p_spl, an.sp_len);
 #undef UP
+  S.sp_mask = reinterpret_cast<const uint2 *>(p_spm);
+  S.sp_len = p_spl;
   S.fz_mask = p_fz;
   S.a_aux = p_aux;
   S.sl_mask = reinterpret_cast<const uint2 *>(p_mask);
@@ -997,6 +1035,9 @@ opm_status alloc_system(opm_solver *h, const Analysis &an) {
   double **vecs[] = {&S.x, &S.r, &S.rh, &S.p, &S.v, &S.ph, &S.s, &S.sh, &S.t, &S.w, &h->vec_in, &h->vec_out};
   for (double **pv : vecs)
     if ((s = dalloc(A, bytes, st, pv, 3 * (size_t)nb)) != OPM_OK) return s;
+  // the backward sweep's upper sums for the products (FP64 factors only)
+  S.uz = nullptr;
+  if (!h->fp32 && (s = dalloc(A, bytes, st, &S.uz, 3 * (size_t)nb)) != OPM_OK) return s;
   if ((s = dalloc(A, bytes, st, &S.partials, 4 * (size_t)S.ntiles_s)) != OPM_OK) return s;
   const size_t ngroups = ((size_t)S.ntiles_s + 31) / 32;
   if ((s = dalloc(A, bytes, st, &S.grp_partials, 4 * ngroups)) != OPM_OK) return s;
@@ -1023,6 +1064,8 @@ void drop_device_lists(Analysis &an) {
   std::vector<int64_t>().swap(an.upd_src);
   std::vector<int64_t>().swap(an.a_aux);
   std::vector<uint32_t>().swap(an.fz_mask);
+  std::vector<uint32_t>().swap(an.sp_mask);
+  std::vector<int32_t>().swap(an.sp_len);
 }
 
 // The host part of an analysis a handle keeps (everything but the lists
@@ -1047,6 +1090,10 @@ void copy_host_part(Analysis &dst, const Analysis &src) {
   dst.d_off = src.d_off;
   dst.lu_vals = src.lu_vals;
   dst.max_row_len = src.max_row_len;
+  dst.nnzb_product = src.nnzb_product;
+  dst.rows_identity = src.rows_identity;
+  dst.rows_reuse = src.rows_reuse;
+  dst.sp_tile = src.sp_tile;
 }
 
 opm_status check_options(const opm_options &o) {
@@ -1057,6 +1104,7 @@ opm_status check_options(const opm_options &o) {
   if (o.small_phase_slices < -1) return OPM_ERR_ARG;
   if (o.cp_sweeps < 0 || o.cp_sweeps > kMaxCpSweeps || o.tri_sweeps < 0 || o.tri_sweeps > kMaxTriSweeps)
     return OPM_ERR_ARG;
+  if (o.product_reuse != 0 && o.product_reuse != -1) return OPM_ERR_ARG;
   return OPM_OK;
 }
 
@@ -1513,6 +1561,9 @@ void analysis_info(const Analysis &an, int32_t *perm, opm_analysis_info *info) {
     info->nnzb_lower = an.nnz_l;
     info->nnzb_upper = an.nnz_u;
     info->nupdates = an.nupd;
+    info->rows_identity = an.rows_identity;
+    info->nnzb_product = an.nnzb_product;
+    info->rows_reuse = an.rows_reuse;
   }
 }
 
@@ -1780,8 +1831,12 @@ opm_status opm_get_info(opm_handle h, opm_info *info) {
   info->nnzb_upper = h->an.nnz_u;
   info->device_bytes = h->dev_bytes + (h->run ? h->run->dev_bytes : 0);
   info->nphases = h->n > 0 ? (int32_t)h->an.phase_ptr.size() - 1 : 0;
-  info->reserved = 0;
+  info->rows_identity = h->an.rows_identity;
   info->nupdates = h->an.nupd;
+  const bool reuse = product_reuse_applies(h->opt, h->fp32);
+  info->nnzb_product = reuse ? h->an.nnzb_product : h->nnzb;
+  info->rows_reuse = reuse ? h->an.rows_reuse : 0;
+  info->reserved2 = 0;
   return OPM_OK;
 }
 

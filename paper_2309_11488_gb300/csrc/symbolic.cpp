@@ -486,6 +486,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
   an.upd_src.clear();
   an.a_aux.assign((size_t)nnzb, -1);
   an.fz_mask.assign((size_t)((n + kWarp - 1) / kWarp), 0u);
+  std::vector<char> upper_hit((size_t)n, 0);  // some product lands on an upper block of the row
   for (int32_t ni = 0; ni < n; ++ni) {
     bool fused = true;
     int64_t lc = an.l_rowptr[ni];
@@ -510,6 +511,7 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
           an.upd_src.push_back(u_slot[ku]);
           if (pcol[ic] == ni) an.a_aux[a_at[c]] = u_slot[ku];
           else fused = false;
+          if (pcol[ic] > ni) upper_hit[ni] = 1;
           do ++ic; while (ic < arp[ni + 1] && !pk[ic]);
           do ++kc; while (kc < arp[k + 1] && !pk[kc]);
           ++ku;
@@ -526,6 +528,40 @@ opm_status analyse(int32_t n, const int32_t *rowptr, const int32_t *colidx, cons
   }
   if (an.upd_dst.size() >= ((size_t)1 << 31)) return OPM_ERR_ARG;
   an.nupd = (int64_t)an.upd_dst.size();
+
+  // ---- what the products after an application walk (sp_mask, sp_len)
+  an.sp_mask.assign((size_t)(2 * nslices), 0u);
+  an.sp_len.assign((size_t)n, 0);
+  an.nnzb_product = 0;
+  an.rows_identity = 0;
+  an.rows_reuse = 0;
+  for (int32_t ni = 0; ni < n; ++ni) {
+    int32_t lower = 0;
+    bool all_kept = true, upper_kept = true, has_upper = false;
+    for (int64_t c = arp[ni]; c < arp[ni + 1]; ++c) {
+      lower += pcol[c] < ni;
+      has_upper = has_upper || pcol[c] > ni;
+      if (!pk[c]) {
+        all_kept = false;
+        if (pcol[c] > ni) upper_kept = false;
+      }
+    }
+    const uint32_t bit = 1u << (ni % kWarp);
+    int32_t len = arp[ni + 1] - arp[ni];
+    if (lower == 0 && all_kept) {
+      an.sp_mask[2 * (ni / kWarp)] |= bit;
+      len = 0;
+      ++an.rows_identity;
+    } else if (has_upper && upper_kept && !upper_hit[ni]) {
+      an.sp_mask[2 * (ni / kWarp) + 1] |= bit;
+      len = 1 + lower;
+      ++an.rows_reuse;
+    }
+    an.sp_len[ni] = len;
+    an.nnzb_product += len;
+  }
+  an.sp_tile.assign((size_t)(((int64_t)n + kSpmvRows - 1) / kSpmvRows), 0);
+  for (int32_t ni = 0; ni < n; ++ni) an.sp_tile[ni / kSpmvRows] += an.sp_len[ni];
   return OPM_OK;
 }
 

@@ -52,7 +52,8 @@ class opm_options(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("spin_limit_us", ctypes.c_int32),
                 ("debug_skip_item", ctypes.c_int32), ("profile_kernels", ctypes.c_int32),
                 ("sweep_launch", ctypes.c_int32), ("small_phase_slices", ctypes.c_int32),
-                ("cp_sweeps", ctypes.c_int32), ("tri_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("cp_sweeps", ctypes.c_int32), ("tri_sweeps", ctypes.c_int32), ("product_reuse", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 OPM_TUNE_MAX = 24
@@ -72,13 +73,15 @@ class opm_info(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int32), ("schedule", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("nsets", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
                 ("nnzb_upper", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("nphases", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nupdates", ctypes.c_int64)]
+                ("nphases", ctypes.c_int32), ("rows_identity", ctypes.c_int32), ("nupdates", ctypes.c_int64),
+                ("nnzb_product", ctypes.c_int64), ("rows_reuse", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class opm_analysis_info(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("nsets", ctypes.c_int32), ("nphases", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("nnzb_kept", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
-                ("nnzb_upper", ctypes.c_int64), ("nupdates", ctypes.c_int64)]
+                ("rows_identity", ctypes.c_int32), ("nnzb_kept", ctypes.c_int64), ("nnzb_lower", ctypes.c_int64),
+                ("nnzb_upper", ctypes.c_int64), ("nupdates", ctypes.c_int64), ("nnzb_product", ctypes.c_int64),
+                ("rows_reuse", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 KERNELS = ["factor", "apply", "spmv", "update", "setup", "finish"]
@@ -427,13 +430,14 @@ class Batch:
     """A set of handles factorised and solved together (see include/opm_bsr.h)."""
 
     def __init__(self, handles, stream=None, chunk=0, sweep_launch="auto", small_phase_slices=0, cp_sweeps=0,
-                 tri_sweeps=0):
+                 tri_sweeps=0, product_reuse=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.handles = list(handles)
         hs = (ctypes.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
         o = opm_options_default(stream=stream, chunk=chunk, sweep_launch=sweep_launch,
-                                small_phase_slices=small_phase_slices, cp_sweeps=cp_sweeps, tri_sweeps=tri_sweeps)
+                                small_phase_slices=small_phase_slices, cp_sweeps=cp_sweeps, tri_sweeps=tri_sweeps,
+                                product_reuse=product_reuse)
         out = ctypes.c_void_p()
         st = lib().opm_batch_create(len(self.handles), hs, ctypes.byref(o), ctypes.byref(out))
         if st != OPM_OK:
@@ -506,14 +510,14 @@ class Solver:
 
     def __init__(self, nb, rowptr, colidx, vals, schedule="auto", precision="fp64", stream=None, chunk=0,
                  spin_limit_us=0, debug_skip_item=-1, profile_kernels=False, sweep_launch="auto",
-                 small_phase_slices=0, part=None, cp_sweeps=0, tri_sweeps=0):
+                 small_phase_slices=0, part=None, cp_sweeps=0, tri_sweeps=0, product_reuse=0):
         if stream is not None and not isinstance(stream, int):
             stream = stream.cuda_stream
         self.options = opm_options_default(schedule=schedule, precision=precision, stream=stream, chunk=chunk,
                                            spin_limit_us=spin_limit_us, debug_skip_item=debug_skip_item,
                                            profile_kernels=int(bool(profile_kernels)), sweep_launch=sweep_launch,
                                            small_phase_slices=small_phase_slices, cp_sweeps=cp_sweeps,
-                                           tri_sweeps=tri_sweeps)
+                                           tri_sweeps=tri_sweeps, product_reuse=product_reuse)
         self.status, self.h = opm_bsr_create(nb, rowptr, colidx, vals, self.options, part=part)
         self.nb = nb
 

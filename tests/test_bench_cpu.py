@@ -65,6 +65,28 @@ def test_work_counts_on_a_hand_counted_system():
     assert jf == int(4.5 * 2 + 9 * 1 * 2 + 9 * 2 * 2) and jb > b.algorithmic_apply_bytes(info, False) // 2
 
 
+def test_work_counts_with_the_product_reuse():
+    """The same two cells with the reuse: row 0 has no block left of its
+    diagonal (its product is p_0, no block walked), row 1 has no upper block
+    (walks its 2 blocks); nothing is stored by the backward sweep."""
+    b = _bench_module()
+    info = _Info(2, 4, 1, 1)
+    info.nnzb_product, info.rows_identity, info.rows_reuse, info.nupdates = 2, 1, 0, 0
+    assert b.product_terms(info) == (2, 1, 0)
+    # 2 walked blocks, A's row pointers, the walk lengths, one slice's row
+    # classes, one added 3-vector
+    assert b.product_bytes(info) == 2 * 76 + 4 * 3 + 4 * 2 + 8 + 24
+    assert b.kernel_work(info, False)["spmv"] == (2 * 76 + 4 * 3 + 4 * 2 + 8 + 24 + 72 * 2, 9 * 2 + 6 * 2)
+    plain = b.algorithmic_apply_bytes(_Info(2, 4, 1, 1), False)
+    assert b.algorithmic_apply_bytes(info, False) == plain + 8
+    nbytes, fma = b.iteration_work(info, False)
+    assert nbytes == 2 * (2 * 76 + 4 * 2 + 4 * 2 + 8 + 24) + 2 * (76 * 4 + 4 * 2 + 8) + 27 * 24 * 2
+    assert fma == 18 * 2 + 18 * 4 + 36 * 2
+    # a reusing row stores its upper sum in each application
+    info.rows_reuse = 1
+    assert b.algorithmic_apply_bytes(info, False) == plain + 8 + 24
+
+
 def test_fp64_fma_peak_is_the_documented_lane_rate():
     b = _bench_module()
     assert np.isclose(b.FP64_FMA_PEAK, 2 * 152 * 2.07e9)
