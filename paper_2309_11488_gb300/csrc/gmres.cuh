@@ -16,11 +16,16 @@ namespace opm {
 constexpr int kGmMaxVec = 65;  // restart length <= 64, plus one vector
 
 // y = A x - wells (schedule order), one row per thread over 256-row tiles.
+// The Arnoldi step's product v = A t right after t = inv(M) w
+// (APPLIED: row_operator_applied with w as the application's input, tiles
+// in the runner's longest-first order).
+template <bool APPLIED>
 __global__ void __launch_bounds__(256) k_gm_operator(Batch B, const double *x, double *y) {
   const Sys &S = B.sys[0];
-  const int i = blockIdx.x * kSpmvRows + threadIdx.x;
+  const int i = (APPLIED ? B.tiles_s[blockIdx.x].y : (int)blockIdx.x) * kSpmvRows + threadIdx.x;
   double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-  row_operator(S, x, i, y0, y1, y2);
+  if (APPLIED) row_operator_applied<true>(S, x, S.w, i, y0, y1, y2);
+  else row_operator(S, x, i, y0, y1, y2);
   if (i < S.n) {
     y[3ll * i] = y0;
     y[3ll * i + 1] = y1;

@@ -1225,9 +1225,12 @@ opm_status gm_build(opm_solver *h) {
     k_gm_dots_s<<<ntile, 256, 0, cap>>>(n3, Vb, n3, gs, sel, w, part);
     k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile, gs, sel, out);
   };
-  auto op = [&](int which, const double *in, double *out) {  // out = A in - wells
+  // out = A in - wells; applied: in = inv(M) w was just formed (the product
+  // may take the application's sums)
+  auto op = [&](int which, const double *in, double *out, bool applied) {
     if (R.has_wells) k_wells<<<1, 256, 0, cap>>>(R.B, which);
-    k_gm_operator<<<ntile, 256, 0, cap>>>(R.B, in, out);
+    if (applied && R.reuse) k_gm_operator<true><<<ntile, 256, 0, cap>>>(R.B, in, out);
+    else k_gm_operator<false><<<ntile, 256, 0, cap>>>(R.B, in, out);
   };
   // ---- start, loop node, end
   if (cudaGraphCreate(&g, 0) != cudaSuccess ||
@@ -1246,7 +1249,7 @@ opm_status gm_build(opm_solver *h) {
       s = capture_conditional(cap, ch_loop, cudaGraphCondTypeWhile, &body);
     }
     if (s == OPM_OK) {
-      op(2, S.x, S.v);
+      op(2, S.x, S.v, false);
       k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);
       dots(S.r, 1, S.r, &gs->nrm2);
       k_gm_final<<<1, 1, 0, cap>>>(gs);
@@ -1264,7 +1267,7 @@ opm_status gm_build(opm_solver *h) {
     } else {
       k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 0, nullptr, S.w);  // w = v_j
       launch_apply<kModePlain>(R, cap);                                    // t = inv(M) v_j
-      op(4, S.t, S.v);                                                     // v = A t
+      op(4, S.t, S.v, true);                                               // v = A t
       dots(V, 0, S.v, gs->h1);
       // first correction with the second pass's projections, second
       // correction with the norm: one pass over V and w fewer each
@@ -1292,7 +1295,7 @@ opm_status gm_build(opm_solver *h) {
       k_gm_combine_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, gs->y, S.w, 1);  // w = V y
       launch_apply<kModePlain>(R, cap);                                       // t = inv(M) V y
       k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.t, S.t, S.x, 1, gs);           // x += t
-      op(2, S.x, S.v);
+      op(2, S.x, S.v, false);
       k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);           // r = b - A x
       dots(S.r, 1, S.r, &gs->nrm2);
       k_gm_restart<<<1, 1, 0, cap>>>(gs);

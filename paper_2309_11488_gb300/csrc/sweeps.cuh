@@ -218,10 +218,10 @@ __device__ __forceinline__ void fwd_rows(const Sys &S, int sl, int r0, int r1) {
 
 // Backward substitution for the rows of slice sl inside [r0, r1) that have
 // U blocks: z_i = inv(U_ii)(y_i - sum_{j>i} U_ij z_j) (Algorithm 1,
-// equation 4).  PRE as for fwd_rows.  With FP64 factors the upper sum
-// w_i = sum_{j>i} U_ij z_j is formed on its own (from zero) and then
-// subtracted; in a BiCGStab application the rows whose product takes it
-// (sp_mask.y) store it in uz.
+// equation 4).  PRE as for fwd_rows.  With FP64 factors, the rows whose
+// product after the application takes the upper sum w_i = sum_{j>i} U_ij z_j
+// (sp_mask.y) store it in uz as y_i - a, a = y_i - sum_{j>i} U_ij z_j being
+// the walk's result (y_i read again: it is not kept live across the walk).
 template <typename TF, int MODE, int PRE>
 __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
   constexpr int NP = PRE > 0 ? PRE : 1;
@@ -251,20 +251,16 @@ __device__ __forceinline__ void bwd_rows(const Sys &S, int sl, int r0, int r1) {
   if (act) yi = load3cg(y + 3ll * i);
   if (PRE > 0) gather_preloaded<double, NP>(z, len, act, jp, vv);
   if (MODE != kModePlain && !(status == kRunning && err == 0)) return;
-  constexpr bool kSep = sizeof(TF) == sizeof(double);  // upper sum on its own
-  TF a0 = kSep ? TF(0) : yi.c0, a1 = kSep ? TF(0) : yi.c1, a2 = kSep ? TF(0) : yi.c2;
+  TF a0 = yi.c0, a1 = yi.c1, a2 = yi.c2;
   if (PRE > 0) preloaded_sub<TF, double, NP>(len, act, bp, vv, a0, a1, a2);
   row_sub<TF, double>(S.u_col, lu + S.u_off, z, len, base, PRE, maxlen, act, a0, a1, a2);
   if (act) {
-    if (kSep) {
-      // a = -w exactly (negated products, round-to-nearest is symmetric)
-      if (MODE != kModePlain && S.uz && ((__ldg(S.sp_mask + sl).y >> lane) & 1u)) {
-        double *w = S.uz + 3ll * i;
-        w[0] = -(double)a0; w[1] = -(double)a1; w[2] = -(double)a2;
-      }
-      a0 = yi.c0 + a0;
-      a1 = yi.c1 + a1;
-      a2 = yi.c2 + a2;
+    if (sizeof(TF) == sizeof(double) && S.uz && ((__ldg(S.sp_mask + sl).y >> lane) & 1u)) {
+      const Vec3<TF> yr = load3cg(y + 3ll * i);
+      double *w = S.uz + 3ll * i;
+      w[0] = (double)(yr.c0 - a0);
+      w[1] = (double)(yr.c1 - a1);
+      w[2] = (double)(yr.c2 - a2);
     }
     if (PRE == 0) load_dinv<TF>(D, d);
     store_dinv_product<TF>(z + 3ll * i, d, a0, a1, a2);
