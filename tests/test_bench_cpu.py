@@ -85,6 +85,8 @@ def test_work_counts_with_the_product_reuse():
     # a reusing row stores its upper sum in each application
     info.rows_reuse = 1
     assert b.algorithmic_apply_bytes(info, False) == plain + 8 + 24
+    # the textbook count of the same iteration: all of A in every product
+    assert b.iteration_work(b.PlainInfo(info), False) == b.iteration_work(_Info(2, 4, 1, 1), False)
 
 
 def test_fp64_fma_peak_is_the_documented_lane_rate():
