@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.  REUSE as
 // for k_spmv_v.
 template <bool REUSE>
-__global__ void __launch_bounds__(256, REUSE ? 6 : 8) k_spmv_t(Batch B) {
+__global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
 
   pdl_enter();
   OPM_TILE_S(B, S, lt);
