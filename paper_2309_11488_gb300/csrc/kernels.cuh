@@ -644,9 +644,12 @@ __global__ void __launch_bounds__(256, 8) k_spmv_v(Batch B) {
 }
 
 // t = A s^, (t,s), (t,t), (s,s); the half-step test and omega.  REUSE as
-// for k_spmv_v.
-template <bool REUSE>
-__global__ void __launch_bounds__(256, 8) k_spmv_t(Batch B) {
+// for k_spmv_v.  WIDE: eight CTAs per SM (32 registers; with REUSE its
+// three sums spill 56 bytes per thread), for launches with more tiles than
+// six CTAs per SM hold; otherwise (REUSE) six CTAs per SM and no spill,
+// which a small system's latency-bound product prefers.
+template <bool REUSE, bool WIDE = true>
+__global__ void __launch_bounds__(256, (REUSE && !WIDE) ? 6 : 8) k_spmv_t(Batch B) {
 
   pdl_enter();
   OPM_TILE_S(B, S, lt);

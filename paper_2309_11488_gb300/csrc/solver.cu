@@ -85,6 +85,7 @@ struct Runner {
   bool reuse = false;     // products after an application use Sys::uz (opm_options.product_reuse)
   int chunk = 2, nsys = 0, nphases = 0, ntiles = 0, ntiles_s = 0;
   int small_entries = 0;  // sweep phases with at most this many slices take the latency form
+  int sms = 1;            // SMs of the device
   int cp_sweeps = 0;      // > 0: iterative ILU0 with this many sweeps instead of the phases
   int tri_sweeps = 0;     // > 0: Jacobi triangular solves with this many sweeps per triangle
   int nall = 0;           // slices of all systems (the iterative kernels' work list)
@@ -428,7 +429,8 @@ int launch_iteration(Runner &R, cudaStream_t st, cudaEvent_t *ev) {
     launch_pdl(k_wells, R.nsys, 256, st, R.B, 1);
     ++n;
   }
-  if (R.reuse) launch_pdl(k_spmv_t<true>, R.ntiles_s, 256, st, R.B);
+  if (R.reuse && R.ntiles_s > 6 * R.sms) launch_pdl(k_spmv_t<true, true>, R.ntiles_s, 256, st, R.B);
+  else if (R.reuse) launch_pdl(k_spmv_t<true, false>, R.ntiles_s, 256, st, R.B);
   else launch_pdl(k_spmv_t<false>, R.ntiles_s, 256, st, R.B);
   mark(4);
   launch_pdl(k_update, R.ntiles, 256, st, R.B);
@@ -645,6 +647,7 @@ opm_status runner_create(const std::vector<opm_solver *> &mem, cudaStream_t stre
     return fail(OPM_ERR_CUDA);
   }
   R->small_entries = o.small_phase_slices > 0 ? o.small_phase_slices : o.small_phase_slices < 0 ? 0 : 10 * sms;
+  R->sms = sms;
   R->cp_sweeps = o.cp_sweeps;
   R->tri_sweeps = o.tri_sweeps;
   R->reuse = product_reuse_applies(o, R->fp32);
