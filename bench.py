@@ -15,8 +15,8 @@ times the same solve on the step's factors, without the refactorisation.
 calls from pinned host buffers: each step copies the values and b in and
 reads x back.  It is measured one step at a time, and again as
 `e2e.overlapped`, with two handles on two streams used alternately so that a
-step's copies overlap the other handle's kernels (the median of three timed
-blocks).
+step's copies overlap the other handle's kernels; each is the median of three
+timed blocks of steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -477,14 +477,20 @@ def run_ours(args, rank, world, dist):
 
     for _ in range(2):
         e2e_step()
+    # three timed blocks of n_e2e steps, the median block: a block lasts a
+    # few tens of ms and crosses the host link, so one host stall would
+    # otherwise decide the figure
     n_e2e = max(10, args.steps // 2)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    barrier()
+    e2e_blocks = []
+    for _ in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_blocks.append(max_over_ranks(time.perf_counter() - t0))
+        barrier()
+    e2e_s = float(np.median(e2e_blocks))
 
     # the same calls through two handles of the pattern, each on its own
     # stream, used alternately: step k+1's host -> device copies overlap step
@@ -509,8 +515,7 @@ def run_ours(args, rank, world, dist):
                 st, it, rr = pair[q][0].wait()
                 assert st == 0, st
 
-    # three timed blocks of n_e2e steps, the median block: a block lasts a
-    # few tens of ms, so one host stall would otherwise decide the figure
+    # timed as the one-handle figure: the median of three blocks
     e2e_overlapped(4)
     blocks = []
     for _ in range(3):
@@ -631,6 +636,7 @@ def run_ours(args, rank, world, dist):
         "e2e": {"value": round(world * n_e2e / e2e_s, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(s.vals.nbytes + 24 * s.nb), "d2h_bytes_per_step": int(24 * s.nb),
                 "form": "one handle; each step's copies, refactor and solve, then its wait",
+                "blocks_s": [round(v, 5) for v in e2e_blocks], "steps_per_block": n_e2e,
                 "overlapped": {"value": round(world * n_e2e / e2e2_s, 3), "unit": UNIT,
                                "blocks_s": [round(v, 5) for v in blocks], "steps_per_block": n_e2e,
                                "form": "two handles on two streams used alternately: a step's copies overlap "
