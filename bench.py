@@ -10,7 +10,9 @@ the seeded 100^3 grid with a 5% inactive mask and 1% fault connections
 library's own SpMV.  Inputs (456 MB of values) are larger than L2.
 
 `value` is device-timed with the inputs resident in HBM; `without_refactor`
-times the same solve on the step's factors, without the refactorisation.
+times the same solve on the step's factors, without the refactorisation;
+`product_reuse_off` the same step with every BiCGStab product walking all of
+A.
 `e2e` makes the same
 calls from pinned host buffers: each step copies the values and b in and
 reads x back.  It is measured one step at a time, and again as
@@ -659,6 +661,8 @@ def run_ours(args, rank, world, dist):
     sv64.close()
     sv32.close()
     del vals_h, b_h, x_h
+    if r64["info"].nnzb_product < r64["info"].nnzb:
+        out["product_reuse_off"] = measure_reuse_off(args, s, r64, barrier, max_over_ranks, world)
     tight_x = None
     if not args.no_tight:
         out["c3_rtol1e-6"], tight_x = measure_tight(args, s, r64, r32, barrier, max_over_ranks, world)
@@ -685,6 +689,43 @@ def run_ours(args, rank, world, dist):
         if tight_x is not None:
             out["c3_rtol1e-6"]["cpu_baseline"] = cpu_baseline_tight(s, out["c3_rtol1e-6"]["schedule"], tight_x)
     return out
+
+
+def measure_reuse_off(args, s, r64, barrier, max_over_ranks, world):
+    """The headline step (FP64, the same launch options) with every product
+    walking all of A (opm_options.product_reuse = -1): the product reuse's
+    effect measured beside the headline, and x against the headline's."""
+    import torch
+    from paper_2309_11488_gb300 import opm
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, ci, vals = dev(s.rowptr), dev(s.colidx), dev(s.vals)
+    kw = dict(r64["options"], product_reuse=-1)
+    with opm.Solver(s.nb, rp, ci, vals, precision="fp64", **kw) as sv:
+        b = sv.spmv(dev(s.x_true))
+        x = torch.empty_like(b)
+
+        def step():
+            sv.launch(vals, b, x, rtol=RTOL, maxit=200)
+            return sv.wait()
+        for _ in range(max(3, args.warmup)):
+            step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            st, it, rr = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        xo = x.cpu().numpy()
+    xr = r64["x"]
+    return {"value": round(world * args.steps / (ms * 1e-3), 3), "unit": UNIT,
+            "ms_per_step": round(ms / args.steps, 4), "iters": int(it), "status": int(st),
+            "options": kw, "product_blocks": int(r64["info"].nnzb),
+            "x_rel_diff_vs_reuse": float(np.linalg.norm(xo - xr) / np.linalg.norm(xr)),
+            "form": "the headline step with every BiCGStab product walking all of A "
+                    "(opm_options.product_reuse = -1); the headline's products walk "
+                    f"{int(r64['info'].nnzb_product):,} of {int(r64['info'].nnzb):,} blocks"}
 
 
 def measure_jacobi(args, s, barrier, max_over_ranks, world):
