@@ -53,25 +53,40 @@ struct GmState {
 
 __device__ __forceinline__ int gm_nv(const GmState *gs, int sel) { return sel == 0 ? gs->j + 1 : 1; }
 
+// The Gram-Schmidt kernels work on tiles of kGmRows rows, four rows per
+// thread (rows t, t + 256, t + 512, t + 768 of the tile): a thread sums its
+// rows before the warp's butterfly, which costs the FP64 pipe as much per
+// value as the dot itself.  With one row per thread a projection pass took
+// 15.5 us per basis vector at the 949,871-cell system, bound by that pipe;
+// the combination pass, with no reduction, 5 us.
+constexpr int kGmRows = 1024;
+
 // part[tile][q] = V_q . w for q < nv (sel 0: the columns 0..j; sel 1: V = w
 // itself, nv = 1), as k_gm_dots.
 __global__ void __launch_bounds__(256) k_gm_dots_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
                                                    int sel, const double *w, double *part) {
   __shared__ double sm[kGmMaxVec][8];
   const int nv = gm_nv(gs, sel);
-  const int64_t e0 = (int64_t)blockIdx.x * 3 * kSpmvRows + 3 * threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * 3 * kGmRows + 3 * threadIdx.x;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-  if (e0 + 2 < n3) {
-    w0 = __ldcg(w + e0);
-    w1 = __ldcg(w + e0 + 1);
-    w2 = __ldcg(w + e0 + 2);
+  double x[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t e = b0 + 3 * 256 * k;
+    const bool in = e + 2 < n3;
+    x[k][0] = in ? __ldcg(w + e) : 0.0;
+    x[k][1] = in ? __ldcg(w + e + 1) : 0.0;
+    x[k][2] = in ? __ldcg(w + e + 2) : 0.0;
   }
   for (int q = 0; q < nv; ++q) {
     double d[1] = {0.0};
-    if (e0 + 2 < n3) {
-      const double *v = V + q * stride + e0;
-      d[0] = fma(__ldcg(v + 2), w2, fma(__ldcg(v + 1), w1, __ldcg(v) * w0));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t e = b0 + 3 * 256 * k;
+      if (e + 2 < n3) {
+        const double *v = V + q * stride + e;
+        d[0] = fma(__ldcg(v + 2), x[k][2], fma(__ldcg(v + 1), x[k][1], fma(__ldcg(v), x[k][0], d[0])));
+      }
     }
     warp_sum<1>(d);
     if (lane == 0) sm[q][wp] = d[0];
@@ -117,32 +132,43 @@ __global__ void __launch_bounds__(256) k_gm_correct_s(int64_t n3, const double *
   const int nv = gs->j + 1;
   for (int q = threadIdx.x; q < nv; q += blockDim.x) c[q] = coef[q];
   __syncthreads();
-  const int64_t e0 = (int64_t)blockIdx.x * 3 * kSpmvRows + 3 * threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * 3 * kGmRows + 3 * threadIdx.x;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const bool in = e0 + 2 < n3;
-  double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-  if (in) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int q = 0; q < nv; ++q) {
-      const double *v = V + q * stride + e0;
-      a0 = fma(c[q], __ldcg(v), a0);
-      a1 = fma(c[q], __ldcg(v + 1), a1);
-      a2 = fma(c[q], __ldcg(v + 2), a2);
+  double x[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t e = b0 + 3 * 256 * k;
+    x[k][0] = x[k][1] = x[k][2] = 0.0;
+    if (e + 2 < n3) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int q = 0; q < nv; ++q) {
+        const double *v = V + q * stride + e;
+        a0 = fma(c[q], __ldcg(v), a0);
+        a1 = fma(c[q], __ldcg(v + 1), a1);
+        a2 = fma(c[q], __ldcg(v + 2), a2);
+      }
+      x[k][0] = w[e] - a0;
+      x[k][1] = w[e + 1] - a1;
+      x[k][2] = w[e + 2] - a2;
+      w[e] = x[k][0];
+      w[e + 1] = x[k][1];
+      w[e + 2] = x[k][2];
     }
-    w0 = w[e0] - a0;
-    w1 = w[e0 + 1] - a1;
-    w2 = w[e0 + 2] - a2;
-    w[e0] = w0;
-    w[e0 + 1] = w1;
-    w[e0 + 2] = w2;
   }
   const int nd = NEXT_DOTS ? nv : 1;
   for (int q = 0; q < nd; ++q) {
     double d[1] = {0.0};
-    if (in) {
-      const double *v = NEXT_DOTS ? V + q * stride + e0 : nullptr;
-      d[0] = NEXT_DOTS ? fma(__ldcg(v + 2), w2, fma(__ldcg(v + 1), w1, __ldcg(v) * w0))
-                       : fma(w2, w2, fma(w1, w1, w0 * w0));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t e = b0 + 3 * 256 * k;
+      if (e + 2 < n3) {
+        if (NEXT_DOTS) {
+          const double *v = V + q * stride + e;
+          d[0] = fma(__ldcg(v + 2), x[k][2], fma(__ldcg(v + 1), x[k][1], fma(__ldcg(v), x[k][0], d[0])));
+        } else {
+          d[0] = fma(x[k][2], x[k][2], fma(x[k][1], x[k][1], fma(x[k][0], x[k][0], d[0])));
+        }
+      }
     }
     warp_sum<1>(d);
     if (lane == 0) sm[q][wp] = d[0];
@@ -177,9 +203,10 @@ __global__ void __launch_bounds__(256) k_gm_scale_s(int64_t n3, const double *w,
                                                     double *V, int64_t stride) {
   if (sel == 1 && gs->status != kRunning) return;
   const double d = sel == 0 ? sqrt(gs->nrm2) : gs->beta;
+  const double rd = d != 0.0 ? 1.0 / d : 0.0;  // one division, then products
   double *out = V + (sel == 0 ? (int64_t)(gs->j + 1) * stride : 0);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = d != 0.0 ? w[e] / d : 0.0;
+    out[e] = w[e] * rd;
 }
 
 // dst = V_j (sel 0) or src (sel 1).
