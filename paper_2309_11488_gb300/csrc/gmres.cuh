@@ -198,23 +198,32 @@ __global__ void __launch_bounds__(256) k_gm_combine_s(int64_t n3, const double *
 }
 
 // sel 0: V_{j+1} = w / sqrt(nrm2) (zero when the norm is); sel 1: V_0 = w /
-// beta at the start of a cycle (only while the solve runs).
+// beta at the start of a cycle (only while the solve runs).  The new basis
+// vector also goes to next, the next Arnoldi step's input.  One thread per
+// CTA takes the square root and the reciprocal: at one per thread they cost
+// more FP64 issue slots than the pass itself.
 __global__ void __launch_bounds__(256) k_gm_scale_s(int64_t n3, const double *w, const GmState *gs, int sel,
-                                                    double *V, int64_t stride) {
+                                                    double *V, int64_t stride, double *next) {
+  __shared__ double srd;
   if (sel == 1 && gs->status != kRunning) return;
-  const double d = sel == 0 ? sqrt(gs->nrm2) : gs->beta;
-  const double rd = d != 0.0 ? 1.0 / d : 0.0;  // one division, then products
+  if (threadIdx.x == 0) {
+    const double d = sel == 0 ? sqrt(gs->nrm2) : gs->beta;
+    srd = d != 0.0 ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
+  const double rd = srd;
   double *out = V + (sel == 0 ? (int64_t)(gs->j + 1) * stride : 0);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = w[e] * rd;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x) {
+    const double u = w[e] * rd;
+    out[e] = u;
+    next[e] = u;
+  }
 }
 
-// dst = V_j (sel 0) or src (sel 1).
-__global__ void __launch_bounds__(256) k_gm_copy_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
-                                                   int sel, const double *src, double *dst) {
-  const double *from = sel == 0 ? V + (int64_t)gs->j * stride : src;
+// dst = src.
+__global__ void __launch_bounds__(256) k_gm_copy_s(int64_t n3, const double *src, double *dst) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = from[e];
+    dst[e] = src[e];
 }
 
 // mode 0: out = a - b; mode 1: out += a when the closing cycle updates x;

@@ -1207,9 +1207,9 @@ opm_status capture_handle(cudaStream_t cap, cudaGraphConditionalHandle *ch) {
 // preconditioner and the operator, classical Gram-Schmidt twice, the norm,
 // v_{j+1}, then the Hessenberg column, Givens rotations and g in one
 // thread) with a conditional end-of-cycle branch (H y = g, x += inv(M) V y,
-// r = b - A x, the restart test, v_0 = r / beta), and the end (true
-// residual, x back to the caller's order, zero on failure).  The host reads
-// the outcome once.
+// r = b - A x, the restart test, v_0 = r / beta), and the end (relres from
+// that branch's true residual, x back to the caller's order, zero on
+// failure).  The host reads the outcome once.
 opm_status gm_build(opm_solver *h) {
   Runner &R = *h->run;
   const Sys &S = h->sys;
@@ -1242,23 +1242,22 @@ opm_status gm_build(opm_solver *h) {
     s = OPM_ERR_CUDA;
   if (s == OPM_OK) {
     k_gather<<<R.ntiles, 256, 0, cap>>>(R.B);
-    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.w, S.p);
-    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.w, S.r);
+    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, S.w, S.p);
+    k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, S.w, S.r);
     if (cudaMemsetAsync(S.x, 0, sizeof(double) * (size_t)n3, cap) != cudaSuccess) s = OPM_ERR_CUDA;
     dots(S.r, 1, S.r, &gs->nrm2);
     s = capture_handle(cap, &ch_loop);
     if (s == OPM_OK) {
       k_gm_init<<<1, 1, 0, cap>>>(gs, ch_loop);
-      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3);
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3, S.w);
       s = capture_conditional(cap, ch_loop, cudaGraphCondTypeWhile, &body);
     }
     if (s == OPM_OK) {
-      op(2, S.x, S.v, false);
-      k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);
-      dots(S.r, 1, S.r, &gs->nrm2);
+      // the loop only ends after an end-of-cycle branch, whose last norm is
+      // ||b - A x|| of the final x; without a cycle x = 0 and r = b
       k_gm_final<<<1, 1, 0, cap>>>(gs);
       k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.x, S.x, S.x, 2, gs);  // x = 0 on failure
-      k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 1, S.x, S.t);
+      k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, S.x, S.t);
       k_scatter<<<R.ntiles, 256, 0, cap>>>(R.B);
     }
     if (cudaStreamEndCapture(cap, &g) != cudaSuccess) s = OPM_ERR_CUDA;
@@ -1269,8 +1268,7 @@ opm_status gm_build(opm_solver *h) {
         cudaSuccess) {
       s = OPM_ERR_CUDA;
     } else {
-      k_gm_copy_s<<<egrid, 256, 0, cap>>>(n3, V, n3, gs, 0, nullptr, S.w);  // w = v_j
-      launch_apply<kModePlain>(R, cap);                                    // t = inv(M) v_j
+      launch_apply<kModePlain>(R, cap);                                    // t = inv(M) v_j (held in w)
       op(4, S.t, S.v, true);                                               // v = A t
       dots(V, 0, S.v, gs->h1);
       // first correction with the second pass's projections, second
@@ -1279,7 +1277,7 @@ opm_status gm_build(opm_solver *h) {
       k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile_g, gs, 0, gs->h2);
       k_gm_correct_s<false><<<ntile_g, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, part);
       k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile_g, gs, 1, &gs->nrm2);
-      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.v, gs, 0, V, n3);
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.v, gs, 0, V, n3, S.w);  // v_{j+1}, also into w
       s = capture_handle(cap, &ch_end);
       if (s == OPM_OK) {
         k_gm_step<<<1, 1, 0, cap>>>(gs, ch_end);
@@ -1303,7 +1301,7 @@ opm_status gm_build(opm_solver *h) {
       k_gm_vec_s<<<egrid, 256, 0, cap>>>(n3, S.p, S.v, S.r, 0, gs);           // r = b - A x
       dots(S.r, 1, S.r, &gs->nrm2);
       k_gm_restart<<<1, 1, 0, cap>>>(gs);
-      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3);             // v_0 = r / beta
+      k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.r, gs, 1, V, n3, S.w);        // v_0 = r / beta, also into w
       if (cudaStreamEndCapture(cap, &tail_body) != cudaSuccess) s = OPM_ERR_CUDA;
     }
   }
