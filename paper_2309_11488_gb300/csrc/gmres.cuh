@@ -53,44 +53,89 @@ struct GmState {
 
 __device__ __forceinline__ int gm_nv(const GmState *gs, int sel) { return sel == 0 ? gs->j + 1 : 1; }
 
-// The Gram-Schmidt kernels work on tiles of kGmRows rows, four rows per
-// thread (rows t, t + 256, t + 512, t + 768 of the tile): a thread sums its
-// rows before the warp's butterfly, which costs the FP64 pipe as much per
-// value as the dot itself.  With one row per thread a projection pass took
-// 15.5 us per basis vector at the 949,871-cell system, bound by that pipe;
-// the combination pass, with no reduction, 5 us.
-constexpr int kGmRows = 1024;
+// The Gram-Schmidt kernels work on tiles of 256 R rows, R rows per thread
+// (rows t, t + 256, ... of the tile): a thread sums its rows before the
+// warp reduces, and the warp reduces eight projections at once
+// (warp_sum8_split), since a butterfly per value costs the FP64 pipe as much
+// per thread as the dots themselves.  With one row per thread a projection
+// pass took 15.5 us per basis vector at the 949,871-cell system, bound by
+// that pipe.  The host picks R so that the tiles fill whole rounds of the
+// SMs (gm_rows_per_thread).
+
+// Sums each of v[0..7] over the 32 lanes of the warp with 9 shuffles and
+// additions per lane instead of 40: three halving exchanges (a lane keeps
+// half of its values and adds its partner's copies of them) leave lane l
+// with value l >> 2 summed over 8 lanes, and two butterfly steps finish it.
+// Returns value (lane >> 2)'s sum; every step adds the same two numbers in
+// both partners, so all four lanes holding a value hold the same bits.
+__device__ __forceinline__ double warp_sum8_split(const double (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  double u[4], t[2];
+  bool hi = lane & 16;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double keep = hi ? v[i + 4] : v[i], send = hi ? v[i] : v[i + 4];
+    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  hi = lane & 8;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double keep = hi ? u[i + 2] : u[i], send = hi ? u[i] : u[i + 2];
+    t[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  hi = lane & 4;
+  double s = (hi ? t[1] : t[0]) + __shfl_xor_sync(0xffffffffu, hi ? t[0] : t[1], 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
+// The partial projections V_q . x over this thread's R rows (x[k] = its
+// entries of row k), reduced over the warp in chunks of eight and stored
+// to sm[q][warp] for q < nv.
+template <int R>
+__device__ __forceinline__ void gm_project(int64_t n3, const double *V, int64_t stride, int64_t b0, int nv,
+                                           const double (&x)[R][3], double (*sm)[8]) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int q0 = 0; q0 < nv; q0 += 8) {
+    double d[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      d[u] = 0.0;
+      if (q0 + u < nv) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const int64_t e = b0 + 3 * 256 * k;
+          if (e + 2 < n3) {
+            const double *v = V + (q0 + u) * stride + e;
+            d[u] = fma(__ldcg(v + 2), x[k][2], fma(__ldcg(v + 1), x[k][1], fma(__ldcg(v), x[k][0], d[u])));
+          }
+        }
+      }
+    }
+    const double s = warp_sum8_split(d);
+    if ((lane & 3) == 0 && q0 + (lane >> 2) < nv) sm[q0 + (lane >> 2)][wp] = s;
+  }
+}
 
 // part[tile][q] = V_q . w for q < nv (sel 0: the columns 0..j; sel 1: V = w
 // itself, nv = 1), as k_gm_dots.
+template <int R>
 __global__ void __launch_bounds__(256) k_gm_dots_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
                                                    int sel, const double *w, double *part) {
   __shared__ double sm[kGmMaxVec][8];
   const int nv = gm_nv(gs, sel);
-  const int64_t b0 = (int64_t)blockIdx.x * 3 * kGmRows + 3 * threadIdx.x;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  double x[4][3];
+  const int64_t b0 = (int64_t)blockIdx.x * 3 * 256 * R + 3 * threadIdx.x;
+  double x[R][3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < R; ++k) {
     const int64_t e = b0 + 3 * 256 * k;
     const bool in = e + 2 < n3;
     x[k][0] = in ? __ldcg(w + e) : 0.0;
     x[k][1] = in ? __ldcg(w + e + 1) : 0.0;
     x[k][2] = in ? __ldcg(w + e + 2) : 0.0;
   }
-  for (int q = 0; q < nv; ++q) {
-    double d[1] = {0.0};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t e = b0 + 3 * 256 * k;
-      if (e + 2 < n3) {
-        const double *v = V + q * stride + e;
-        d[0] = fma(__ldcg(v + 2), x[k][2], fma(__ldcg(v + 1), x[k][1], fma(__ldcg(v), x[k][0], d[0])));
-      }
-    }
-    warp_sum<1>(d);
-    if (lane == 0) sm[q][wp] = d[0];
-  }
+  gm_project<R>(n3, V, stride, b0, nv, x, sm);
   __syncthreads();
   if (threadIdx.x < nv) {
     double acc = 0.0;
@@ -122,9 +167,10 @@ __global__ void __launch_bounds__(256) k_gm_reduce_s(const double *part, int nti
 // k_gm_dots_s: w -= sum_{q <= j} coef[q] V_q, then (NEXT_DOTS) the partial
 // projections V_q . w of the corrected w for q <= j, or (!NEXT_DOTS) the
 // partial ||w||^2.  Each entry's correction is the same expression as in
-// k_gm_combine_s and each partial the same as in k_gm_dots_s, so the results
-// are those of the separate kernels, with one pass over V and w fewer.
-template <bool NEXT_DOTS>
+// k_gm_combine_s and each partial projection the same as in k_gm_dots_s, so
+// the results are those of the separate kernels, with one pass over V and w
+// fewer.
+template <int R, bool NEXT_DOTS>
 __global__ void __launch_bounds__(256) k_gm_correct_s(int64_t n3, const double *V, int64_t stride, const GmState *gs,
                                                       const double *coef, double *w, double *part) {
   __shared__ double c[kGmMaxVec];
@@ -132,11 +178,10 @@ __global__ void __launch_bounds__(256) k_gm_correct_s(int64_t n3, const double *
   const int nv = gs->j + 1;
   for (int q = threadIdx.x; q < nv; q += blockDim.x) c[q] = coef[q];
   __syncthreads();
-  const int64_t b0 = (int64_t)blockIdx.x * 3 * kGmRows + 3 * threadIdx.x;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  double x[4][3];
+  const int64_t b0 = (int64_t)blockIdx.x * 3 * 256 * R + 3 * threadIdx.x;
+  double x[R][3];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < R; ++k) {
     const int64_t e = b0 + 3 * 256 * k;
     x[k][0] = x[k][1] = x[k][2] = 0.0;
     if (e + 2 < n3) {
@@ -155,30 +200,51 @@ __global__ void __launch_bounds__(256) k_gm_correct_s(int64_t n3, const double *
       w[e + 2] = x[k][2];
     }
   }
-  const int nd = NEXT_DOTS ? nv : 1;
-  for (int q = 0; q < nd; ++q) {
+  if (NEXT_DOTS) {
+    gm_project<R>(n3, V, stride, b0, nv, x, sm);
+  } else {
     double d[1] = {0.0};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t e = b0 + 3 * 256 * k;
-      if (e + 2 < n3) {
-        if (NEXT_DOTS) {
-          const double *v = V + q * stride + e;
-          d[0] = fma(__ldcg(v + 2), x[k][2], fma(__ldcg(v + 1), x[k][1], fma(__ldcg(v), x[k][0], d[0])));
-        } else {
-          d[0] = fma(x[k][2], x[k][2], fma(x[k][1], x[k][1], fma(x[k][0], x[k][0], d[0])));
-        }
-      }
-    }
+    for (int k = 0; k < R; ++k)
+      d[0] = fma(x[k][2], x[k][2], fma(x[k][1], x[k][1], fma(x[k][0], x[k][0], d[0])));
     warp_sum<1>(d);
-    if (lane == 0) sm[q][wp] = d[0];
+    if ((threadIdx.x & 31) == 0) sm[0][threadIdx.x >> 5] = d[0];
   }
   __syncthreads();
+  const int nd = NEXT_DOTS ? nv : 1;
   if (threadIdx.x < nd) {
     double acc = 0.0;
     for (int k = 0; k < 8; ++k) acc += sm[threadIdx.x][k];
     part[(int64_t)blockIdx.x * kGmMaxVec + threadIdx.x] = acc;
   }
+}
+
+// The Gram-Schmidt kernels for R rows per thread.
+struct GmKernels {
+  void (*dots)(int64_t, const double *, int64_t, const GmState *, int, const double *, double *);
+  void (*correct)(int64_t, const double *, int64_t, const GmState *, const double *, double *, double *);
+  void (*correct_norm)(int64_t, const double *, int64_t, const GmState *, const double *, double *, double *);
+  int rows;  // rows per tile, 256 R
+};
+
+template <int R>
+GmKernels gm_kernels_for() {
+  return {k_gm_dots_s<R>, k_gm_correct_s<R, true>, k_gm_correct_s<R, false>, 256 * R};
+}
+
+// Rows per thread of the Gram-Schmidt kernels for n rows on sms SMs: the one
+// of 4, 5, 6, 8 whose tiles give the smallest per-SM share when every SM
+// takes whole tiles, the smaller R on ties (more threads per row).
+inline GmKernels gm_rows_per_thread(int64_t n, int sms) {
+  const GmKernels k[4] = {gm_kernels_for<4>(), gm_kernels_for<5>(), gm_kernels_for<6>(), gm_kernels_for<8>()};
+  int best = 0;
+  int64_t cost = -1;
+  for (int i = 0; i < 4; ++i) {
+    const int64_t tiles = (n + k[i].rows - 1) / k[i].rows;
+    const int64_t c = ((tiles + sms - 1) / sms) * k[i].rows;
+    if (cost < 0 || c < cost) cost = c, best = i;
+  }
+  return k[best];
 }
 
 // mode 0: w -= sum_{q <= j} coef[q] V_q (a Gram-Schmidt pass); mode 1:

@@ -1215,7 +1215,8 @@ opm_status gm_build(opm_solver *h) {
   const Sys &S = h->sys;
   const int64_t n3 = 3ll * h->n;
   const int ntile = S.ntiles_s;
-  const int ntile_g = std::max(1, (int)((h->n + kGmRows - 1) / kGmRows));  // Gram-Schmidt tiles
+  const GmKernels gk = gm_rows_per_thread(h->n, R.sms);
+  const int ntile_g = std::max(1, (int)((h->n + gk.rows - 1) / gk.rows));  // Gram-Schmidt tiles
   const int egrid = (int)std::min<int64_t>((n3 + 255) / 256, 152 * 8);
   double *V = h->gm_V;
   GmState *gs = h->gm_state;
@@ -1226,7 +1227,7 @@ opm_status gm_build(opm_solver *h) {
   cudaGraph_t g = nullptr, body = nullptr, tail_body = nullptr;
   cudaGraphConditionalHandle ch_loop = 0, ch_end = 0;
   auto dots = [&](const double *Vb, int sel, const double *w, double *out) {
-    k_gm_dots_s<<<ntile_g, 256, 0, cap>>>(n3, Vb, n3, gs, sel, w, part);
+    gk.dots<<<ntile_g, 256, 0, cap>>>(n3, Vb, n3, gs, sel, w, part);
     k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile_g, gs, sel, out);
   };
   // out = A in - wells; applied: in = inv(M) w was just formed (the product
@@ -1273,9 +1274,9 @@ opm_status gm_build(opm_solver *h) {
       dots(V, 0, S.v, gs->h1);
       // first correction with the second pass's projections, second
       // correction with the norm: one pass over V and w fewer each
-      k_gm_correct_s<true><<<ntile_g, 256, 0, cap>>>(n3, V, n3, gs, gs->h1, S.v, part);
+      gk.correct<<<ntile_g, 256, 0, cap>>>(n3, V, n3, gs, gs->h1, S.v, part);
       k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile_g, gs, 0, gs->h2);
-      k_gm_correct_s<false><<<ntile_g, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, part);
+      gk.correct_norm<<<ntile_g, 256, 0, cap>>>(n3, V, n3, gs, gs->h2, S.v, part);
       k_gm_reduce_s<<<kGmMaxVec, 256, 0, cap>>>(part, ntile_g, gs, 1, &gs->nrm2);
       k_gm_scale_s<<<egrid, 256, 0, cap>>>(n3, S.v, gs, 0, V, n3, S.w);  // v_{j+1}, also into w
       s = capture_handle(cap, &ch_end);
