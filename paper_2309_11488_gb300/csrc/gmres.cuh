@@ -1,12 +1,12 @@
 // Kernels of restarted GMRES(m) (OPM's other Krylov solver, Section 2):
 // products with the system operator in the schedule's order, and the
 // vector work of the Arnoldi process with classical Gram-Schmidt applied
-// twice: all projections of a pass in one launch (partial sums per 256-row
-// tile, then a fixed-order reduction), the corrections in another.  The
-// scalar part (Hessenberg column, Givens rotations, the small triangular
-// solve, the restart test) runs in FP64 on the device, in one warp, in the
-// oracle's order; the whole solve is one graph launch whose Arnoldi steps
-// are the body of a device-side while loop.
+// twice: all projections of a pass in one launch (partial sums per tile,
+// then a fixed-order reduction), the corrections in another.  The scalar
+// part (Hessenberg column, Givens rotations, the small triangular solve, the
+// restart test) runs in FP64 on the device, in one thread, in the oracle's
+// order; the whole solve is one graph launch whose Arnoldi steps are the
+// body of a device-side while loop.
 #pragma once
 
 #include "kernels.cuh"
