@@ -233,13 +233,15 @@ GmKernels gm_kernels_for() {
 }
 
 // Rows per thread of the Gram-Schmidt kernels for n rows on sms SMs: the one
-// of 4, 5, 6, 8 whose tiles give the smallest per-SM share when every SM
-// takes whole tiles, the smaller R on ties (more threads per row).
+// of 4, 5, 6 whose tiles give the smallest per-SM share when every SM takes
+// whole tiles, the smaller R on ties (more threads per row).  On 152 SMs
+// R = 4 up to 155,648 rows, then each of the three in turn (R = 5 at the
+// 949,871-cell system); a larger R never wins below 1.2 M rows.
 inline GmKernels gm_rows_per_thread(int64_t n, int sms) {
-  const GmKernels k[4] = {gm_kernels_for<4>(), gm_kernels_for<5>(), gm_kernels_for<6>(), gm_kernels_for<8>()};
+  const GmKernels k[3] = {gm_kernels_for<4>(), gm_kernels_for<5>(), gm_kernels_for<6>()};
   int best = 0;
   int64_t cost = -1;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 3; ++i) {
     const int64_t tiles = (n + k[i].rows - 1) / k[i].rows;
     const int64_t c = ((tiles + sms - 1) / sms) * k[i].rows;
     if (cost < 0 || c < cost) cost = c, best = i;

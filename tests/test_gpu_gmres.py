@@ -66,6 +66,15 @@ def test_gmres_config3_full_size():
     check_gmres(synth.config3(), "colour_sl", 1e-3, 30)
 
 
+@pytest.mark.parametrize("n", [54, 56, 60])
+def test_gmres_gram_schmidt_tilings(n):
+    """Faulted grids of 149,595, 166,822 and 205,187 cells: on 152 SMs the
+    Gram-Schmidt kernels take 4, 5 and 6 rows per thread there (the host
+    picks the count whose tiles fill whole rounds of the SMs), each with a
+    ragged last tile; restarts every 10 steps."""
+    check_gmres(synth.config3(n=n), "colour_kempe", 1e-6, 10)
+
+
 def test_gmres_maxit_and_zero_rhs():
     s = synth.config2()
     b = dev(rhs(s))
