@@ -573,8 +573,9 @@ opm_status opm_autotune_batch(int32_t nsys, const int32_t *nb, const int32_t *co
  *   and the call return OPM_ERR_PATTERN.  A rowptr[nb] past the end of the
  *   caller's arrays cannot be detected.
  *   Work is issued on stream (NULL = default stream); the call synchronises
- *   that stream before it returns.  Returns OPM_OK, OPM_ERR_ARG,
- *   OPM_ERR_PATTERN or OPM_ERR_CUDA.
+ *   that stream before it returns, so it cannot be recorded in a CUDA graph:
+ *   do not call it on a stream that is capturing.  Returns OPM_OK,
+ *   OPM_ERR_ARG, OPM_ERR_PATTERN or OPM_ERR_CUDA.
  * Its scratch is a fixed 131,328-byte array in device memory that every GPU
  * using the library holds until the process exits.  The first call on a
  * device looks up that array's device address (once per device, with the
